@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 multi-objective Digital Annealer (MDA).
+
+One *step* is one complete anneal of the workload: every replica runs all
+I_max iterations of Alg. 3 (Sec. 3.3 of arXiv 2205.13399) -- parallel-trial
+acceptance over all n^2 bits, one flip, archive update or archive jump --
+through the C ABI.  Default workload: n = 25 (625-bit QUBO), 128 replicas,
+I_max = 10^5, seed 0; synthetic instance (rounded Euclidean distances on a
+100 x 100 grid, uniform [0, 99] flows with Gaussian-copula correlation 0.5).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload P25]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  ``value`` is replica-steps/s of the whole
+job from CUDA-event kernel times (inputs resident); ``e2e`` is the same
+metric through the public API with host matrices (instance upload, anneal,
+merged non-dominated archive read-back) timed by wall clock.  Under torchrun
+every rank anneals its own replica indices (weak scaling, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Algorithmic integer work of one bit-trial (one bit tested at one
+# iteration): field update 2, Delta E of both objectives with the penalty
+# term 10, acceptance penalty and threshold tests 6, ballot bookkeeping 2.
+OPS_PER_BIT_TRIAL = 20
+# INT32 lanes per SM (4 sub-partitions x 32 lanes issue one warp
+# instruction per clock each).
+INT_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["moda", "reference"], default="moda")
+    ap.add_argument("--workload", default="P25", choices=["P8", "P25", "P50", "P75"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--I-max", dest="I_max", type=int, default=None,
+                    help="override the workload's iteration budget (profiling only)")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard(total_replicas: int, rank: int, world: int):
+    """Weak scaling: every rank anneals ``total_replicas`` runs with its own
+    replica indices [rank * total, (rank + 1) * total)."""
+    return rank * total_replicas, total_replicas
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(workload: str, budget_threads: int | None = None):
+    """The CPU oracle, as it stands, on the host cores: one replica per core,
+    each for the workload's full I_max (the whole cooling schedule)."""
+    import oracle
+    from paper_2205_13399_gb300 import inputs
+    inst = inputs.workload_instance(workload)
+    run = inputs.WORKLOAD_RUN[workload]
+    cores = budget_threads or (os.cpu_count() or 1)
+    reps = min(cores, run["replicas"])
+    I_max = run["I_max"]
+    oi = oracle.Instance(inst.F1, inst.F2, inst.D)
+    t0 = time.perf_counter()
+    oracle.run(oi, I_max=I_max, replicas=range(reps), seed=run["seed"], threads=cores)
+    dt = time.perf_counter() - t0
+    value = reps * I_max / dt
+    return {"value": value, "unit": "replica-steps/s", "cores": min(cores, reps),
+            "kind": "oracle",
+            "sample": f"{reps} of {run['replicas']} replicas, full I_max={I_max}, "
+                      f"{dt:.1f} s wall"}, dt
+
+
+def workload_config(workload, inst, run, extra=None):
+    cfg = {"workload": f"{workload}: bi-objective QAP n={inst.n} ({inst.n * inst.n}-bit QUBO), "
+                       f"{run['replicas']} replicas, I_max={run['I_max']}",
+           "n": inst.n, "bits": inst.n * inst.n, "replicas": run["replicas"],
+           "I_max": run["I_max"], "seed": run["seed"], "accept": "strict",
+           "archive": "explore", "escape": "archive",
+           "schedule": {"delta0": 1e9, "deltaf": 1e4, "xi": 1e-3},
+           "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2205_13399_gb300 import inputs
+    inst = inputs.workload_instance(args.workload)
+    run = inputs.WORKLOAD_RUN[args.workload]
+    vals, dts = [], []
+    base = None
+    for k in range(args.warmup + args.steps):
+        base, dt = cpu_baseline(args.workload)
+        if k >= args.warmup:
+            vals.append(base["value"])
+            dts.append(dt)
+    value = statistics.median(vals)
+    rep_steps = run["replicas"] * run["I_max"]
+    line = {
+        "impl": "reference", "metric": "replica-steps/s", "value": value,
+        "unit": "replica-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * rep_steps / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(args.workload, inst, run),
+        "cpu_baseline": {**base, "value": value},
+        "e2e": {"value": value, "unit": "replica-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "note": "the CPU oracle timed on a bounded sample of the workload per step; "
+                "ms_per_step extrapolates to the full workload",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2205_13399_gb300 import inputs, moda
+
+    inst_np = inputs.workload_instance(args.workload)
+    run = dict(inputs.WORKLOAD_RUN[args.workload])
+    if args.I_max is not None:
+        run["I_max"] = args.I_max
+    R, I_max = run["replicas"], run["I_max"]
+    base, R = shard(R, rank, world)
+    m = inst_np.n * inst_np.n
+    g = moda.Instance(inst_np.F1, inst_np.F2, inst_np.D)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kw = dict(replicas=R, replica_base=base, I_max=I_max, seed=run["seed"],
+              block_threads=args.block_threads)
+
+    def step():
+        r = moda.anneal(g, stream=stream, **kw).wait()
+        ms = r.elapsed_ms()
+        r.close()
+        return ms, None
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    kernel_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ms, _ = step()
+        kernel_ms.append(ms)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = reduce_max(sum(kernel_ms), world, dev)
+    rep_steps_all = R * I_max * args.steps * world
+    value = rep_steps_all / (total_ms / 1e3)
+
+    # End to end through the public API with host buffers.
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 3))
+    h2d = 3 * m * 4  # Fs1, Fs2, D uploaded as int32 by moda_create_instance
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    npts = 0
+    for _ in range(e2e_steps):
+        gi = moda.Instance(inst_np.F1, inst_np.F2, inst_np.D)
+        r = moda.anneal(gi, stream=stream, **kw).wait()
+        front = r.read_archive(-1)
+        npts = len(front)
+        r.close()
+        gi.close()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    W = (m + 31) // 32
+    s = m
+    d2h = R * 4 + R * s * 16 + npts * W * 4
+    e2e_value = R * I_max * e2e_steps * world / e2e_s
+
+    # Roofline of the annealing kernel: integer issue bound.
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_ops = sms * INT_LANES_PER_SM * sm_max_mhz * 1e6
+    ops_per_launch = R * I_max * m * OPS_PER_BIT_TRIAL
+    mean_launch_s = statistics.mean(kernel_ms) / 1e3
+    achieved = ops_per_launch / mean_launch_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "anneal_kernel",
+                "per_unit": f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial",
+                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} INT32 lanes x "
+                               f"{sm_max_mhz:.0f} MHz (derived; no measured INT peak)"}
+
+    line = {
+        "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": workload_config(args.workload, inst_np, run,
+                                  {"parallelism": f"replicas x{world} GPU(s)"}),
+        "bit_trials_per_s": value * m,
+        "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": args.steps,
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * moda.h -- C ABI of the GB300 multi-objective Digital Annealer (MDA) for
+ * the bi-objective quadratic assignment problem (bQAP).
+ *
+ * Method: Ayodele, Allmendinger, Lopez-Ibanez, Parizy, "Multi-objective QUBO
+ * Solver: Bi-objective Quadratic Assignment Problem", arXiv 2205.13399.
+ *   - Sec. 2.3, Eq. bf / mqap: the two penalised energies
+ *       E_k(x) = c_k(x) + alpha_k g(x),
+ *       c_k(x) = sum_{i,j,u,v} h^k_ij d_uv x_iu x_jv (Eq. cqap),
+ *       g(x)   = sum_i (1 - sum_u x_iu)^2 + sum_u (1 - sum_i x_iu)^2 (Eq. gqap),
+ *     over the n*n-bit two-way one-hot encoding (Sec. 2.2): bit i*n + u is
+ *     set when facility i sits at location u.
+ *   - Sec. 3.2, Eq. vermap / wvermaa and Sec. 3.3: alpha_k = w_k / 2 with
+ *     w_k the largest change of c_k one flip can make.
+ *   - Sec. 3.3, Alg. 3: the MDA loop (cooling, Delta E of every bit by
+ *     Eq. cale, parallel trial by Eq. pacceptms or pacceptml, one accepted
+ *     flip picked uniformly, archive update by Alg. 4 or Alg. 5, otherwise a
+ *     jump to a random archive member); the alternative escape raises an
+ *     energy offset by beta as the single-objective DA does (Alg. 1,
+ *     Eq. paccepts).
+ *
+ * Every replica is an independent run of Alg. 3 with its own random stream:
+ * Philox4x32-10 keyed by the seed, counter (bit group, iteration, replica
+ * index, purpose).  The acceptance variate of bit p at iteration t is the
+ * top 16 bits of word p mod 4 of counter (p / 4, t, replica, 0); a bit with
+ * penalty a >= 0 (strict: sum_k max(0, dE_k); lenient: min_k max(0, dE_k);
+ * dE_k reduced by the offset when that escape is used) is accepted iff
+ * (double)a <= delta_t * (-ln((idx + 0.5) / 65536)) in IEEE double.  Runs
+ * are bit-exact and independent of how replicas are placed on the device.
+ *
+ * Conventions for every call:
+ *   - Status codes, never exceptions; on error no output is written and
+ *     moda_last_error() returns a message (thread-local).
+ *   - Host pointers are read during the call only; the library copies what
+ *     it keeps.  Handles are owned by the library and freed by their
+ *     destroy call.
+ *   - Device work runs on the CUDA device that is current on the calling
+ *     thread when the instance is created; later calls switch to it.
+ *   - Flows and distances are non-negative int16; distances symmetric with
+ *     a zero diagonal (MODA_EINVAL otherwise).  n in [2, 128].
+ */
+#ifndef MODA_H_
+#define MODA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MODA_OK = 0,
+  MODA_EINVAL = 1,       /* bad argument */
+  MODA_ENOMEM = 2,       /* host or device allocation failed */
+  MODA_EOVERFLOW = 3,    /* a local field could leave int32 (see below) */
+  MODA_EUNSUPPORTED = 4, /* size or mode this build does not handle */
+  MODA_ECUDA = 5,        /* CUDA runtime error, or a device-side check */
+  MODA_ETIMEOUT = 6,     /* moda_wait ran out of time; the run continues */
+  MODA_EBUSY = 7         /* the run is still executing */
+} moda_status;
+
+typedef struct moda_instance_s *moda_instance;
+typedef struct moda_run_s *moda_run;
+
+/* Sec. 3.3: strict = product of the per-objective probabilities
+ * (Eq. pacceptms); lenient = their maximum (Eq. pacceptml). */
+typedef enum { MODA_STRICT = 0, MODA_LENIENT = 1 } moda_accept;
+/* Sec. 3.3: explorative (Alg. 4) or exploitative (Alg. 5) update. */
+typedef enum { MODA_EXPLORE = 0, MODA_EXPLOIT = 1 } moda_archive;
+/* Escape when no flip is accepted: jump to a random archive member
+ * (Alg. 3), or raise the energy offset by beta (Alg. 1, Eq. paccepts). */
+typedef enum { MODA_ESC_ARCHIVE = 0, MODA_ESC_OFFSET = 1 } moda_escape;
+
+/* Penalty weights.  kind 0: w_k = (max_i sum_j Fs^k_ij) * (max_u sum_v d_uv)
+ * with Fs^k = F^k + F^k^T, which is Eq. vermap on the symmetric form of
+ * the cost QUBO when flows and distances are non-negative; kind 1: the
+ * given w1, w2 (>= 0).  alpha_k = w_k / 2; g is always even, so every
+ * energy is an exact integer. */
+typedef struct {
+  int32_t kind;
+  int64_t w1, w2;
+} moda_penalty;
+
+/* Parameters of one anneal (Table 1 of the paper gives delta0 = 1e9,
+ * deltaf = 1e4, xi = 1e-3, s = m, I_max = 0.25 m^2, beta = delta0 / I_max). */
+typedef struct {
+  int32_t replicas;      /* independent runs, >= 1 */
+  int32_t replica_base;  /* replica index of the first run (RNG counter) */
+  int64_t I_max;         /* iterations, 0 <= I_max < 2^32 */
+  double delta0;         /* initial temperature, > 0 */
+  double deltaf;         /* final temperature, > 0 */
+  double xi;             /* decay, 0 < xi < 1 */
+  int64_t beta;          /* offset increase (MODA_ESC_OFFSET), >= 0 */
+  int32_t archive_size;  /* s, 0 means m = n*n; 1 <= s <= m */
+  int32_t accept;        /* moda_accept */
+  int32_t archive;       /* moda_archive */
+  int32_t escape;        /* moda_escape */
+  uint64_t seed;         /* Philox key */
+  int32_t block_threads; /* 0: pick automatically; else a multiple of 32 */
+  int32_t trace;         /* 1: record (E1, E2, event) of every iteration */
+} moda_params;
+
+/* One archive member as returned by moda_read_archive. */
+typedef struct {
+  int64_t E1, E2;     /* penalised energies (Eq. mqap) */
+  int64_t c1, c2;     /* QAP costs c_k = E_k - alpha_k g */
+  int64_t g;          /* constraint value (0 iff a permutation) */
+  int32_t feasible;   /* g == 0 */
+  int32_t replica;    /* run index within the anneal (0-based) */
+  int32_t slot;       /* archive slot within that run */
+  int32_t pad;
+} moda_point;
+
+/* Build an instance from host flow matrices F1, F2 and distances D, each
+ * n x n row-major int16 (Sec. 2.3: h_kij and d_uv).  Copies them to the
+ * current device.  MODA_EOVERFLOW when (max_i sum_j Fs^k_ij) *
+ * (max_u sum_v d_uv) >= 2^31 for either objective, the bound of the int32
+ * local fields.  pen == NULL selects kind 0. */
+moda_status moda_create_instance(int32_t n, const int16_t *F1,
+                                 const int16_t *F2, const int16_t *D,
+                                 const moda_penalty *pen, moda_instance *out);
+void moda_destroy_instance(moda_instance inst);
+/* n and the penalty weights w1, w2 of an instance (any pointer may be
+ * NULL). */
+moda_status moda_instance_info(moda_instance inst, int32_t *n, int64_t *w1,
+                               int64_t *w2);
+
+/* Enqueue params->replicas independent runs of Alg. 3 on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream) and return at once.
+ * The run owns its device buffers until moda_destroy_run. */
+moda_status moda_anneal(moda_instance inst, const moda_params *params,
+                        void *cuda_stream, moda_run *out);
+
+/* Wait for a run: MODA_OK when it finished, MODA_ETIMEOUT when timeout_ms
+ * (>= 0; < 0 waits forever) passed first, MODA_ECUDA on a device error. */
+moda_status moda_wait(moda_run run, int64_t timeout_ms);
+
+/* Raw per-run results of a finished run, replica r (0-based), or all
+ * replicas at once when r == -1 (arrays then hold `replicas` blocks):
+ *   count    [1]        archive size |A|
+ *   E        [s][2]     archive energies (E1, E2) in slot order
+ *   bits     [s][W]     archive states, W = ceil(m / 32) words, bit p in
+ *                       word p / 32 at position p % 32
+ *   x        [W]        state after the last iteration
+ *   E_final  [2]        its energies
+ *   stats    [4]        accepted flips, jumps to the archive, escapes with an
+ *                       empty archive, offset raises
+ * Any pointer may be NULL.  MODA_EBUSY while the run executes. */
+moda_status moda_read_replica(moda_run run, int32_t r, int32_t *count,
+                              int64_t *E, uint32_t *bits, uint32_t *x,
+                              int64_t *E_final, int64_t *stats);
+
+/* (E1, E2, event) of every iteration of replica r when params.trace was
+ * set: event >= 0 is the flipped bit, -1 - slot a jump to that archive slot,
+ * INT64_MIN an iteration without a flip or a jump.  trace holds I_max * 3
+ * values. */
+moda_status moda_read_trace(moda_run run, int32_t r, int64_t *trace);
+
+/* The non-dominated members of replica r's archive (r >= 0), or of the
+ * union of all replicas (r == -1), Sec. 3.3 "return all non-dominated
+ * solutions from archive A" and Sec. 4.2 (merging runs).  Among equal
+ * energy vectors the lowest (replica, slot) is kept.  Points are sorted by
+ * E1.  Writes min(cap, total) points and sets *count to the total.  perms,
+ * if not NULL, receives n bytes per written point: the location of each
+ * facility, or 0xFF for an infeasible point. */
+moda_status moda_read_archive(moda_run run, int32_t r, moda_point *pts,
+                              int32_t cap, int32_t *count, uint8_t *perms);
+
+/* Device time of the anneal kernel of a finished run, in milliseconds
+ * (CUDA events on the run's stream). */
+moda_status moda_run_elapsed_ms(moda_run run, float *ms);
+
+void moda_destroy_run(moda_run run);
+
+/* Thread-local message of the last failed call on this thread. */
+const char *moda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MODA_H_ */

@@ -254,7 +254,8 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
         archive_size: int = 0, check: bool = False, trace: bool = False,
         threads: int | None = None) -> dict:
-    """Alg. 3 for each replica index in ``replicas``.
+    """Alg. 3 for each replica index in ``replicas`` (an int r means the
+    replica indices 0..r-1).
 
     Returns numpy arrays: ``count`` [R], ``E`` [R, s, 2], ``bits`` [R, s, m],
     ``x`` [R, m], ``E_final`` [R, 2], ``stats`` [R, 4] (flips, jumps to the
@@ -262,6 +263,8 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
     [R, I_max, 3] (E1, E2, event) when asked for.
     """
     lib = _load()
+    if isinstance(replicas, (int, np.integer)):
+        replicas = range(int(replicas))  # a count means replicas 0..count-1
     reps = np.ascontiguousarray(np.asarray(replicas, dtype=np.uint32).reshape(-1))
     R, m = reps.size, inst.m
     s = archive_size if archive_size > 0 else m

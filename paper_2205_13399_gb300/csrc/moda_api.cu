@@ -1,0 +1,588 @@
+// Host side of the C ABI declared in include/moda.h: validation, instance
+// upload, the cooling schedule with its integer acceptance thresholds, the
+// -ln(u) table, run buffers, launch, wait and result read-back.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "moda.h"
+#include "moda_internal.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+moda_status fail(moda_status st, const std::string &msg) {
+  g_error = msg;
+  return st;
+}
+
+moda_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(MODA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MODA_CUDA(call)                                 \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Per-device constant data: the -ln(u) table and schedules.
+struct DeviceData {
+  double *table = nullptr;
+  double tmin = 0, tmax = 0;
+  struct Sched {
+    double *delta = nullptr;
+    int64_t *lo = nullptr, *hi = nullptr;
+    int32_t count = 0;
+    bool frozen = false;  // the last entry holds for every later iteration
+  };
+  std::map<std::tuple<double, double, double>, Sched> schedules;
+};
+
+std::mutex g_dev_mutex;
+std::map<int, DeviceData> g_dev;
+
+std::vector<double> neglog_table_host() {
+  std::vector<double> T(moda::kTableSize);
+  for (int idx = 0; idx < moda::kTableSize; ++idx)
+    T[idx] = -std::log((static_cast<double>(idx) + 0.5) / 65536.0);
+  return T;
+}
+
+// Returns the device table (built once per device); caller holds the lock.
+moda_status device_table(int dev, DeviceData **out) {
+  DeviceData &dd = g_dev[dev];
+  if (!dd.table) {
+    std::vector<double> T = neglog_table_host();
+    double *d = nullptr;
+    MODA_CUDA(cudaMalloc(&d, sizeof(double) * T.size()));
+    cudaError_t e = cudaMemcpy(d, T.data(), sizeof(double) * T.size(),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "upload -ln(u) table");
+    }
+    dd.table = d;
+    dd.tmax = T.front();
+    dd.tmin = T.back();
+  }
+  *out = &dd;
+  return MODA_OK;
+}
+
+// Alg. 3: before each iteration, "if delta > delta_f: delta <- delta (1 -
+// xi)".  The entries stop changing at the first delta <= delta_f; later
+// iterations reuse the last entry.  Thresholds: a <= floor(delta T_min)
+// accepts for every draw, a > floor(delta T_max) rejects for every draw,
+// because delta * T is monotone in T under IEEE rounding.
+moda_status device_schedule(DeviceData &dd, double d0, double df, double xi,
+                            int64_t I_max, DeviceData::Sched *out) {
+  auto key = std::make_tuple(d0, df, xi);
+  auto it = dd.schedules.find(key);
+  if (it != dd.schedules.end() &&
+      (it->second.frozen || it->second.count >= I_max)) {
+    *out = it->second;
+    return MODA_OK;
+  }
+  std::vector<double> delta;
+  std::vector<int64_t> lo, hi;
+  double d = d0;
+  const double factor = 1.0 - xi;
+  bool frozen = false;
+  for (int64_t t = 1; t <= std::max<int64_t>(I_max, 1); ++t) {
+    if (d > df) d = d * factor;
+    delta.push_back(d);
+    lo.push_back(static_cast<int64_t>(std::floor(d * dd.tmin)));
+    hi.push_back(static_cast<int64_t>(std::floor(d * dd.tmax)));
+    if (!(d > df)) {
+      frozen = true;
+      break;
+    }
+  }
+  DeviceData::Sched s;
+  s.count = static_cast<int32_t>(delta.size());
+  s.frozen = frozen;
+  MODA_CUDA(cudaMalloc(&s.delta, sizeof(double) * delta.size()));
+  MODA_CUDA(cudaMalloc(&s.lo, sizeof(int64_t) * lo.size()));
+  MODA_CUDA(cudaMalloc(&s.hi, sizeof(int64_t) * hi.size()));
+  MODA_CUDA(cudaMemcpy(s.delta, delta.data(), sizeof(double) * delta.size(),
+                       cudaMemcpyHostToDevice));
+  MODA_CUDA(cudaMemcpy(s.lo, lo.data(), sizeof(int64_t) * lo.size(),
+                       cudaMemcpyHostToDevice));
+  MODA_CUDA(cudaMemcpy(s.hi, hi.data(), sizeof(int64_t) * hi.size(),
+                       cudaMemcpyHostToDevice));
+  // A shorter schedule for the same key may still be read by a run in
+  // flight, so it is kept, not freed.
+  dd.schedules[key] = s;
+  *out = s;
+  return MODA_OK;
+}
+
+}  // namespace
+
+struct moda_instance_s {
+  int32_t n = 0, m = 0, W = 0;
+  int device = 0;
+  int64_t w1 = 0, w2 = 0;
+  std::vector<int32_t> Fs1, Fs2, D;  // host copies
+  int32_t *dFs1 = nullptr, *dFs2 = nullptr, *dD = nullptr;
+};
+
+struct moda_run_s {
+  moda_instance inst = nullptr;
+  moda_params prm{};
+  int32_t R = 0, s = 0, threads = 0, bpt = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t start = nullptr, stop = nullptr;
+  int64_t *arch_E = nullptr;
+  uint32_t *arch_bits = nullptr;
+  int32_t *arch_count = nullptr;
+  uint32_t *x_final = nullptr;
+  int64_t *E_final = nullptr;
+  int64_t *stats = nullptr;
+  int64_t *trace = nullptr;
+  int32_t *error = nullptr;
+  bool checked = false;
+};
+
+namespace {
+
+void free_run_buffers(moda_run r) {
+  void *ptrs[] = {r->arch_E, r->arch_bits, r->arch_count, r->x_final,
+                  r->E_final, r->stats, r->trace, r->error};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (r->start) cudaEventDestroy(r->start);
+  if (r->stop) cudaEventDestroy(r->stop);
+}
+
+bool run_done(moda_run r) { return cudaEventQuery(r->stop) == cudaSuccess; }
+
+}  // namespace
+
+extern "C" {
+
+const char *moda_last_error(void) { return g_error.c_str(); }
+
+moda_status moda_create_instance(int32_t n, const int16_t *F1,
+                                 const int16_t *F2, const int16_t *D,
+                                 const moda_penalty *pen, moda_instance *out) {
+  if (!out) return fail(MODA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!F1 || !F2 || !D) return fail(MODA_EINVAL, "NULL matrix");
+  if (n < 2 || n > moda::kMaxN)
+    return fail(MODA_EINVAL, "n must be in [2, 128]");
+  if (pen && pen->kind != 0 && pen->kind != 1)
+    return fail(MODA_EINVAL, "penalty kind must be 0 or 1");
+  if (pen && pen->kind == 1 && (pen->w1 < 0 || pen->w2 < 0))
+    return fail(MODA_EINVAL, "explicit penalty weights must be >= 0");
+  const int nn = n * n;
+  for (int e = 0; e < nn; ++e)
+    if (F1[e] < 0 || F2[e] < 0 || D[e] < 0)
+      return fail(MODA_EINVAL, "flows and distances must be non-negative");
+  for (int a = 0; a < n; ++a) {
+    if (D[a * n + a] != 0)
+      return fail(MODA_EINVAL, "distance matrix needs a zero diagonal");
+    for (int b = 0; b < a; ++b)
+      if (D[a * n + b] != D[b * n + a])
+        return fail(MODA_EINVAL, "distance matrix must be symmetric");
+  }
+  moda_instance inst = new (std::nothrow) moda_instance_s;
+  if (!inst) return fail(MODA_ENOMEM, "host allocation");
+  inst->n = n;
+  inst->m = nn;
+  inst->W = (nn + 31) / 32;
+  inst->Fs1.resize(nn);
+  inst->Fs2.resize(nn);
+  inst->D.resize(nn);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      inst->Fs1[i * n + j] = (int32_t)F1[i * n + j] + (int32_t)F1[j * n + i];
+      inst->Fs2[i * n + j] = (int32_t)F2[i * n + j] + (int32_t)F2[j * n + i];
+      inst->D[i * n + j] = D[i * n + j];
+    }
+  // Bound of every local field and of w_k: (max row sum of Fs) x (max row
+  // sum of D).
+  int64_t dmax = 0, f1max = 0, f2max = 0;
+  for (int i = 0; i < n; ++i) {
+    int64_t sd = 0, s1 = 0, s2 = 0;
+    for (int j = 0; j < n; ++j) {
+      sd += inst->D[i * n + j];
+      s1 += inst->Fs1[i * n + j];
+      s2 += inst->Fs2[i * n + j];
+    }
+    dmax = std::max(dmax, sd);
+    f1max = std::max(f1max, s1);
+    f2max = std::max(f2max, s2);
+  }
+  const int64_t b1 = f1max * dmax, b2 = f2max * dmax;
+  if (b1 >= (int64_t(1) << 31) || b2 >= (int64_t(1) << 31)) {
+    delete inst;
+    return fail(MODA_EOVERFLOW, "local fields may exceed int32");
+  }
+  if (pen && pen->kind == 1) {
+    inst->w1 = pen->w1;
+    inst->w2 = pen->w2;
+  } else {
+    inst->w1 = b1;
+    inst->w2 = b2;
+  }
+  cudaGetDevice(&inst->device);
+  const size_t bytes = sizeof(int32_t) * nn;
+  cudaError_t e = cudaMalloc(&inst->dFs1, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&inst->dFs2, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&inst->dD, bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(inst->dFs1, inst->Fs1.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(inst->dFs2, inst->Fs2.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(inst->dD, inst->D.data(), bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    moda_destroy_instance(inst);
+    return cuda_fail(e, "instance upload");
+  }
+  *out = inst;
+  return MODA_OK;
+}
+
+void moda_destroy_instance(moda_instance inst) {
+  if (!inst) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(inst->device);
+  if (inst->dFs1) cudaFree(inst->dFs1);
+  if (inst->dFs2) cudaFree(inst->dFs2);
+  if (inst->dD) cudaFree(inst->dD);
+  cudaSetDevice(prev);
+  delete inst;
+}
+
+moda_status moda_instance_info(moda_instance inst, int32_t *n, int64_t *w1,
+                               int64_t *w2) {
+  if (!inst) return fail(MODA_EINVAL, "NULL instance");
+  if (n) *n = inst->n;
+  if (w1) *w1 = inst->w1;
+  if (w2) *w2 = inst->w2;
+  return MODA_OK;
+}
+
+moda_status moda_anneal(moda_instance inst, const moda_params *p,
+                        void *cuda_stream, moda_run *out) {
+  if (!out) return fail(MODA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!inst || !p) return fail(MODA_EINVAL, "NULL instance or params");
+  const int m = inst->m;
+  if (p->replicas < 1) return fail(MODA_EINVAL, "replicas must be >= 1");
+  if (p->I_max < 0 || p->I_max > 0xFFFFFFFFll)
+    return fail(MODA_EINVAL, "I_max must be in [0, 2^32)");
+  if (!(p->delta0 > 0) || !(p->deltaf > 0) || !(p->xi > 0) || !(p->xi < 1))
+    return fail(MODA_EINVAL, "need delta0 > 0, deltaf > 0, 0 < xi < 1");
+  if (p->beta < 0) return fail(MODA_EINVAL, "beta must be >= 0");
+  if (p->archive_size < 0 || p->archive_size > m)
+    return fail(MODA_EINVAL, "archive_size must be in [0, m]");
+  if (p->accept != MODA_STRICT && p->accept != MODA_LENIENT)
+    return fail(MODA_EINVAL, "accept must be MODA_STRICT or MODA_LENIENT");
+  if (p->archive != MODA_EXPLORE && p->archive != MODA_EXPLOIT)
+    return fail(MODA_EINVAL, "archive must be MODA_EXPLORE or MODA_EXPLOIT");
+  if (p->escape != MODA_ESC_ARCHIVE && p->escape != MODA_ESC_OFFSET)
+    return fail(MODA_EINVAL, "escape must be MODA_ESC_ARCHIVE or MODA_ESC_OFFSET");
+  if ((uint64_t)p->replica_base + (uint64_t)p->replicas > 0x100000000ull)
+    return fail(MODA_EINVAL, "replica indices must fit 32 bits");
+
+  // Block shape: B bits per thread, T threads, B * T >= m.
+  int T = 0, B = 0;
+  if (p->block_threads > 0) {
+    if (p->block_threads % 32 || p->block_threads > moda::kMaxThreads)
+      return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 1024");
+    T = p->block_threads;
+    for (int b : {1, 2, 4, 8})
+      if ((int64_t)b * T >= m) {
+        B = b;
+        break;
+      }
+    if (!B) return fail(MODA_EUNSUPPORTED, "block_threads too small for n");
+  } else {
+    for (int b : {1, 2, 4, 8})
+      if ((int64_t)b * moda::kMaxThreads >= m) {
+        B = b;
+        break;
+      }
+    if (!B) return fail(MODA_EUNSUPPORTED, "n too large for this build");
+    T = ((m + B - 1) / B + 31) / 32 * 32;
+  }
+  const moda::SmemLayout lay = moda::smem_layout(inst->n, m, T, B);
+  int dev_smem = 0;
+  cudaSetDevice(inst->device);
+  MODA_CUDA(cudaDeviceGetAttribute(&dev_smem,
+                                   cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                   inst->device));
+  if ((int64_t)lay.total > dev_smem)
+    return fail(MODA_EUNSUPPORTED, "shared memory need exceeds the device limit");
+
+  moda_run r = new (std::nothrow) moda_run_s;
+  if (!r) return fail(MODA_ENOMEM, "host allocation");
+  r->inst = inst;
+  r->prm = *p;
+  r->R = p->replicas;
+  r->s = p->archive_size > 0 ? p->archive_size : m;
+  r->threads = T;
+  r->bpt = B;
+  r->stream = static_cast<cudaStream_t>(cuda_stream);
+
+  const size_t R = r->R, s = r->s, W = inst->W;
+  moda_status st = MODA_OK;
+  auto alloc = [&](void **ptr, size_t bytes) {
+    if (st != MODA_OK) return;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) st = fail(MODA_ENOMEM, std::string("device allocation: ") +
+                                                     cudaGetErrorString(e));
+  };
+  alloc((void **)&r->arch_E, R * s * 2 * sizeof(int64_t));
+  alloc((void **)&r->arch_bits, R * s * W * sizeof(uint32_t));
+  alloc((void **)&r->arch_count, R * sizeof(int32_t));
+  alloc((void **)&r->x_final, R * W * sizeof(uint32_t));
+  alloc((void **)&r->E_final, R * 2 * sizeof(int64_t));
+  alloc((void **)&r->stats, R * 4 * sizeof(int64_t));
+  alloc((void **)&r->error, sizeof(int32_t));
+  if (p->trace && p->I_max > 0)
+    alloc((void **)&r->trace, R * (size_t)p->I_max * 3 * sizeof(int64_t));
+  if (st != MODA_OK) {
+    free_run_buffers(r);
+    delete r;
+    return st;
+  }
+
+  DeviceData *dd = nullptr;
+  DeviceData::Sched sch;
+  {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    st = device_table(inst->device, &dd);
+    if (st == MODA_OK)
+      st = device_schedule(*dd, p->delta0, p->deltaf, p->xi, p->I_max, &sch);
+  }
+  if (st != MODA_OK) {
+    free_run_buffers(r);
+    delete r;
+    return st;
+  }
+
+  moda::AnnealArgs a{};
+  a.n = inst->n;
+  a.m = m;
+  a.W = inst->W;
+  a.s = r->s;
+  a.I_max = p->I_max;
+  a.replica_base = (uint32_t)p->replica_base;
+  a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
+  a.seed_hi = (uint32_t)(p->seed >> 32);
+  a.w1 = inst->w1;
+  a.w2 = inst->w2;
+  a.beta = p->beta;
+  a.accept = p->accept;
+  a.archive = p->archive;
+  a.escape = p->escape;
+  a.nsched = sch.count;
+  a.sch_delta = sch.delta;
+  a.sch_lo = sch.lo;
+  a.sch_hi = sch.hi;
+  a.table = dd->table;
+  a.Fs1 = inst->dFs1;
+  a.Fs2 = inst->dFs2;
+  a.D = inst->dD;
+  a.arch_E = r->arch_E;
+  a.arch_bits = r->arch_bits;
+  a.arch_count = r->arch_count;
+  a.x_final = r->x_final;
+  a.E_final = r->E_final;
+  a.stats = r->stats;
+  a.trace = r->trace;
+  a.error = r->error;
+
+  cudaError_t e = cudaEventCreate(&r->start);
+  if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
+  if (e == cudaSuccess) e = cudaMemsetAsync(r->error, 0, sizeof(int32_t), r->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(r->start, r->stream);
+  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, r->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(r->stop, r->stream);
+  if (e != cudaSuccess) {
+    free_run_buffers(r);
+    delete r;
+    return cuda_fail(e, "launch");
+  }
+  *out = r;
+  return MODA_OK;
+}
+
+moda_status moda_wait(moda_run r, int64_t timeout_ms) {
+  if (!r) return fail(MODA_EINVAL, "NULL run");
+  cudaSetDevice(r->inst->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(r->stop);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "run");
+    if (timeout_ms >= 0) {
+      const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                          std::chrono::steady_clock::now() - t0)
+                          .count();
+      if (ms >= timeout_ms) return fail(MODA_ETIMEOUT, "run still executing");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (!r->checked) {
+    int32_t err = 0;
+    MODA_CUDA(cudaMemcpy(&err, r->error, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err != 0) return fail(MODA_ECUDA, "device-side check failed: code " +
+                                              std::to_string(err));
+    r->checked = true;
+  }
+  return MODA_OK;
+}
+
+moda_status moda_read_replica(moda_run r, int32_t rep, int32_t *count,
+                              int64_t *E, uint32_t *bits, uint32_t *x,
+                              int64_t *E_final, int64_t *stats) {
+  if (!r) return fail(MODA_EINVAL, "NULL run");
+  if (rep < -1 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  const size_t first = rep < 0 ? 0 : (size_t)rep;
+  const size_t cnt = rep < 0 ? (size_t)r->R : 1;
+  const size_t s = r->s, W = r->inst->W;
+  auto d2h = cudaMemcpyDeviceToHost;
+  if (count)
+    MODA_CUDA(cudaMemcpy(count, r->arch_count + first, cnt * sizeof(int32_t), d2h));
+  if (E)
+    MODA_CUDA(cudaMemcpy(E, r->arch_E + first * s * 2, cnt * s * 2 * sizeof(int64_t), d2h));
+  if (bits)
+    MODA_CUDA(cudaMemcpy(bits, r->arch_bits + first * s * W,
+                         cnt * s * W * sizeof(uint32_t), d2h));
+  if (x)
+    MODA_CUDA(cudaMemcpy(x, r->x_final + first * W, cnt * W * sizeof(uint32_t), d2h));
+  if (E_final)
+    MODA_CUDA(cudaMemcpy(E_final, r->E_final + first * 2, cnt * 2 * sizeof(int64_t), d2h));
+  if (stats)
+    MODA_CUDA(cudaMemcpy(stats, r->stats + first * 4, cnt * 4 * sizeof(int64_t), d2h));
+  return MODA_OK;
+}
+
+moda_status moda_read_trace(moda_run r, int32_t rep, int64_t *trace) {
+  if (!r || !trace) return fail(MODA_EINVAL, "NULL argument");
+  if (!r->trace) return fail(MODA_EINVAL, "run was not traced");
+  if (rep < 0 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  const size_t len = (size_t)r->prm.I_max * 3;
+  MODA_CUDA(cudaMemcpy(trace, r->trace + (size_t)rep * len, len * sizeof(int64_t),
+                       cudaMemcpyDeviceToHost));
+  return MODA_OK;
+}
+
+moda_status moda_read_archive(moda_run r, int32_t rep, moda_point *pts,
+                              int32_t cap, int32_t *count, uint8_t *perms) {
+  if (!r || !count) return fail(MODA_EINVAL, "NULL argument");
+  if (rep < -1 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
+  if (cap < 0 || (cap > 0 && !pts)) return fail(MODA_EINVAL, "bad output buffer");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  const int n = r->inst->n, W = r->inst->W;
+  const size_t s = r->s;
+  const int first = rep < 0 ? 0 : rep, last = rep < 0 ? r->R : rep + 1;
+  const size_t nrep = (size_t)(last - first);
+  std::vector<int32_t> counts(nrep);
+  std::vector<int64_t> E(nrep * s * 2);
+  moda_status st = moda_read_replica(r, rep, counts.data(), E.data(), nullptr,
+                                     nullptr, nullptr, nullptr);
+  if (st != MODA_OK) return st;
+  struct Cand {
+    int64_t e1, e2;
+    int32_t rep, slot;
+  };
+  std::vector<Cand> c;
+  for (size_t q = 0; q < nrep; ++q)
+    for (int32_t k = 0; k < counts[q]; ++k)
+      c.push_back({E[(q * s + k) * 2], E[(q * s + k) * 2 + 1], (int32_t)(first + q), k});
+  std::sort(c.begin(), c.end(), [](const Cand &a, const Cand &b) {
+    if (a.e1 != b.e1) return a.e1 < b.e1;
+    if (a.e2 != b.e2) return a.e2 < b.e2;
+    if (a.rep != b.rep) return a.rep < b.rep;
+    return a.slot < b.slot;
+  });
+  // Sweep in E1 order: a point survives iff its E2 is below every E2 seen
+  // so far (points with equal E1 and larger E2 are dominated; equal vectors
+  // keep the first, i.e. the lowest (replica, slot)).
+  std::vector<Cand> keep;
+  bool any = false;
+  int64_t best2 = 0;
+  for (const Cand &q : c) {
+    if (!any || q.e2 < best2) {
+      keep.push_back(q);
+      best2 = q.e2;
+      any = true;
+    }
+  }
+  *count = (int32_t)keep.size();
+  const int wr = std::min<int32_t>(cap, (int32_t)keep.size());
+  std::vector<uint32_t> word(W);
+  for (int k = 0; k < wr; ++k) {
+    const Cand &q = keep[k];
+    MODA_CUDA(cudaMemcpy(word.data(), r->arch_bits + ((size_t)q.rep * s + q.slot) * W,
+                         W * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    std::vector<int> rows(n, 0), cols(n, 0), loc(n, -1);
+    for (int p = 0; p < n * n; ++p)
+      if ((word[p >> 5] >> (p & 31)) & 1u) {
+        rows[p / n]++;
+        cols[p % n]++;
+        loc[p / n] = p % n;
+      }
+    int64_t g = 0;
+    for (int i = 0; i < n; ++i)
+      g += (int64_t)(1 - rows[i]) * (1 - rows[i]) + (int64_t)(1 - cols[i]) * (1 - cols[i]);
+    moda_point &o = pts[k];
+    o.E1 = q.e1;
+    o.E2 = q.e2;
+    o.g = g;
+    o.c1 = q.e1 - r->inst->w1 * (g / 2);
+    o.c2 = q.e2 - r->inst->w2 * (g / 2);
+    o.feasible = g == 0;
+    o.replica = q.rep;
+    o.slot = q.slot;
+    o.pad = 0;
+    if (perms)
+      for (int i = 0; i < n; ++i)
+        perms[(size_t)k * n + i] = g == 0 ? (uint8_t)loc[i] : (uint8_t)0xFF;
+  }
+  return MODA_OK;
+}
+
+moda_status moda_run_elapsed_ms(moda_run r, float *ms) {
+  if (!r || !ms) return fail(MODA_EINVAL, "NULL argument");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  MODA_CUDA(cudaEventElapsedTime(ms, r->start, r->stop));
+  return MODA_OK;
+}
+
+void moda_destroy_run(moda_run r) {
+  if (!r) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->inst->device);
+  if (r->stop) cudaEventSynchronize(r->stop);
+  free_run_buffers(r);
+  cudaSetDevice(prev);
+  delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the host library (moda_api.cu) and the
+// annealing kernels (moda_kernel.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace moda {
+
+constexpr int kMaxN = 128;          // n <= 128: a bit index fits (i << 8) | u
+constexpr int kMaxThreads = 1024;
+constexpr int kTableSize = 65536;   // -ln(u) table, u quantised to 2^-16
+
+// Purposes of a Philox draw (fourth counter word).
+enum : uint32_t { kTagAccept = 0, kTagSelect = 1, kTagRestart = 2,
+                  kTagExploit = 3, kTagInit = 4 };
+
+// Everything one launch of the single-instance annealing kernel needs.
+// All pointers are device pointers.
+struct AnnealArgs {
+  int32_t n, m, W;          // W = ceil(m / 32) words per bit vector
+  int32_t s;                // archive capacity
+  int64_t I_max;
+  uint32_t replica_base;
+  uint32_t seed_lo, seed_hi;
+  int64_t w1, w2;           // penalty weights, alpha_k = w_k / 2
+  int64_t beta;
+  int32_t accept, archive, escape;
+  int32_t nsched;           // entries of the schedule; later iterations
+                            // reuse the last one
+  const double *sch_delta;  // [nsched] delta_t, t = 1..nsched
+  const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
+  const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
+  const double *table;      // [65536] -ln((idx + 0.5) / 65536)
+  const int32_t *Fs1, *Fs2; // [n][n] F_k + F_k^T (symmetric)
+  const int32_t *D;         // [n][n] symmetric distances, zero diagonal
+  // outputs, one block per replica of this launch
+  int64_t *arch_E;          // [R][s][2]
+  uint32_t *arch_bits;      // [R][s][W]
+  int32_t *arch_count;      // [R]
+  uint32_t *x_final;        // [R][W]
+  int64_t *E_final;         // [R][2]
+  int64_t *stats;           // [R][4]
+  int64_t *trace;           // [R][I_max][3] or nullptr
+  int32_t *error;           // device status word, 0 = fine
+};
+
+// Byte offsets of the shared-memory carve-up of one annealing block.
+struct SmemLayout {
+  size_t Fs1, Fs2, D, L1, L2, R, C, mask, amask, ones, X, red, bcast, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) {
+  return (v + a - 1) / a * a;
+}
+
+__host__ __device__ inline SmemLayout smem_layout(int n, int m, int threads,
+                                                  int bits_per_thread) {
+  SmemLayout L;
+  size_t o = 0;
+  const size_t nn = (size_t)n * n;
+  const int nw = threads / 32;
+  L.Fs1 = o;   o = align_up(o + 4 * nn, 16);
+  L.Fs2 = o;   o = align_up(o + 4 * nn, 16);
+  L.D = o;     o = align_up(o + 4 * nn, 16);
+  L.L1 = o;    o = align_up(o + 4 * (size_t)m, 16);
+  L.L2 = o;    o = align_up(o + 4 * (size_t)m, 16);
+  L.R = o;     o = align_up(o + 4 * (size_t)n, 16);
+  L.C = o;     o = align_up(o + 4 * (size_t)n, 16);
+  L.mask = o;  o = align_up(o + 4 * (size_t)bits_per_thread * nw, 16);
+  L.amask = o; o = align_up(o + 4 * (size_t)bits_per_thread * nw, 16);
+  L.ones = o;  o = align_up(o + 2 * (size_t)m, 16);
+  L.X = o;     o = align_up(o + (size_t)m, 16);
+  L.red = o;   o = align_up(o + 8 * (size_t)32, 16);
+  L.bcast = o; o = align_up(o + 128, 16);
+  L.total = o;
+  return L;
+}
+
+// Launch one block per replica on `stream`.  Returns the launch error.
+cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,
+                          int bits_per_thread, cudaStream_t stream);
+
+// Bits per thread the kernel is instantiated for.
+bool supported_bits_per_thread(int b);
+
+}  // namespace moda

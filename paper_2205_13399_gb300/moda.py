@@ -1,0 +1,275 @@
+"""ctypes binding of the C ABI in include/moda.h (argument marshalling only).
+
+Every step of the annealing path runs in the CUDA library; this module only
+converts numpy arrays and torch streams to the plain pointers the ABI takes.
+It raises at import time when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", f"libmoda_{platform.machine()}.so")
+
+OK, EINVAL, ENOMEM, EOVERFLOW, EUNSUPPORTED, ECUDA, ETIMEOUT, EBUSY = range(8)
+STATUS_NAMES = ["MODA_OK", "MODA_EINVAL", "MODA_ENOMEM", "MODA_EOVERFLOW",
+                "MODA_EUNSUPPORTED", "MODA_ECUDA", "MODA_ETIMEOUT", "MODA_EBUSY"]
+ACCEPT = {"strict": 0, "lenient": 1}
+ARCHIVE = {"explore": 0, "exploit": 1}
+ESCAPE = {"archive": 0, "offset": 1}
+
+# Functions declared in include/moda.h.
+ABI_FUNCTIONS = [
+    "moda_create_instance", "moda_destroy_instance", "moda_instance_info",
+    "moda_anneal", "moda_wait", "moda_read_replica", "moda_read_trace",
+    "moda_read_archive", "moda_run_elapsed_ms", "moda_destroy_run",
+    "moda_last_error",
+]
+
+
+class MODAError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+        self.status = status
+
+
+class Penalty(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("w1", ctypes.c_int64), ("w2", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("replicas", ctypes.c_int32),
+        ("replica_base", ctypes.c_int32),
+        ("I_max", ctypes.c_int64),
+        ("delta0", ctypes.c_double),
+        ("deltaf", ctypes.c_double),
+        ("xi", ctypes.c_double),
+        ("beta", ctypes.c_int64),
+        ("archive_size", ctypes.c_int32),
+        ("accept", ctypes.c_int32),
+        ("archive", ctypes.c_int32),
+        ("escape", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("block_threads", ctypes.c_int32),
+        ("trace", ctypes.c_int32),
+    ]
+
+
+class Point(ctypes.Structure):
+    _fields_ = [
+        ("E1", ctypes.c_int64), ("E2", ctypes.c_int64),
+        ("c1", ctypes.c_int64), ("c2", ctypes.c_int64),
+        ("g", ctypes.c_int64),
+        ("feasible", ctypes.c_int32), ("replica", ctypes.c_int32),
+        ("slot", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libmoda is not built ({path}); run "
+                          "`python -m paper_2205_13399_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    st = ctypes.c_int
+    lib.moda_create_instance.restype = st
+    lib.moda_create_instance.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty), ctypes.POINTER(P)]
+    lib.moda_destroy_instance.restype = None
+    lib.moda_destroy_instance.argtypes = [P]
+    lib.moda_instance_info.restype = st
+    lib.moda_instance_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                       ctypes.POINTER(i64)]
+    lib.moda_anneal.restype = st
+    lib.moda_anneal.argtypes = [P, ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+    lib.moda_wait.restype = st
+    lib.moda_wait.argtypes = [P, i64]
+    lib.moda_read_replica.restype = st
+    lib.moda_read_replica.argtypes = [P, i32, P, P, P, P, P, P]
+    lib.moda_read_trace.restype = st
+    lib.moda_read_trace.argtypes = [P, i32, P]
+    lib.moda_read_archive.restype = st
+    lib.moda_read_archive.argtypes = [P, i32, ctypes.POINTER(Point), i32,
+                                      ctypes.POINTER(i32), P]
+    lib.moda_run_elapsed_ms.restype = st
+    lib.moda_run_elapsed_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.moda_destroy_run.restype = None
+    lib.moda_destroy_run.argtypes = [P]
+    lib.moda_last_error.restype = ctypes.c_char_p
+    lib.moda_last_error.argtypes = []
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(status: int):
+    if status != OK:
+        raise MODAError(status, _lib.moda_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream) -> int | None:
+    """A cudaStream_t from a torch.cuda.Stream, an int handle, or None."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Instance:
+    """A bi-objective QAP instance resident on the current CUDA device
+    (``moda_create_instance``).  F1, F2, D: n x n non-negative int16; D
+    symmetric with a zero diagonal.  ``w=(w1, w2)`` gives explicit penalty
+    weights; default: the paper's choice (Eq. vermap)."""
+
+    def __init__(self, F1, F2, D, w=None):
+        D = np.ascontiguousarray(np.asarray(D, dtype=np.int16))
+        n = int(D.shape[0])
+        self._F1 = np.ascontiguousarray(np.asarray(F1, dtype=np.int16))
+        self._F2 = np.ascontiguousarray(np.asarray(F2, dtype=np.int16))
+        self._D = D
+        pen = None if w is None else ctypes.byref(Penalty(1, int(w[0]), int(w[1])))
+        h = ctypes.c_void_p()
+        _check(_lib.moda_create_instance(n, _ptr(self._F1), _ptr(self._F2), _ptr(self._D),
+                                         pen, ctypes.byref(h)))
+        self._h = h
+        nn = ctypes.c_int32()
+        w1, w2 = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.moda_instance_info(self._h, ctypes.byref(nn), ctypes.byref(w1),
+                                       ctypes.byref(w2)))
+        self.n = nn.value
+        self.m = self.n * self.n
+        self.W = (self.m + 31) // 32
+        self.w = (w1.value, w2.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.moda_destroy_instance(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+@dataclass
+class ReplicaResult:
+    count: np.ndarray   # [R]
+    E: np.ndarray       # [R, s, 2]
+    bits: np.ndarray    # [R, s, W] uint32
+    x: np.ndarray       # [R, W] uint32
+    E_final: np.ndarray  # [R, 2]
+    stats: np.ndarray   # [R, 4]
+
+
+def unpack_bits(words: np.ndarray, m: int) -> np.ndarray:
+    """[..., W] uint32 words -> [..., m] uint8 bits (bit p in word p // 32)."""
+    w = np.asarray(words, dtype=np.uint32)
+    b = ((w[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.uint8)
+    return b.reshape(*w.shape[:-1], w.shape[-1] * 32)[..., :m]
+
+
+class Run:
+    """Handle of one enqueued anneal (``moda_anneal``)."""
+
+    def __init__(self, inst: Instance, handle, params: Params):
+        self.inst = inst  # keeps the instance alive while the run exists
+        self._h = handle
+        self.params = params
+        self.R = params.replicas
+        self.s = params.archive_size if params.archive_size > 0 else inst.m
+
+    def wait(self, timeout_ms: int = -1):
+        _check(_lib.moda_wait(self._h, int(timeout_ms)))
+        return self
+
+    def elapsed_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(_lib.moda_run_elapsed_ms(self._h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def read(self, replica: int = -1) -> ReplicaResult:
+        R = self.R if replica < 0 else 1
+        s, W = self.s, self.inst.W
+        out = ReplicaResult(
+            count=np.zeros(R, dtype=np.int32),
+            E=np.zeros((R, s, 2), dtype=np.int64),
+            bits=np.zeros((R, s, W), dtype=np.uint32),
+            x=np.zeros((R, W), dtype=np.uint32),
+            E_final=np.zeros((R, 2), dtype=np.int64),
+            stats=np.zeros((R, 4), dtype=np.int64),
+        )
+        _check(_lib.moda_read_replica(self._h, int(replica), _ptr(out.count), _ptr(out.E),
+                                      _ptr(out.bits), _ptr(out.x), _ptr(out.E_final),
+                                      _ptr(out.stats)))
+        return out
+
+    def read_trace(self, replica: int) -> np.ndarray:
+        tr = np.zeros((self.params.I_max, 3), dtype=np.int64)
+        _check(_lib.moda_read_trace(self._h, int(replica), _ptr(tr)))
+        return tr
+
+    def read_archive(self, replica: int = -1, cap: int | None = None, perms: bool = True):
+        """Non-dominated archive members (``moda_read_archive``) as a list of
+        dicts with E1, E2, c1, c2, g, feasible, replica, slot and perm."""
+        cnt = ctypes.c_int32()
+        _check(_lib.moda_read_archive(self._h, int(replica), None, 0, ctypes.byref(cnt), None))
+        total = cnt.value if cap is None else min(cap, cnt.value)
+        pts = (Point * max(total, 1))()
+        pbuf = np.zeros((max(total, 1), self.inst.n), dtype=np.uint8)
+        _check(_lib.moda_read_archive(self._h, int(replica), pts, total, ctypes.byref(cnt),
+                                      _ptr(pbuf) if perms else None))
+        out = []
+        for k in range(total):
+            p = pts[k]
+            d = dict(E1=p.E1, E2=p.E2, c1=p.c1, c2=p.c2, g=p.g, feasible=bool(p.feasible),
+                     replica=p.replica, slot=p.slot)
+            if perms:
+                d["perm"] = [int(v) for v in pbuf[k]] if p.feasible else None
+            out.append(d)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.moda_destroy_run(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "strict",
+                archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
+                deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
+                archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
+                trace: bool = False) -> Params:
+    if beta is None:
+        beta = int(round(delta0 / I_max)) if I_max > 0 else 0
+    return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
+                  float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
+                  ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
+                  int(bool(trace)))
+
+
+def anneal(inst: Instance, params: Params | None = None, stream=None, **kw) -> Run:
+    """Enqueue ``params.replicas`` independent MDA runs (``moda_anneal``) on
+    ``stream`` (a torch.cuda.Stream, a raw handle, or None for the default
+    stream) and return without waiting."""
+    if params is None:
+        params = make_params(**kw)
+    h = ctypes.c_void_p()
+    _check(_lib.moda_anneal(inst._h, ctypes.byref(params), _stream_handle(stream),
+                            ctypes.byref(h)))
+    return Run(inst, h, params)

@@ -1,0 +1,61 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the CPU oracle on the same seeded instance and compare them element by
+element.  The comparison is bit-exact: every quantity on the path is an
+integer or an IEEE double decided identically on both sides."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def gpu_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explore",
+            escape="archive", delta0=1e9, deltaf=1e4, xi=1e-3, beta=None, archive_size=0,
+            replica_base=0, block_threads=0, trace=False, w=None, stream=None):
+    from paper_2205_13399_gb300 import moda
+    inst = moda.Instance(inst_np.F1, inst_np.F2, inst_np.D, w=w)
+    run = moda.anneal(inst, replicas=replicas, I_max=I_max, seed=seed, accept=accept,
+                      archive=archive, escape=escape, delta0=delta0, deltaf=deltaf, xi=xi,
+                      beta=beta, archive_size=archive_size, replica_base=replica_base,
+                      block_threads=block_threads, trace=trace, stream=stream)
+    run.wait()
+    res = run.read()
+    traces = None
+    if trace:
+        traces = np.stack([run.read_trace(r) for r in range(replicas)])
+    return inst, run, res, traces
+
+
+def oracle_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explore",
+               escape="archive", delta0=1e9, deltaf=1e4, xi=1e-3, beta=None, archive_size=0,
+               trace=False, w=None, threads=None):
+    oi = oracle.Instance(inst_np.F1, inst_np.F2, inst_np.D, w=w)
+    out = oracle.run(oi, I_max=I_max, replicas=replicas, seed=seed, accept=accept,
+                     archive=archive, escape=escape, delta0=delta0, deltaf=deltaf, xi=xi,
+                     beta=beta, archive_size=archive_size, trace=trace, threads=threads)
+    return oi, out
+
+
+def compare(gpu_res, gpu_rows, orc, m, gpu_trace=None):
+    """Assert that replicas ``gpu_rows`` of the GPU result equal the oracle's
+    replicas (same order), bit for bit."""
+    from paper_2205_13399_gb300.moda import unpack_bits
+    for k, g in enumerate(gpu_rows):
+        if gpu_trace is not None:
+            assert "trace" in orc
+            ot = orc["trace"][k]
+            gt = gpu_trace[g]
+            if not np.array_equal(gt, ot):
+                bad = int(np.argmax(np.any(gt != ot, axis=1)))
+                lo = max(0, bad - 3)
+                raise AssertionError(
+                    f"row {g}: trace differs first at iteration {bad + 1}:\n"
+                    f"gpu    {gt[lo:bad + 2].tolist()}\noracle {ot[lo:bad + 2].tolist()}")
+        cnt = int(gpu_res.count[g])
+        assert cnt == int(orc["count"][k]), f"archive size, replica row {g}"
+        assert np.array_equal(gpu_res.E[g, :cnt], orc["E"][k, :cnt]), f"archive energies, row {g}"
+        gb = unpack_bits(gpu_res.bits[g, :cnt], m)
+        assert np.array_equal(gb, orc["bits"][k, :cnt]), f"archive states, row {g}"
+        assert np.array_equal(unpack_bits(gpu_res.x[g], m), orc["x"][k]), f"final state, row {g}"
+        assert np.array_equal(gpu_res.E_final[g], orc["E_final"][k]), f"final energies, row {g}"
+        assert np.array_equal(gpu_res.stats[g], orc["stats"][k]), f"counters, row {g}"

@@ -1,0 +1,108 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/moda.h declares, and rejects bad arguments before
+touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "moda.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(moda_[a-z_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_13399_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_abi():
+    from paper_2205_13399_gb300 import moda
+    assert _declared_functions() == sorted(moda.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_built_for_sm103a():
+    from paper_2205_13399_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def _inst_args(n, F1=None, F2=None, D=None):
+    rng = np.random.default_rng(n)
+    if F1 is None:
+        F1 = rng.integers(0, 100, (n, n)).astype(np.int16)
+    if F2 is None:
+        F2 = rng.integers(0, 100, (n, n)).astype(np.int16)
+    if D is None:
+        D = rng.integers(1, 100, (n, n))
+        D = np.triu(D, 1)
+        D = (D + D.T).astype(np.int16)
+    return F1, F2, D
+
+
+def _create(n, F1, F2, D, pen=None):
+    from paper_2205_13399_gb300 import moda
+    return moda.Instance(F1, F2, D, w=pen)
+
+
+@pytest.mark.parametrize("case", ["n_small", "n_large", "negative", "asym", "diag", "kind"])
+def test_create_instance_rejects_bad_input(case):
+    from paper_2205_13399_gb300 import moda
+    n = 6
+    F1, F2, D = _inst_args(n)
+    pen = None
+    if case == "n_small":
+        F1, F2, D = _inst_args(1)
+    elif case == "n_large":
+        F1, F2, D = _inst_args(129)
+    elif case == "negative":
+        F1 = F1.copy()
+        F1[1, 2] = -1
+    elif case == "asym":
+        D = D.copy()
+        D[0, 1] += 1
+    elif case == "diag":
+        D = D.copy()
+        D[2, 2] = 5
+    elif case == "kind":
+        pen = (-1, 3)
+    with pytest.raises(moda.MODAError) as ei:
+        _create(n, F1, F2, D, pen)
+    assert ei.value.status == moda.EINVAL
+
+
+def test_create_instance_overflow():
+    from paper_2205_13399_gb300 import moda
+    n = 40
+    F1 = np.full((n, n), 30000, dtype=np.int16)
+    np.fill_diagonal(F1, 0)
+    D = np.full((n, n), 30000, dtype=np.int16)
+    np.fill_diagonal(D, 0)
+    with pytest.raises(moda.MODAError) as ei:
+        _create(n, F1, F1, D)
+    assert ei.value.status == moda.EOVERFLOW
+
+
+def test_null_arguments(lib):
+    lib.moda_create_instance.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    assert lib.moda_create_instance(4, None, None, None, None, ctypes.byref(out)) == 1
+    lib.moda_anneal.restype = ctypes.c_int
+    assert lib.moda_anneal(None, None, None, ctypes.byref(out)) == 1
+    lib.moda_wait.restype = ctypes.c_int
+    assert lib.moda_wait(None, ctypes.c_int64(0)) == 1
+    lib.moda_last_error.restype = ctypes.c_char_p
+    assert lib.moda_last_error()

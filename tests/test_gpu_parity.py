@@ -1,0 +1,131 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, bit for bit -- archive sizes, slot energies and states,
+final states and energies, event counters and, where traced, the (E1, E2,
+event) record of every iteration."""
+import numpy as np
+import pytest
+
+from paper_2205_13399_gb300 import inputs
+from parity import compare, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(acc, arc, esc) for acc in ("strict", "lenient")
+            for arc in ("explore", "exploit") for esc in ("archive", "offset")]
+
+# A fast schedule that reaches its floor within a few hundred iterations, so
+# short runs cover hot, cooling and frozen phases, restarts and undecided
+# acceptance tests.
+FAST = dict(delta0=2e6, deltaf=3e3, xi=0.02)
+
+
+@pytest.mark.parametrize("acc,arc,esc", VARIANTS)
+def test_variants_traced_small(acc, arc, esc):
+    """Every acceptance x archive x escape combination on ragged sizes, with
+    per-iteration traces compared."""
+    for n, bt in ((5, 0), (7, 0), (12, 32), (12, 0)):
+        inst = inputs.uniform_instance(n, index=n, workload="P8")
+        kw = dict(replicas=3, I_max=1500, seed=11 + n, accept=acc, archive=arc, escape=esc,
+                  beta=700, **FAST)
+        _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, **kw)
+        _, orc = oracle_run(inst, trace=True, **kw)
+        compare(res, range(3), orc, n * n, gpu_trace=tr)
+
+
+@pytest.mark.parametrize("n,bt", [(20, 64), (20, 0), (25, 160), (25, 320), (25, 0), (31, 0)])
+def test_block_shapes(n, bt):
+    """Several bits per thread (B = 1, 2, 4, 8) and ragged last rounds."""
+    inst = inputs.euclid_instance(n, 0.5, False, index=n, workload="P25")
+    kw = dict(replicas=4, I_max=3000, seed=3, **FAST)
+    _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, **kw)
+    _, orc = oracle_run(inst, trace=True, **kw)
+    compare(res, range(4), orc, n * n, gpu_trace=tr)
+
+
+def test_small_archive_and_replica_base():
+    """Archive capacity below m (the full-archive branches) and a replica
+    offset: rows of a shifted launch equal the oracle's replicas 5..7."""
+    inst = inputs.euclid_instance(10, -0.7, False, index=3, workload="BATCH")
+    kw = dict(I_max=4000, seed=99, archive_size=7, **FAST)
+    for arc in ("explore", "exploit"):
+        _, _, res, _ = gpu_run(inst, replicas=3, replica_base=5, archive=arc, **kw)
+        _, orc = oracle_run(inst, replicas=[5, 6, 7], archive=arc, **kw)
+        compare(res, range(3), orc, 100)
+
+
+def test_explicit_penalty():
+    inst = inputs.uniform_instance(6, index=4, workload="P8")
+    kw = dict(replicas=2, I_max=2000, seed=1, w=(5000, 4000), **FAST)
+    g_inst, _, res, _ = gpu_run(inst, **kw)
+    assert g_inst.w == (5000, 4000)
+    _, orc = oracle_run(inst, **kw)
+    compare(res, range(2), orc, 36)
+
+
+def test_penalty_matches_oracle():
+    for name in ("P8", "P25", "P50", "P75"):
+        inst = inputs.workload_instance(name)
+        from paper_2205_13399_gb300 import moda
+        import oracle
+        if inst.n <= 25:
+            assert moda.Instance(inst.F1, inst.F2, inst.D).w == \
+                oracle.Instance(inst.F1, inst.F2, inst.D).w
+
+
+def test_p8_full_config():
+    """n = 8 workload at its full size: 16 replicas, I_max = 10^4, the paper's
+    schedule (delta0 = 1e9, deltaf = 1e4, xi = 1e-3)."""
+    inst = inputs.workload_instance("P8")
+    run = inputs.WORKLOAD_RUN["P8"]
+    _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=run["I_max"], seed=run["seed"])
+    _, orc = oracle_run(inst, replicas=range(run["replicas"]), I_max=run["I_max"],
+                        seed=run["seed"])
+    compare(res, range(run["replicas"]), orc, 64)
+
+
+def test_p25_full_config_sampled_replicas():
+    """n = 25 workload at full size (128 replicas, I_max = 10^5) in the launch
+    shape the benchmark times; the oracle recomputes sampled replicas."""
+    inst = inputs.workload_instance("P25")
+    run = inputs.WORKLOAD_RUN["P25"]
+    _, grun, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=run["I_max"],
+                              seed=run["seed"])
+    rows = [0, 77, 127]
+    _, orc = oracle_run(inst, replicas=rows, I_max=run["I_max"], seed=run["seed"])
+    compare(res, rows, orc, 625)
+    # properties of every replica: archive energies recomputed from the states
+    import oracle as orc_mod
+    from paper_2205_13399_gb300.moda import unpack_bits
+    oi = orc_mod.Instance(inst.F1, inst.F2, inst.D)
+    for r in range(0, run["replicas"], 9):
+        cnt = int(res.count[r])
+        assert 0 < cnt <= 625
+        bits = unpack_bits(res.bits[r, :cnt], 625)
+        for slot in range(0, cnt, max(1, cnt // 5)):
+            assert res.E[r, slot, 0] == oi.energy(0, bits[slot])
+            assert res.E[r, slot, 1] == oi.energy(1, bits[slot])
+        assert res.stats[r].sum() == run["I_max"]
+    # the merged front is mutually non-dominated and its costs decode
+    front = grun.read_archive(-1)
+    assert front
+    for a in front:
+        for b in front:
+            assert not (a["E1"] <= b["E1"] and a["E2"] <= b["E2"] and
+                        (a["E1"], a["E2"]) != (b["E1"], b["E2"]))
+        if a["feasible"]:
+            assert a["c1"] == orc_mod.qap_cost(inst.F1, inst.D, a["perm"])
+            assert a["c2"] == orc_mod.qap_cost(inst.F2, inst.D, a["perm"])
+
+
+@pytest.mark.parametrize("name", ["P50", "P75"])
+def test_large_configs_prefix(name):
+    """n = 50 / 75 workloads in their full launch shape (256 replicas); the
+    schedule does not depend on I_max, so a shorter run is an exact prefix of
+    the full one and the oracle recomputes two sampled replicas of it."""
+    inst = inputs.workload_instance(name)
+    run = inputs.WORKLOAD_RUN[name]
+    I_max = 20000
+    _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=I_max, seed=run["seed"])
+    rows = [1, run["replicas"] - 1]
+    _, orc = oracle_run(inst, replicas=rows, I_max=I_max, seed=run["seed"])
+    compare(res, rows, orc, inst.n * inst.n)

@@ -300,20 +300,21 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   if ((uint64_t)p->replica_base + (uint64_t)p->replicas > 0x100000000ull)
     return fail(MODA_EINVAL, "replica indices must fit 32 bits");
 
-  // Block shape: B bits per thread, T threads, B * T >= m.
+  // Block shape: B rounds of T threads own the bits, B * T >= m.
+  static const int kRounds[] = {1, 2, 3, 4, 6, 8};
   int T = 0, B = 0;
   if (p->block_threads > 0) {
     if (p->block_threads % 32 || p->block_threads > moda::kMaxThreads)
       return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 1024");
     T = p->block_threads;
-    for (int b : {1, 2, 4, 8})
+    for (int b : kRounds)
       if ((int64_t)b * T >= m) {
         B = b;
         break;
       }
     if (!B) return fail(MODA_EUNSUPPORTED, "block_threads too small for n");
   } else {
-    for (int b : {1, 2, 4, 8})
+    for (int b : kRounds)
       if ((int64_t)b * moda::kMaxThreads >= m) {
         B = b;
         break;
@@ -321,14 +322,33 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     if (!B) return fail(MODA_EUNSUPPORTED, "n too large for this build");
     T = ((m + B - 1) / B + 31) / 32 * 32;
   }
-  const moda::SmemLayout lay = moda::smem_layout(inst->n, m, T, B);
+  const int s_cap = p->archive_size > 0 ? p->archive_size : m;
   int dev_smem = 0;
   cudaSetDevice(inst->device);
   MODA_CUDA(cudaDeviceGetAttribute(&dev_smem,
                                    cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                    inst->device));
+  // Archive energies, then archive states, move into shared memory when
+  // they fit; otherwise they stay in the run's device buffers.
+  bool e_smem = false, b_smem = false;
+  moda::SmemLayout lay =
+      moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, false, false);
   if ((int64_t)lay.total > dev_smem)
     return fail(MODA_EUNSUPPORTED, "shared memory need exceeds the device limit");
+  {
+    moda::SmemLayout l2 =
+        moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, true, false);
+    if ((int64_t)l2.total <= dev_smem) {
+      e_smem = true;
+      lay = l2;
+      moda::SmemLayout l3 =
+          moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, true, true);
+      if ((int64_t)l3.total <= dev_smem) {
+        b_smem = true;
+        lay = l3;
+      }
+    }
+  }
 
   moda_run r = new (std::nothrow) moda_run_s;
   if (!r) return fail(MODA_ENOMEM, "host allocation");
@@ -392,6 +412,9 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   a.accept = p->accept;
   a.archive = p->archive;
   a.escape = p->escape;
+  a.magic = (uint32_t)(0xFFFFFFFFu / (uint32_t)inst->n) + 1u;
+  a.energies_in_smem = e_smem;
+  a.bits_in_smem = b_smem;
   a.nsched = sch.count;
   a.sch_delta = sch.delta;
   a.sch_lo = sch.lo;
@@ -413,7 +436,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->error, 0, sizeof(int32_t), r->stream);
   if (e == cudaSuccess) e = cudaEventRecord(r->start, r->stream);
-  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, r->stream);
+  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, lay.total, r->stream);
   if (e == cudaSuccess) e = cudaEventRecord(r->stop, r->stream);
   if (e != cudaSuccess) {
     free_run_buffers(r);

@@ -25,11 +25,14 @@ struct AnnealArgs {
   int64_t I_max;
   uint32_t replica_base;
   uint32_t seed_lo, seed_hi;
+  uint32_t magic;           // ceil(2^32 / n): q / n = umulhi(q, magic), q < 2^14
   int64_t w1, w2;           // penalty weights, alpha_k = w_k / 2
   int64_t beta;
   int32_t accept, archive, escape;
   int32_t nsched;           // entries of the schedule; later iterations
                             // reuse the last one
+  int32_t energies_in_smem; // archive energies kept in shared memory
+  int32_t bits_in_smem;     // archive states kept in shared memory
   const double *sch_delta;  // [nsched] delta_t, t = 1..nsched
   const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
   const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
@@ -49,41 +52,42 @@ struct AnnealArgs {
 
 // Byte offsets of the shared-memory carve-up of one annealing block.
 struct SmemLayout {
-  size_t Fs1, Fs2, D, L1, L2, R, C, mask, amask, ones, X, red, bcast, total;
+  size_t Fs, D, M, dE, mask, xmask, amask, rnd, RC, red, archE, archB, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) {
   return (v + a - 1) / a * a;
 }
 
-__host__ __device__ inline SmemLayout smem_layout(int n, int m, int threads,
-                                                  int bits_per_thread) {
+__host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
+                                                  int threads, int rounds,
+                                                  bool energies_in_smem,
+                                                  bool bits_in_smem) {
   SmemLayout L;
   size_t o = 0;
   const size_t nn = (size_t)n * n;
-  const int nw = threads / 32;
-  L.Fs1 = o;   o = align_up(o + 4 * nn, 16);
-  L.Fs2 = o;   o = align_up(o + 4 * nn, 16);
+  const size_t items = (size_t)rounds * (threads / 32);
+  L.Fs = o;    o = align_up(o + 8 * nn, 16);                 // int2 pairs
   L.D = o;     o = align_up(o + 4 * nn, 16);
-  L.L1 = o;    o = align_up(o + 4 * (size_t)m, 16);
-  L.L2 = o;    o = align_up(o + 4 * (size_t)m, 16);
-  L.R = o;     o = align_up(o + 4 * (size_t)n, 16);
-  L.C = o;     o = align_up(o + 4 * (size_t)n, 16);
-  L.mask = o;  o = align_up(o + 4 * (size_t)bits_per_thread * nw, 16);
-  L.amask = o; o = align_up(o + 4 * (size_t)bits_per_thread * nw, 16);
-  L.ones = o;  o = align_up(o + 2 * (size_t)m, 16);
-  L.X = o;     o = align_up(o + (size_t)m, 16);
-  L.red = o;   o = align_up(o + 8 * (size_t)32, 16);
-  L.bcast = o; o = align_up(o + 128, 16);
+  L.M = o;     o = align_up(o + 4 * nn, 16);                 // X * D
+  L.dE = o;    o = align_up(o + 16 * (size_t)rounds * threads, 16);
+  L.mask = o;  o = align_up(o + 2 * 4 * items, 16);          // two buffers
+  L.xmask = o; o = align_up(o + 2 * 4 * items, 16);
+  L.amask = o; o = align_up(o + 4 * items, 16);
+  L.rnd = o;   o = align_up(o + 2 * 4 * 4, 16);
+  L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);  // 2 x (R, C)
+  L.red = o;   o = align_up(o + 8 * 32, 16);
+  L.archE = o; if (energies_in_smem) o = align_up(o + 16 * (size_t)s, 16);
+  L.archB = o; if (bits_in_smem) o = align_up(o + 4 * (size_t)s * W, 16);
   L.total = o;
   return L;
 }
 
+// Bits per thread the kernel is instantiated for.
+bool supported_rounds(int b);
+
 // Launch one block per replica on `stream`.  Returns the launch error.
 cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,
-                          int bits_per_thread, cudaStream_t stream);
-
-// Bits per thread the kernel is instantiated for.
-bool supported_bits_per_thread(int b);
+                          int rounds, size_t smem_bytes, cudaStream_t stream);
 
 }  // namespace moda

@@ -2,26 +2,37 @@
 // Alg. 3 of arXiv 2205.13399, for the bi-objective QAP: one thread block
 // runs one replica for all I_max iterations, its state held on chip.
 //
-// State of a replica (shared memory):
-//   X[p]        the n*n-bit two-way one-hot state, bit p = i*n + u
-//               (facility i at location u, Sec. 2.2);
-//   R[i], C[u]  row and column counts of X;
-//   L1[p], L2[p] cost-only local fields
-//               L_k[(i,u)] = sum_{(j,v)} Fs^k_ij d_uv x_jv,  Fs^k = F^k + F^k^T.
+// State of a replica.  Thread `tid` of a T-thread block owns the bits
+// p = k*T + tid, k < B ("rounds"), of the n*n-bit two-way one-hot state
+// (bit p = i*n + u: facility i at location u, Sec. 2.2) and keeps in
+// registers, per owned bit:
+//   x_p                 (a bit of `xmask`),
+//   rc_p = R_i + C_u    (row count of facility i plus column count of u),
+//   L1_p, L2_p          cost-only local fields
+//                       L_k[(i,u)] = sum_{(j,v)} Fs^k_ij d_uv x_jv,
+//                       Fs^k = F^k + F^k^T.
 // With zero-diagonal symmetric distances, P^k_(i,u),(j,v) = Fs^k_ij d_uv is
 // the off-diagonal of Eq. cale's P for the cost QUBO and its diagonal is 0,
-// so the cost part of Delta E_k at bit p is (1 - 2 x_p) L_k[p].  The
-// penalty part follows from the counts: flipping (i,u) changes g by
-//   2 (1 - 2 x)(R_i + C_u - 1 - 2 x)          (Eq. gqap),
-// so Delta E_k = (1 - 2x) L_k + w_k (1 - 2x)(R_i + C_u - 1 - 2x) with
-// alpha_k = w_k / 2 (Eq. wqubom).  Q is never stored: a flip of (j,v)
-// updates every field by s * Fs^k_ij * d_uv (the outer product of a flow
-// column and a distance column), s = +1 when the bit turns on.
+// so the cost part of Delta E_k at bit p is (1 - 2 x_p) L_k[p].  Flipping
+// bit (i,u) changes g (Eq. gqap) by 2 (1 - 2x)(rc - 1 - 2x), hence
+//   Delta E_k = (1 - 2x) L_k + w_k (1 - 2x)(rc - 1 - 2x),  alpha_k = w_k/2
+// (Eq. wqubom).  Q is never stored: a flip of (j,v) changes every field by
+// s * Fs^k_ij * d_uv -- the outer product of a flow column and a distance
+// column, s = +1 when the bit turns on.
 //
-// Bit ownership is round-robin: thread `tid` owns bits p = k*T + tid,
-// k < B, so a warp ballot per k yields accept masks whose (k, warp, lane)
-// order is ascending bit order -- the order in which "one flip at random"
-// (Alg. 3) is ranked.
+// One iteration (Alg. 3):
+//   A  every thread: Delta E and the parallel trial of its bits; accepted
+//      bits publish (dE1, dE2); warp ballots give accept and state masks in
+//      (round, warp, lane) order = ascending bit order.  One warp draws the
+//      iteration's select / restart / exploit words meanwhile.
+//   -- barrier --
+//   B  every warp, redundantly: count, rank-select one accepted bit, read
+//      its Delta E; every thread applies the flip to its own registers.
+//      Flip:    archive dominance ballots -- barrier -- every warp picks the
+//               target slot (Alg. 4 / Alg. 5) and writes its words of x.
+//      No flip: jump to a random archive member: every thread rebuilds its
+//               own fields and counts from that member's set bits (no
+//               barrier), or raise the offset by beta.
 #include <cstdint>
 
 #include "moda_internal.h"
@@ -66,25 +77,14 @@ __device__ __forceinline__ int nth_set_bit(uint32_t mask, int r) {
   return __ffs(mask) - 1;
 }
 
-struct Bcast {
-  int32_t count;   // accepted bits this iteration
-  int32_t p;       // the flipped bit
-  int32_t sgn;     // +1: the bit turned on, -1: off
-  int32_t slot;    // restart slot, or archive target (-1: none)
-  int32_t acount;  // archive size after the update
-  int32_t nones;   // set bits collected by a rebuild
-  int32_t pad0, pad1;
-  int64_t E1, E2;  // energies after the flip
-};
-
 __device__ __forceinline__ bool dominates(int64_t a1, int64_t a2, int64_t b1,
                                           int64_t b2) {
   return a1 <= b1 && a2 <= b2 && !(a1 == b1 && a2 == b2);
 }
 
-// Warp-0 helper: over `items` ballot masks in (k, warp) order, the total
-// number of set bits and, for rank r (r < total, uniform), the flat index
-// k*T + warp*32 + lane of the r-th set bit (valid in every lane).
+// Over `items` ballot masks in (round, warp) order: each lane sums a
+// contiguous chunk; returns the total (all lanes) and the lane's inclusive
+// prefix and own count.
 __device__ __forceinline__ int warp_mask_total(const uint32_t *masks,
                                                int items, int lane, int &incl,
                                                int &cnt) {
@@ -103,6 +103,8 @@ __device__ __forceinline__ int warp_mask_total(const uint32_t *masks,
   return __shfl_sync(kFull, incl, 31);
 }
 
+// Flat index round*T + warp*32 + lane of the r-th set bit (r < total), in
+// every lane.
 __device__ __forceinline__ int warp_mask_select(const uint32_t *masks,
                                                 int items, int nw, int T,
                                                 int lane, int incl, int cnt,
@@ -146,114 +148,148 @@ template <int B>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = A.n, m = A.m, W = A.W;
+  const int n = A.n, m = A.m, W = A.W, s = A.s;
   const int T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, NW = T >> 5;
-  const SmemLayout lay = smem_layout(n, m, T, B);
-  int32_t *sFs1 = reinterpret_cast<int32_t *>(smem + lay.Fs1);
-  int32_t *sFs2 = reinterpret_cast<int32_t *>(smem + lay.Fs2);
+  const int items = B * NW;
+  const SmemLayout lay = smem_layout(n, m, W, s, T, B, A.energies_in_smem != 0,
+                                     A.bits_in_smem != 0);
+  int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
   int32_t *sD = reinterpret_cast<int32_t *>(smem + lay.D);
-  int32_t *sL1 = reinterpret_cast<int32_t *>(smem + lay.L1);
-  int32_t *sL2 = reinterpret_cast<int32_t *>(smem + lay.L2);
-  int32_t *sR = reinterpret_cast<int32_t *>(smem + lay.R);
-  int32_t *sC = reinterpret_cast<int32_t *>(smem + lay.C);
+  longlong2 *sDE = reinterpret_cast<longlong2 *>(smem + lay.dE);
   uint32_t *sMask = reinterpret_cast<uint32_t *>(smem + lay.mask);
+  uint32_t *sXm = reinterpret_cast<uint32_t *>(smem + lay.xmask);
   uint32_t *sAmask = reinterpret_cast<uint32_t *>(smem + lay.amask);
-  uint16_t *sOnes = reinterpret_cast<uint16_t *>(smem + lay.ones);
-  uint8_t *sX = reinterpret_cast<uint8_t *>(smem + lay.X);
+  uint32_t *sRnd = reinterpret_cast<uint32_t *>(smem + lay.rnd);
+  // Row and column counts of the last rebuilt state, two buffers used in
+  // turn (rebuild q fills buffer q % 2 and clears the other one).
+  int32_t *sRC = reinterpret_cast<int32_t *>(smem + lay.RC);
+  int rc_buf = 0;
   int64_t *sRed = reinterpret_cast<int64_t *>(smem + lay.red);
-  Bcast *bc = reinterpret_cast<Bcast *>(smem + lay.bcast);
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
   const uint32_t k0 = A.seed_lo, k1 = A.seed_hi;
-  const int s = A.s;
-  int64_t *aE = A.arch_E + (size_t)rb * s * 2;
-  uint32_t *aBits = A.arch_bits + (size_t)rb * s * W;
-  const int items = B * NW;
+  int64_t *gE = A.arch_E + (size_t)rb * s * 2;
+  uint32_t *gBits = A.arch_bits + (size_t)rb * s * W;
+  longlong2 *aE = A.energies_in_smem
+                      ? reinterpret_cast<longlong2 *>(smem + lay.archE)
+                      : reinterpret_cast<longlong2 *>(gE);
+  uint32_t *aBits = A.bits_in_smem
+                        ? reinterpret_cast<uint32_t *>(smem + lay.archB)
+                        : gBits;
 
   for (int e = tid; e < n * n; e += T) {
-    sFs1[e] = A.Fs1[e];
-    sFs2[e] = A.Fs2[e];
+    sFs[e] = make_int2(A.Fs1[e], A.Fs2[e]);
     sD[e] = A.D[e];
   }
-  // Own bits: facility i and location u packed as (i << 8) | u, -1 if p >= m.
+  for (int e = tid; e < 4 * n; e += T) sRC[e] = 0;
+
+  // Own bit k (valid when k*T + tid < m): own[k] packs facility i (bits
+  // 8..15), location u (bits 0..7) and rc = R_i + C_u (bits 16..31).
   int own[B];
+  int32_t L1[B], L2[B];
+  uint32_t xmask = 0;
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const int p = k * T + tid;
-    own[k] = p < m ? (((p / n) << 8) | (p % n)) : -1;
+    own[k] = p < m ? (((p / n) << 8) | (p % n)) : 0;
+    L1[k] = 0;
+    L2[k] = 0;
   }
   // Initial state (Alg. 3: "a random binary solution"): bit p is bit p % 32
   // of word (p / 32) % 4 of the draw (p / 128, 0, replica, init).
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    if (own[k] < 0) continue;
+    if (k * T + tid >= m) continue;
     const int p = k * T + tid;
     uint32_t c[4] = {(uint32_t)p >> 7, 0u, rep, kTagInit};
     philox10(c, k0, k1);
-    sX[p] = (uint8_t)((word_of(c, (p >> 5) & 3) >> (p & 31)) & 1u);
+    xmask |= ((word_of(c, (p >> 5) & 3) >> (p & 31)) & 1u) << k;
   }
-  for (int e = tid; e < n; e += T) {
-    sR[e] = 0;
-    sC[e] = 0;
+  // State words of the initial x, in shared memory for the rebuild below
+  // (the accept-mask buffer is free until the first iteration).
+  uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.dE);
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+    if (lane == 0 && k * NW + warp < W) sInit[k * NW + warp] = wv;
   }
-  if (tid == 0) bc->nones = 0;
   __syncthreads();
 
-  // Counts, the list of set bits and the fields from scratch.
-  auto collect = [&]() {
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (own[k] < 0) continue;
-      const int p = k * T + tid;
-      if (sX[p]) {
-        atomicAdd(&sR[own[k] >> 8], 1);
-        atomicAdd(&sC[own[k] & 255], 1);
-        const int pos = atomicAdd(&bc->nones, 1);
-        sOnes[pos] = (uint16_t)own[k];
+  // Fields, counts and owned bits of the state held in `words`, in two
+  // passes around one barrier: (1) M = X * D (M_ju = sum_v x_jv d_vu) and
+  // the row / column counts into shared memory; (2) every thread forms
+  // L_k[(i,u)] = sum_j Fs^k_ij M_ju for its own bits.  Both passes are
+  // exact int32 arithmetic (the instance check bounds every field).
+  int32_t *sM = reinterpret_cast<int32_t *>(smem + lay.M);
+  auto rebuild = [&](const uint32_t *words) {
+    for (int e = tid; e < n * n; e += T) {
+      const int j = (int)__umulhi((uint32_t)e, A.magic);
+      const int u = e - j * n;
+      const int lo_bit = j * n, hi_bit = j * n + n;  // row j: [lo_bit, hi_bit)
+      int32_t acc = 0;
+      for (int w = lo_bit >> 5; w <= (hi_bit - 1) >> 5; ++w) {
+        uint32_t word = words[w];
+        const int base = w * 32;
+        if (base < lo_bit) word &= ~0u << (lo_bit - base);
+        if (base + 32 > hi_bit) word &= ~0u >> (base + 32 - hi_bit);
+        while (word) {
+          const int v = base + __ffs(word) - 1 - lo_bit;
+          word &= word - 1;
+          acc += sD[v * n + u];
+        }
+      }
+      sM[e] = acc;
+      if ((words[e >> 5] >> (e & 31)) & 1u) {  // bit e = (j, u) is set
+        atomicAdd(&sRC[rc_buf * 2 * n + j], 1);
+        atomicAdd(&sRC[rc_buf * 2 * n + n + u], 1);
       }
     }
-  };
-  auto rebuild_fields = [&]() {
-    const int no = bc->nones;
+    xmask = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      if (own[k] < 0) continue;
-      const int p = k * T + tid;
-      const int i = own[k] >> 8, u = own[k] & 255;
-      int32_t acc1 = 0, acc2 = 0;
-      for (int q = 0; q < no; ++q) {
-        const int jv = sOnes[q];
-        const int j = jv >> 8, v = jv & 255;
-        const int32_t d = sD[v * n + u];
-        acc1 += sFs1[j * n + i] * d;
-        acc2 += sFs2[j * n + i] * d;
-      }
-      sL1[p] = acc1;
-      sL2[p] = acc2;
+      if (k * T + tid >= m) continue;
+      const int q = k * T + tid;
+      xmask |= ((words[q >> 5] >> (q & 31)) & 1u) << k;
     }
+    __syncthreads();
+    const int32_t *cR = sRC + rc_buf * 2 * n, *cC = cR + n;
+    for (int e = tid; e < 2 * n; e += T) sRC[(1 - rc_buf) * 2 * n + e] = 0;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (k * T + tid >= m) continue;
+      const int i = (own[k] >> 8) & 255, u = own[k] & 255;
+      int32_t a1 = 0, a2 = 0;
+      const int2 *frow = sFs + i * n;  // Fs symmetric: row i = column i
+#pragma unroll 5
+      for (int j = 0; j < n; ++j) {
+        const int2 f = frow[j];
+        const int32_t mm = sM[j * n + u];
+        a1 += f.x * mm;
+        a2 += f.y * mm;
+      }
+      L1[k] = a1;
+      L2[k] = a2;
+      own[k] = ((cR[i] + cC[u]) << 16) | (i << 8) | u;
+    }
+    rc_buf ^= 1;
   };
-  collect();
-  __syncthreads();
-  rebuild_fields();
-  __syncthreads();
+  rebuild(sInit);
 
-  // E_k = c_k + w_k g / 2 with c_k = (sum_p x_p L_k[p]) / 2.
+  // E_k = c_k + w_k g / 2 with c_k = (sum_p x_p L_k[p]) / 2 and g from the
+  // row and column counts.
   int64_t E1, E2;
   {
     int64_t s1 = 0, s2 = 0, gp = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      if (own[k] < 0) continue;
-      const int p = k * T + tid;
-      if (sX[p]) {
-        s1 += sL1[p];
-        s2 += sL2[p];
-      }
+      if (k * T + tid >= m || !((xmask >> k) & 1u)) continue;
+      s1 += L1[k];
+      s2 += L2[k];
     }
     for (int e = tid; e < n; e += T) {
-      const int64_t dr = 1 - sR[e], dc = 1 - sC[e];
+      const int64_t dr = 1 - sRC[e], dc = 1 - sRC[n + e];
       gp += dr * dr + dc * dc;
     }
     s1 = block_sum(s1, sRed, lane, warp, NW);
@@ -266,9 +302,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int64_t Eoff = 0;
   int acount = 0;
   int64_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
+  const int rng_warp = NW - 1;
 
   for (int64_t it = 1; it <= A.I_max; ++it) {
     const uint32_t t = (uint32_t)it;
+    const int buf = (int)(t & 1u);
+    uint32_t *mask = sMask + buf * items;
+    uint32_t *xm = sXm + buf * items;
+    uint32_t *rnd = sRnd + buf * 4;
     const int si = (int)((it <= A.nsched ? it : (int64_t)A.nsched) - 1);
     const double delta = A.sch_delta[si];
     const int64_t lo = A.sch_lo[si], hi = A.sch_hi[si];
@@ -277,18 +318,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       bool acc = false;
-      if (own[k] >= 0) {
+      const uint32_t xv = (xmask >> k) & 1u;
+      if (k * T + tid < m) {
         const int p = k * T + tid;
-        const int xv = sX[p];
-        const int sg = 1 - 2 * xv;
-        const int h = sg * (sR[own[k] >> 8] + sC[own[k] & 255] - 1 - 2 * xv);
-        int64_t e1 = (int64_t)(sg * sL1[p]) + A.w1 * h;
-        int64_t e2 = (int64_t)(sg * sL2[p]) + A.w2 * h;
+        const int sg = 1 - 2 * (int)xv;
+        const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
+        int64_t e1 = (int64_t)(sg * L1[k]) + A.w1 * h;
+        int64_t e2 = (int64_t)(sg * L2[k]) + A.w2 * h;
+        int64_t f1 = e1, f2 = e2;
         if (A.escape == 1) {
-          e1 -= Eoff;
-          e2 -= Eoff;
+          f1 -= Eoff;
+          f2 -= Eoff;
         }
-        const int64_t a1 = e1 > 0 ? e1 : 0, a2 = e2 > 0 ? e2 : 0;
+        const int64_t a1 = f1 > 0 ? f1 : 0, a2 = f2 > 0 ? f2 : 0;
         const int64_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
         if (a <= lo) {
           acc = true;
@@ -298,142 +340,104 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           const uint32_t w = word_of(c, p & 3);
           acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
         }
+        if (acc) sDE[p] = make_longlong2(e1, e2);
       }
       const uint32_t bal = __ballot_sync(kFull, acc);
-      if (lane == 0) sMask[k * NW + warp] = bal;
-    }
-    __syncthreads();
-
-    // Phase B (warp 0): count, pick one accepted bit, apply it to X, R, C.
-    if (warp == 0) {
-      int incl, cnt;
-      const int total = warp_mask_total(sMask, items, lane, incl, cnt);
-      if (lane == 0) bc->count = total;
-      if (total > 0) {
-        uint32_t c[4] = {0u, t, rep, kTagSelect};
-        philox10(c, k0, k1);
-        const int r = pick(c[0], total);
-        const int p = warp_mask_select(sMask, items, NW, T, lane, incl, cnt, r);
-        if (lane == 0) {
-          const int i = p / n, u = p - (p / n) * n;
-          const int xv = sX[p];
-          const int sg = 1 - 2 * xv;
-          const int h = sg * (sR[i] + sC[u] - 1 - 2 * xv);
-          bc->p = p;
-          bc->sgn = sg;
-          bc->E1 = E1 + (int64_t)(sg * sL1[p]) + A.w1 * h;
-          bc->E2 = E2 + (int64_t)(sg * sL2[p]) + A.w2 * h;
-          sX[p] = (uint8_t)(1 - xv);
-          sR[i] += sg;
-          sC[u] += sg;
-        }
-      } else if (A.escape == 0 && acount > 0) {
-        uint32_t c[4] = {0u, t, rep, kTagRestart};
-        philox10(c, k0, k1);
-        if (lane == 0) {
-          bc->slot = pick(c[0], acount);
-          bc->nones = 0;
-        }
-        for (int e = lane; e < n; e += 32) {
-          sR[e] = 0;
-          sC[e] = 0;
-        }
+      const uint32_t xb = __ballot_sync(kFull, xv != 0);
+      if (lane == 0) {
+        mask[k * NW + warp] = bal;
+        xm[k * NW + warp] = xb;
       }
     }
+    if (warp == rng_warp && lane < 3) {
+      uint32_t c[4] = {0u, t, rep, kTagSelect + (uint32_t)lane};
+      philox10(c, k0, k1);
+      rnd[lane] = c[0];
+    }
     __syncthreads();
 
+    // Phase B: every warp reaches the same decision from shared memory.
+    int incl, cnt;
+    const int total = warp_mask_total(mask, items, lane, incl, cnt);
     int64_t event = INT64_MIN;
-    const int count = bc->count;
-    if (count > 0) {
-      const int p = bc->p, sg = bc->sgn;
-      const int64_t nE1 = bc->E1, nE2 = bc->E2;
-      const int j = p / n, v = p - (p / n) * n;
-      // Outer-product field update for the flip of (j, v).
+    if (total > 0) {
+      const int ps = warp_mask_select(mask, items, NW, T, lane, incl, cnt,
+                                      pick(rnd[0], total));
+      const longlong2 de = sDE[ps];
+      const int kk = ps / T;
+      const int rr = ps - kk * T;
+      const int xs = (int)((xm[kk * NW + (rr >> 5)] >> (rr & 31)) & 1u);
+      const int sg = 1 - 2 * xs;
+      const int j = (int)__umulhi((uint32_t)ps, A.magic);
+      const int v = ps - j * n;
+      const int64_t nE1 = E1 + de.x, nE2 = E2 + de.y;
+      // Apply the flip of (j, v) to the owned registers.
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        if (own[k] < 0) continue;
-        const int q = k * T + tid;
-        const int32_t d = sg * sD[v * n + (own[k] & 255)];
-        sL1[q] += sFs1[j * n + (own[k] >> 8)] * d;
-        sL2[q] += sFs2[j * n + (own[k] >> 8)] * d;
+        if (k * T + tid >= m) continue;
+        const int i = (own[k] >> 8) & 255, u = own[k] & 255;
+        const int2 f = sFs[j * n + i];
+        const int32_t d = sg * sD[v * n + u];
+        L1[k] += f.x * d;
+        L2[k] += f.y * d;
+        own[k] += (sg * ((i == j) + (u == v))) * 65536;
+        if (k * T + tid == ps) xmask ^= 1u << k;
       }
-      // Archive: ballots of "x dominates slot y" in slot order; for the
-      // exploitative update also whether some member dominates x.
+      // Archive: ballots of "x dominates slot y" in slot order, and (for
+      // the exploitative update) whether some member dominates x.
       int anyd = 0;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const int y = k * T + tid;
         bool dom = false;
         if (y < acount) {
-          const int64_t y1 = aE[2 * y], y2 = aE[2 * y + 1];
-          dom = dominates(nE1, nE2, y1, y2);
-          if (dominates(y1, y2, nE1, nE2)) anyd = 1;
+          const longlong2 ye = aE[y];
+          dom = dominates(nE1, nE2, ye.x, ye.y);
+          if (dominates(ye.x, ye.y, nE1, nE2)) anyd = 1;
         }
         const uint32_t bal = __ballot_sync(kFull, dom);
         if (lane == 0) sAmask[k * NW + warp] = bal;
       }
       anyd = __syncthreads_or(anyd);
-      if (warp == 0) {
-        int incl, cnt;
-        const int nb = warp_mask_total(sAmask, items, lane, incl, cnt);
-        int target = -1, newcount = acount;
-        if (A.archive == 0) {
-          // Alg. 4: replace the first dominated member, else append.
-          if (nb > 0)
-            target = warp_mask_select(sAmask, items, NW, T, lane, incl, cnt, 0);
-          else if (acount < s)
-            target = newcount++;
-        } else if (!anyd) {
-          // Alg. 5: replace a random dominated member, else append.
-          if (nb > 0) {
-            uint32_t c[4] = {0u, t, rep, kTagExploit};
-            philox10(c, k0, k1);
-            target = warp_mask_select(sAmask, items, NW, T, lane, incl, cnt,
-                                      pick(c[0], nb));
-          } else if (acount < s) {
-            target = newcount++;
-          }
-        }
-        if (lane == 0) {
-          bc->slot = target;
-          bc->acount = newcount;
-        }
+      int aincl, acnt;
+      const int nb = warp_mask_total(sAmask, items, lane, aincl, acnt);
+      int target = -1;
+      if (A.archive == 0) {
+        // Alg. 4: replace the first dominated member, else append.
+        if (nb > 0)
+          target = warp_mask_select(sAmask, items, NW, T, lane, aincl, acnt, 0);
+        else if (acount < s)
+          target = acount++;
+      } else if (!anyd) {
+        // Alg. 5: replace a random dominated member, else append.
+        if (nb > 0)
+          target = warp_mask_select(sAmask, items, NW, T, lane, aincl, acnt,
+                                    pick(rnd[2], nb));
+        else if (acount < s)
+          target = acount++;
       }
-      __syncthreads();
-      const int target = bc->slot;
-      acount = bc->acount;
       if (target >= 0) {
-        for (int w = warp; w < W; w += NW) {
-          const int q = w * 32 + lane;
-          const uint32_t word = __ballot_sync(kFull, q < m && sX[q] != 0);
-          if (lane == 0) aBits[(size_t)target * W + w] = word;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+          const int wi = k * NW + warp;
+          if (lane == 0 && wi < W) aBits[(size_t)target * W + wi] = wv;
         }
-        if (tid == 0) {
-          aE[2 * target] = nE1;
-          aE[2 * target + 1] = nE2;
-        }
+        if (tid == 0) aE[target] = make_longlong2(nE1, nE2);
       }
       E1 = nE1;
       E2 = nE2;
       Eoff = 0;
       ++st_flip;
-      event = p;
+      event = ps;
     } else if (A.escape == 0) {
       if (acount > 0) {
-        // Alg. 3: jump to a random archive member; rebuild its fields.
-        const int slot = bc->slot;
-        E1 = aE[2 * slot];
-        E2 = aE[2 * slot + 1];
-        const uint32_t *src = aBits + (size_t)slot * W;
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-          if (own[k] < 0) continue;
-          const int q = k * T + tid;
-          sX[q] = (uint8_t)((src[q >> 5] >> (q & 31)) & 1u);
-        }
-        collect();
-        __syncthreads();
-        rebuild_fields();
+        // Alg. 3: jump to a random archive member.
+        const int slot = pick(rnd[1], acount);
+        const longlong2 se = aE[slot];
+        E1 = se.x;
+        E2 = se.y;
+        rebuild(aBits + (size_t)slot * W);
         ++st_jump;
         event = -1 - (int64_t)slot;
       } else {
@@ -452,10 +456,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 
   __syncthreads();
-  for (int w = warp; w < W; w += NW) {
-    const int q = w * 32 + lane;
-    const uint32_t word = __ballot_sync(kFull, q < m && sX[q] != 0);
-    if (lane == 0) A.x_final[(size_t)rb * W + w] = word;
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+    const int wi = k * NW + warp;
+    if (lane == 0 && wi < W) A.x_final[(size_t)rb * W + wi] = wv;
+  }
+  if (A.energies_in_smem) {
+    for (int e = tid; e < acount; e += T) {
+      const longlong2 v = aE[e];
+      gE[2 * e] = v.x;
+      gE[2 * e + 1] = v.y;
+    }
+  }
+  if (A.bits_in_smem) {
+    for (int e = tid; e < acount * W; e += T) gBits[e] = aBits[e];
   }
   if (tid == 0) {
     A.arch_count[rb] = acount;
@@ -470,29 +485,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
 template <int B>
 cudaError_t launch_b(const AnnealArgs &args, int replicas, int threads,
-                     cudaStream_t stream) {
-  const SmemLayout lay = smem_layout(args.n, args.m, threads, B);
-  cudaError_t e = cudaFuncSetAttribute(anneal_kernel<B>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lay.total);
+                     size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(
+      anneal_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  anneal_kernel<B><<<replicas, threads, lay.total, stream>>>(args);
+  anneal_kernel<B><<<replicas, threads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool supported_bits_per_thread(int b) {
-  return b == 1 || b == 2 || b == 4 || b == 8;
+bool supported_rounds(int b) {
+  return b == 1 || b == 2 || b == 3 || b == 4 || b == 6 || b == 8;
 }
 
 cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,
-                          int bits_per_thread, cudaStream_t stream) {
-  switch (bits_per_thread) {
-    case 1: return launch_b<1>(args, replicas, threads, stream);
-    case 2: return launch_b<2>(args, replicas, threads, stream);
-    case 4: return launch_b<4>(args, replicas, threads, stream);
-    case 8: return launch_b<8>(args, replicas, threads, stream);
+                          int rounds, size_t smem, cudaStream_t stream) {
+  switch (rounds) {
+    case 1: return launch_b<1>(args, replicas, threads, smem, stream);
+    case 2: return launch_b<2>(args, replicas, threads, smem, stream);
+    case 3: return launch_b<3>(args, replicas, threads, smem, stream);
+    case 4: return launch_b<4>(args, replicas, threads, smem, stream);
+    case 6: return launch_b<6>(args, replicas, threads, smem, stream);
+    case 8: return launch_b<8>(args, replicas, threads, smem, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -99,6 +99,11 @@ typedef struct {
   uint64_t seed;         /* Philox key */
   int32_t block_threads; /* 0: pick automatically; else a multiple of 32 */
   int32_t trace;         /* 1: record (E1, E2, event) of every iteration */
+  int32_t field_cache;   /* jumps to the archive reload the member's local
+                            fields from a per-slot device copy instead of
+                            rebuilding them: 0 auto (when it fits in 60 % of
+                            free device memory), 1 on (MODA_EUNSUPPORTED if it
+                            does not fit), 2 off.  Results are identical. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */

@@ -152,6 +152,7 @@ struct moda_run_s {
   int64_t *stats = nullptr;
   int64_t *trace = nullptr;
   int32_t *error = nullptr;
+  unsigned char *fcache = nullptr;
   bool checked = false;
 };
 
@@ -159,7 +160,7 @@ namespace {
 
 void free_run_buffers(moda_run r) {
   void *ptrs[] = {r->arch_E, r->arch_bits, r->arch_count, r->x_final,
-                  r->E_final, r->stats, r->trace, r->error};
+                  r->E_final, r->stats, r->trace, r->error, r->fcache};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (r->start) cudaEventDestroy(r->start);
@@ -328,27 +329,42 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   MODA_CUDA(cudaDeviceGetAttribute(&dev_smem,
                                    cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                    inst->device));
-  // Archive energies, then archive states, move into shared memory when
-  // they fit; otherwise they stay in the run's device buffers.
-  bool e_smem = false, b_smem = false;
-  moda::SmemLayout lay =
-      moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, false, false);
-  if ((int64_t)lay.total > dev_smem)
-    return fail(MODA_EUNSUPPORTED, "shared memory need exceeds the device limit");
-  {
-    moda::SmemLayout l2 =
-        moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, true, false);
-    if ((int64_t)l2.total <= dev_smem) {
-      e_smem = true;
-      lay = l2;
-      moda::SmemLayout l3 =
-          moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, true, true);
-      if ((int64_t)l3.total <= dev_smem) {
-        b_smem = true;
-        lay = l3;
+  if (p->field_cache < 0 || p->field_cache > 2)
+    return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
+  // Field cache: one record of the fields per archive slot, so a jump to
+  // the archive reloads the member's fields instead of rebuilding them.
+  // Used when the escape jumps to the archive and the records fit in (by
+  // default) 60 % of the free device memory.
+  const size_t cache_bytes =
+      (size_t)p->replicas * s_cap * moda::slot_layout(m).bytes;
+  bool want_cache = p->escape == MODA_ESC_ARCHIVE && p->field_cache != 2;
+  if (want_cache && p->field_cache == 0) {
+    size_t free_b = 0, total_b = 0;
+    MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    want_cache = cache_bytes <= free_b / 10 * 6;
+  }
+  // Shared-memory placement, best first: archive energies and states on
+  // chip, then energies only, then neither; with the field cache if it
+  // fits, else without.
+  bool e_smem = false, b_smem = false, use_cache = false, placed = false;
+  moda::SmemLayout lay{};
+  for (int c = want_cache ? 1 : 0; c >= 0 && !placed; --c)
+    for (int opt = 0; opt < 3 && !placed; ++opt) {
+      const bool es = opt <= 1, bs = opt == 0;
+      moda::SmemLayout l =
+          moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, es, bs, c == 1);
+      if ((int64_t)l.total <= dev_smem) {
+        lay = l;
+        e_smem = es;
+        b_smem = bs;
+        use_cache = c == 1;
+        placed = true;
       }
     }
-  }
+  if (!placed)
+    return fail(MODA_EUNSUPPORTED, "shared memory need exceeds the device limit");
+  if (p->field_cache == 1 && !use_cache)
+    return fail(MODA_EUNSUPPORTED, "field cache does not fit");
 
   moda_run r = new (std::nothrow) moda_run_s;
   if (!r) return fail(MODA_ENOMEM, "host allocation");
@@ -369,7 +385,9 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
                                                      cudaGetErrorString(e));
   };
   alloc((void **)&r->arch_E, R * s * 2 * sizeof(int64_t));
-  alloc((void **)&r->arch_bits, R * s * W * sizeof(uint32_t));
+  // 32 spare bytes: a bulk copy reads whole 16-byte blocks around a state
+  alloc((void **)&r->arch_bits, R * s * W * sizeof(uint32_t) + 32);
+  if (use_cache) alloc((void **)&r->fcache, cache_bytes);
   alloc((void **)&r->arch_count, R * sizeof(int32_t));
   alloc((void **)&r->x_final, R * W * sizeof(uint32_t));
   alloc((void **)&r->E_final, R * 2 * sizeof(int64_t));
@@ -423,6 +441,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   a.Fs1 = inst->dFs1;
   a.Fs2 = inst->dFs2;
   a.D = inst->dD;
+  a.fcache = r->fcache;
   a.arch_E = r->arch_E;
   a.arch_bits = r->arch_bits;
   a.arch_count = r->arch_count;

@@ -17,6 +17,27 @@ constexpr int kTableSize = 65536;   // -ln(u) table, u quantised to 2^-16
 enum : uint32_t { kTagAccept = 0, kTagSelect = 1, kTagRestart = 2,
                   kTagExploit = 3, kTagInit = 4 };
 
+// Device status codes written to AnnealArgs::error.
+enum : int32_t { kErrNone = 0, kErrCopyTimeout = 1 };
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) {
+  return (v + a - 1) / a * a;
+}
+
+// Per-slot record of the field cache: the fields (L1, L2) of every bit as
+// int2, then R_i + C_u of every bit as uint16, each part padded to 16 B.
+struct SlotLayout {
+  size_t fields, rc, bytes;
+};
+__host__ __device__ inline SlotLayout slot_layout(int m) {
+  SlotLayout S;
+  const size_t m8 = align_up((size_t)m, 8);
+  S.fields = 0;
+  S.rc = 8 * m8;
+  S.bytes = 8 * m8 + 2 * m8;
+  return S;
+}
+
 // Everything one launch of the single-instance annealing kernel needs.
 // All pointers are device pointers.
 struct AnnealArgs {
@@ -39,30 +60,33 @@ struct AnnealArgs {
   const double *table;      // [65536] -ln((idx + 0.5) / 65536)
   const int32_t *Fs1, *Fs2; // [n][n] F_k + F_k^T (symmetric)
   const int32_t *D;         // [n][n] symmetric distances, zero diagonal
+  // Field cache, [R][s] records of slot_layout(m).bytes, or nullptr: the
+  // fields of every archive member, written when the member is stored and
+  // read back (by a bulk copy started at the top of the iteration) when
+  // the replica jumps to it.
+  unsigned char *fcache;
   // outputs, one block per replica of this launch
   int64_t *arch_E;          // [R][s][2]
-  uint32_t *arch_bits;      // [R][s][W]
+  uint32_t *arch_bits;      // [R][s][W] (+ 32 bytes of padding at the end)
   int32_t *arch_count;      // [R]
   uint32_t *x_final;        // [R][W]
   int64_t *E_final;         // [R][2]
   int64_t *stats;           // [R][4]
   int64_t *trace;           // [R][I_max][3] or nullptr
-  int32_t *error;           // device status word, 0 = fine
+  int32_t *error;           // device status word, kErrNone = fine
 };
 
 // Byte offsets of the shared-memory carve-up of one annealing block.
 struct SmemLayout {
-  size_t Fs, D, M, dE, mask, xmask, amask, rnd, RC, red, archE, archB, total;
+  size_t Fs, D, M, mask, amask, rnd, RC, red, bc, init, mbar, pbuf, pbuf_bytes,
+      archE, archB, total;
 };
-
-__host__ __device__ inline size_t align_up(size_t v, size_t a) {
-  return (v + a - 1) / a * a;
-}
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
                                                   int threads, int rounds,
                                                   bool energies_in_smem,
-                                                  bool bits_in_smem) {
+                                                  bool bits_in_smem,
+                                                  bool field_cache) {
   SmemLayout L;
   size_t o = 0;
   const size_t nn = (size_t)n * n;
@@ -70,13 +94,23 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.Fs = o;    o = align_up(o + 8 * nn, 16);                 // int2 pairs
   L.D = o;     o = align_up(o + 4 * nn, 16);
   L.M = o;     o = align_up(o + 4 * nn, 16);                 // X * D
-  L.dE = o;    o = align_up(o + 16 * (size_t)rounds * threads, 16);
   L.mask = o;  o = align_up(o + 2 * 4 * items, 16);          // two buffers
-  L.xmask = o; o = align_up(o + 2 * 4 * items, 16);
   L.amask = o; o = align_up(o + 4 * items, 16);
-  L.rnd = o;   o = align_up(o + 2 * 4 * 4, 16);
-  L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);  // 2 x (R, C)
+  L.rnd = o;   o = align_up(o + 3 * 4 * 4, 16);                // three buffers
+  L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
+  L.bc = o;    o = align_up(o + 32, 16);
+  L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
+  L.mbar = o;  o = align_up(o + 16, 16);
+  // Prefetch buffers (two): slot record, then the slot's energies and the
+  // 16-byte-aligned span of its state words when those live in HBM.
+  L.pbuf_bytes = 0;
+  if (field_cache) {
+    L.pbuf_bytes = slot_layout(m).bytes;
+    if (!energies_in_smem) L.pbuf_bytes += 16;
+    if (!bits_in_smem) L.pbuf_bytes += align_up(4 * (size_t)W, 16) + 16;
+  }
+  L.pbuf = o;  o = align_up(o + 2 * L.pbuf_bytes, 16);
   L.archE = o; if (energies_in_smem) o = align_up(o + 16 * (size_t)s, 16);
   L.archB = o; if (bits_in_smem) o = align_up(o + 4 * (size_t)s * W, 16);
   L.total = o;

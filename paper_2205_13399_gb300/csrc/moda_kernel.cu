@@ -20,19 +20,25 @@
 // s * Fs^k_ij * d_uv -- the outer product of a flow column and a distance
 // column, s = +1 when the bit turns on.
 //
-// One iteration (Alg. 3):
-//   A  every thread: Delta E and the parallel trial of its bits; accepted
-//      bits publish (dE1, dE2); warp ballots give accept and state masks in
-//      (round, warp, lane) order = ascending bit order.  One warp draws the
-//      iteration's select / restart / exploit words meanwhile.
+// One iteration t (Alg. 3):
+//   0  if the replica could jump to the archive this iteration, the slot it
+//      would jump to is already known (the draw and |A| are), so one thread
+//      starts a bulk copy (TMA) of that member's cached fields into shared
+//      memory, completion tracked by an mbarrier.
+//   A  every thread: Delta E and the parallel trial of its bits; warp
+//      ballots give accept masks in (round, warp, lane) order = ascending
+//      bit order.  One warp draws the next iteration's select / restart /
+//      exploit words meanwhile.
 //   -- barrier --
-//   B  every warp, redundantly: count, rank-select one accepted bit, read
-//      its Delta E; every thread applies the flip to its own registers.
-//      Flip:    archive dominance ballots -- barrier -- every warp picks the
-//               target slot (Alg. 4 / Alg. 5) and writes its words of x.
-//      No flip: jump to a random archive member: every thread rebuilds its
-//               own fields and counts from that member's set bits (no
-//               barrier), or raise the offset by beta.
+//   B  every warp, redundantly: count the accepted bits and rank-select one.
+//      Flip:    its owner publishes Delta E -- barrier -- every thread
+//               applies the flip to its registers and ballots "x dominates
+//               slot y" -- barrier -- every warp picks the target slot
+//               (Alg. 4 / Alg. 5) and stores its part of x (and of the
+//               fields, into the cache).
+//      No flip: jump to a random archive member: wait for the prefetched
+//               fields (or rebuild them as L_k = Fs_k (X D)), or raise the
+//               energy offset by beta.
 #include <cstdint>
 
 #include "moda_internal.h"
@@ -41,6 +47,7 @@ namespace moda {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWaitLimit = 1 << 22;  // bounded mbarrier polls
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplies with a Weyl-sequence key schedule.
@@ -81,6 +88,61 @@ __device__ __forceinline__ bool dominates(int64_t a1, int64_t a2, int64_t b1,
                                           int64_t b2) {
   return a1 <= b1 && a2 <= b2 && !(a1 == b1 && a2 == b2);
 }
+
+// ---- mbarrier and bulk-copy (TMA) helpers --------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+// Bulk copy global -> shared; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
+                                         uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], "
+      "%2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of `bar` to complete, at most kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---- warp-level mask scans ----------------------------------------------
 
 // Over `items` ballot masks in (round, warp) order: each lane sums a
 // contiguous chunk; returns the total (all lanes) and the lane's inclusive
@@ -144,6 +206,12 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red,
   return t;
 }
 
+struct Bcast {
+  int64_t dE1, dE2;  // Delta E of the flipped bit
+  int32_t sgn;       // +1: the bit turns on, -1: off
+  int32_t pad;
+};
+
 template <int B>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
@@ -152,38 +220,59 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const int T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, NW = T >> 5;
   const int items = B * NW;
-  const SmemLayout lay = smem_layout(n, m, W, s, T, B, A.energies_in_smem != 0,
-                                     A.bits_in_smem != 0);
+  const bool fc = A.fcache != nullptr;
+  const SmemLayout lay =
+      smem_layout(n, m, W, s, T, B, A.energies_in_smem != 0,
+                  A.bits_in_smem != 0, fc);
+  const SlotLayout sl = slot_layout(m);
   int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
   int32_t *sD = reinterpret_cast<int32_t *>(smem + lay.D);
-  longlong2 *sDE = reinterpret_cast<longlong2 *>(smem + lay.dE);
+  int32_t *sM = reinterpret_cast<int32_t *>(smem + lay.M);
   uint32_t *sMask = reinterpret_cast<uint32_t *>(smem + lay.mask);
-  uint32_t *sXm = reinterpret_cast<uint32_t *>(smem + lay.xmask);
   uint32_t *sAmask = reinterpret_cast<uint32_t *>(smem + lay.amask);
   uint32_t *sRnd = reinterpret_cast<uint32_t *>(smem + lay.rnd);
   // Row and column counts of the last rebuilt state, two buffers used in
   // turn (rebuild q fills buffer q % 2 and clears the other one).
   int32_t *sRC = reinterpret_cast<int32_t *>(smem + lay.RC);
-  int rc_buf = 0;
   int64_t *sRed = reinterpret_cast<int64_t *>(smem + lay.red);
+  Bcast *bc = reinterpret_cast<Bcast *>(smem + lay.bc);
+  uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
+  uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
   const uint32_t k0 = A.seed_lo, k1 = A.seed_hi;
   int64_t *gE = A.arch_E + (size_t)rb * s * 2;
   uint32_t *gBits = A.arch_bits + (size_t)rb * s * W;
+  unsigned char *gF = fc ? A.fcache + (size_t)rb * s * sl.bytes : nullptr;
   longlong2 *aE = A.energies_in_smem
                       ? reinterpret_cast<longlong2 *>(smem + lay.archE)
                       : reinterpret_cast<longlong2 *>(gE);
   uint32_t *aBits = A.bits_in_smem
                         ? reinterpret_cast<uint32_t *>(smem + lay.archB)
                         : gBits;
+  int rc_buf = 0;
 
   for (int e = tid; e < n * n; e += T) {
     sFs[e] = make_int2(A.Fs1[e], A.Fs2[e]);
     sD[e] = A.D[e];
   }
   for (int e = tid; e < 4 * n; e += T) sRC[e] = 0;
+  if (tid == 0 && fc) {
+    mbar_init(&sBar[0], 1);
+    mbar_init(&sBar[1], 1);
+    fence_mbar_init();
+  }
+  // Draws (select, restart, exploit) of iteration t live in sRnd[t % 3]:
+  // they are drawn one iteration ahead, while a slow warp may still read
+  // those of the previous iteration.
+  if (warp == NW - 1 && lane < 3) {
+    uint32_t c[4] = {0u, 1u, rep, kTagSelect + (uint32_t)lane};
+    philox10(c, k0, k1);
+    sRnd[4 + lane] = c[0];
+  }
+  int *sFail = reinterpret_cast<int *>(&bc->pad);
+  if (tid == 0) *sFail = 0;
 
   // Own bit k (valid when k*T + tid < m): own[k] packs facility i (bits
   // 8..15), location u (bits 0..7) and rc = R_i + C_u (bits 16..31).
@@ -207,9 +296,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     philox10(c, k0, k1);
     xmask |= ((word_of(c, (p >> 5) & 3) >> (p & 31)) & 1u) << k;
   }
-  // State words of the initial x, in shared memory for the rebuild below
-  // (the accept-mask buffer is free until the first iteration).
-  uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.dE);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
@@ -222,7 +308,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // the row / column counts into shared memory; (2) every thread forms
   // L_k[(i,u)] = sum_j Fs^k_ij M_ju for its own bits.  Both passes are
   // exact int32 arithmetic (the instance check bounds every field).
-  int32_t *sM = reinterpret_cast<int32_t *>(smem + lay.M);
   auto rebuild = [&](const uint32_t *words) {
     for (int e = tid; e < n * n; e += T) {
       const int j = (int)__umulhi((uint32_t)e, A.magic);
@@ -302,17 +387,54 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int64_t Eoff = 0;
   int acount = 0;
   int64_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
-  const int rng_warp = NW - 1;
+  // Prefetch state (uniform across the block): buffer b has a copy in
+  // flight when pend & (1 << b); its mbarrier's next phase is ph >> b & 1.
+  uint32_t pend = 0, ph = 0;
+  bool failed = false;
 
   for (int64_t it = 1; it <= A.I_max; ++it) {
     const uint32_t t = (uint32_t)it;
     const int buf = (int)(t & 1u);
     uint32_t *mask = sMask + buf * items;
-    uint32_t *xm = sXm + buf * items;
-    uint32_t *rnd = sRnd + buf * 4;
+    const uint32_t *rnd = sRnd + (t % 3u) * 4;
     const int si = (int)((it <= A.nsched ? it : (int64_t)A.nsched) - 1);
     const double delta = A.sch_delta[si];
     const int64_t lo = A.sch_lo[si], hi = A.sch_hi[si];
+
+    // Step 0: prefetch the member a jump in this iteration would land on.
+    unsigned char *pb = smem + lay.pbuf + (size_t)buf * lay.pbuf_bytes;
+    const bool jump_possible = fc && A.escape == 0 && acount > 0;
+    if (jump_possible) {
+      if (pend & (1u << buf)) {  // retire the unused copy of iteration t-2
+        if (!mbar_wait(&sBar[buf], (ph >> buf) & 1u)) {
+          failed = true;
+          *sFail = 1;
+        }
+        ph ^= 1u << buf;
+        pend &= ~(1u << buf);
+      }
+      if (tid == 0) {
+        const int slot = pick(rnd[1], acount);
+        const uint32_t bytes = (uint32_t)sl.bytes;
+        uint32_t eb = 0, bb = 0, boff = 0;
+        if (!A.energies_in_smem) eb = 16;
+        if (!A.bits_in_smem) {
+          const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+          boff = (uint32_t)(b0 & 15);
+          bb = (uint32_t)align_up(boff + 4 * (size_t)W, 16);
+        }
+        fence_proxy_async_shared();
+        mbar_expect_tx(&sBar[buf], bytes + eb + bb);
+        bulk_g2s(pb, gF + (size_t)slot * sl.bytes, bytes, &sBar[buf]);
+        if (eb)
+          bulk_g2s(pb + sl.bytes, gE + (size_t)slot * 2, 16, &sBar[buf]);
+        if (bb)
+          bulk_g2s(pb + sl.bytes + eb,
+                   reinterpret_cast<const unsigned char *>(gBits + (size_t)slot * W) - boff,
+                   bb, &sBar[buf]);
+      }
+      pend |= 1u << buf;
+    }
 
     // Phase A: Delta E (Eq. cale) and the parallel trial of every bit.
 #pragma unroll
@@ -323,9 +445,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int p = k * T + tid;
         const int sg = 1 - 2 * (int)xv;
         const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
-        int64_t e1 = (int64_t)(sg * L1[k]) + A.w1 * h;
-        int64_t e2 = (int64_t)(sg * L2[k]) + A.w2 * h;
-        int64_t f1 = e1, f2 = e2;
+        int64_t f1 = (int64_t)(sg * L1[k]) + A.w1 * h;
+        int64_t f2 = (int64_t)(sg * L2[k]) + A.w2 * h;
         if (A.escape == 1) {
           f1 -= Eoff;
           f2 -= Eoff;
@@ -340,21 +461,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           const uint32_t w = word_of(c, p & 3);
           acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
         }
-        if (acc) sDE[p] = make_longlong2(e1, e2);
       }
       const uint32_t bal = __ballot_sync(kFull, acc);
-      const uint32_t xb = __ballot_sync(kFull, xv != 0);
-      if (lane == 0) {
-        mask[k * NW + warp] = bal;
-        xm[k * NW + warp] = xb;
-      }
+      if (lane == 0) mask[k * NW + warp] = bal;
     }
-    if (warp == rng_warp && lane < 3) {
-      uint32_t c[4] = {0u, t, rep, kTagSelect + (uint32_t)lane};
+    if (warp == NW - 1 && lane < 3) {  // draws of iteration t + 1
+      uint32_t c[4] = {0u, t + 1u, rep, kTagSelect + (uint32_t)lane};
       philox10(c, k0, k1);
-      rnd[lane] = c[0];
+      sRnd[((t + 1u) % 3u) * 4 + lane] = c[0];
     }
     __syncthreads();
+    if (fc && *sFail) break;  // a bulk copy did not complete (uniform exit)
 
     // Phase B: every warp reaches the same decision from shared memory.
     int incl, cnt;
@@ -363,14 +480,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (total > 0) {
       const int ps = warp_mask_select(mask, items, NW, T, lane, incl, cnt,
                                       pick(rnd[0], total));
-      const longlong2 de = sDE[ps];
       const int kk = ps / T;
-      const int rr = ps - kk * T;
-      const int xs = (int)((xm[kk * NW + (rr >> 5)] >> (rr & 31)) & 1u);
-      const int sg = 1 - 2 * xs;
+      if (ps - kk * T == tid) {  // the owner publishes Delta E of the flip
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k != kk) continue;
+          const int xv = (int)((xmask >> k) & 1u);
+          const int sg = 1 - 2 * xv;
+          const int h = sg * ((own[k] >> 16) - 1 - 2 * xv);
+          bc->dE1 = (int64_t)(sg * L1[k]) + A.w1 * h;
+          bc->dE2 = (int64_t)(sg * L2[k]) + A.w2 * h;
+          bc->sgn = sg;
+        }
+      }
+      __syncthreads();
+      const int64_t nE1 = E1 + bc->dE1, nE2 = E2 + bc->dE2;
+      const int sg = bc->sgn;
       const int j = (int)__umulhi((uint32_t)ps, A.magic);
       const int v = ps - j * n;
-      const int64_t nE1 = E1 + de.x, nE2 = E2 + de.y;
       // Apply the flip of (j, v) to the owned registers.
 #pragma unroll
       for (int k = 0; k < B; ++k) {
@@ -424,6 +551,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           if (lane == 0 && wi < W) aBits[(size_t)target * W + wi] = wv;
         }
         if (tid == 0) aE[target] = make_longlong2(nE1, nE2);
+        if (fc) {
+          unsigned char *rec = gF + (size_t)target * sl.bytes;
+          int2 *rf = reinterpret_cast<int2 *>(rec + sl.fields);
+          uint16_t *rr = reinterpret_cast<uint16_t *>(rec + sl.rc);
+#pragma unroll
+          for (int k = 0; k < B; ++k) {
+            const int q = k * T + tid;
+            if (q >= m) continue;
+            rf[q] = make_int2(L1[k], L2[k]);
+            rr[q] = (uint16_t)(own[k] >> 16);
+          }
+          fence_proxy_async_global();  // later bulk copies read these
+        }
+        // The next iteration's bulk copy may read this slot.
+        if (fc) __syncthreads();
       }
       E1 = nE1;
       E2 = nE2;
@@ -434,10 +576,47 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       if (acount > 0) {
         // Alg. 3: jump to a random archive member.
         const int slot = pick(rnd[1], acount);
-        const longlong2 se = aE[slot];
-        E1 = se.x;
-        E2 = se.y;
-        rebuild(aBits + (size_t)slot * W);
+        if (fc) {
+          if (!mbar_wait(&sBar[buf], (ph >> buf) & 1u)) {
+            failed = true;
+            *sFail = 1;
+          }
+          ph ^= 1u << buf;
+          pend &= ~(1u << buf);
+          const int2 *rf = reinterpret_cast<const int2 *>(pb + sl.fields);
+          const uint16_t *rr = reinterpret_cast<const uint16_t *>(pb + sl.rc);
+          longlong2 se;
+          if (A.energies_in_smem)
+            se = aE[slot];
+          else
+            se = *reinterpret_cast<const longlong2 *>(pb + sl.bytes);
+          const uint32_t *words;
+          if (A.bits_in_smem) {
+            words = aBits + (size_t)slot * W;
+          } else {
+            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+            words = reinterpret_cast<const uint32_t *>(
+                pb + sl.bytes + (A.energies_in_smem ? 0 : 16) + (b0 & 15));
+          }
+          E1 = se.x;
+          E2 = se.y;
+          xmask = 0;
+#pragma unroll
+          for (int k = 0; k < B; ++k) {
+            const int q = k * T + tid;
+            if (q >= m) continue;
+            const int2 f = rf[q];
+            L1[k] = f.x;
+            L2[k] = f.y;
+            own[k] = ((int)rr[q] << 16) | (own[k] & 0xFFFF);
+            xmask |= ((words[q >> 5] >> (q & 31)) & 1u) << k;
+          }
+        } else {
+          const longlong2 se = aE[slot];
+          E1 = se.x;
+          E2 = se.y;
+          rebuild(aBits + (size_t)slot * W);
+        }
         ++st_jump;
         event = -1 - (int64_t)slot;
       } else {
@@ -454,6 +633,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       tr[2] = event;
     }
   }
+
+  // No bulk copy may be in flight when the block exits.
+  for (int b = 0; b < 2; ++b)
+    if (pend & (1u << b)) {
+      if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) failed = true;
+    }
+  if (failed && tid == 0) atomicExch(A.error, kErrCopyTimeout);
 
   __syncthreads();
 #pragma unroll

@@ -23,6 +23,7 @@ STATUS_NAMES = ["MODA_OK", "MODA_EINVAL", "MODA_ENOMEM", "MODA_EOVERFLOW",
 ACCEPT = {"strict": 0, "lenient": 1}
 ARCHIVE = {"explore": 0, "exploit": 1}
 ESCAPE = {"archive": 0, "offset": 1}
+FIELD_CACHE = {"auto": 0, "on": 1, "off": 2}
 
 # Functions declared in include/moda.h.
 ABI_FUNCTIONS = [
@@ -60,6 +61,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("block_threads", ctypes.c_int32),
         ("trace", ctypes.c_int32),
+        ("field_cache", ctypes.c_int32),
     ]
 
 
@@ -254,13 +256,13 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
                 deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
-                trace: bool = False) -> Params:
+                trace: bool = False, field_cache: str = "auto") -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
-                  int(bool(trace)))
+                  int(bool(trace)), FIELD_CACHE[field_cache])
 
 
 def anneal(inst: Instance, params: Params | None = None, stream=None, **kw) -> Run:

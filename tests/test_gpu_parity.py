@@ -19,36 +19,43 @@ VARIANTS = [(acc, arc, esc) for acc in ("strict", "lenient")
 FAST = dict(delta0=2e6, deltaf=3e3, xi=0.02)
 
 
+@pytest.mark.parametrize("cache", ["on", "off"])
 @pytest.mark.parametrize("acc,arc,esc", VARIANTS)
-def test_variants_traced_small(acc, arc, esc):
+def test_variants_traced_small(acc, arc, esc, cache):
     """Every acceptance x archive x escape combination on ragged sizes, with
-    per-iteration traces compared."""
+    per-iteration traces compared, with and without the field cache."""
+    if esc == "offset" and cache == "on":
+        pytest.skip("the field cache serves only jumps to the archive")
     for n, bt in ((5, 0), (7, 0), (12, 32), (12, 0)):
         inst = inputs.uniform_instance(n, index=n, workload="P8")
         kw = dict(replicas=3, I_max=1500, seed=11 + n, accept=acc, archive=arc, escape=esc,
                   beta=700, **FAST)
-        _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, **kw)
+        _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, field_cache=cache, **kw)
         _, orc = oracle_run(inst, trace=True, **kw)
         compare(res, range(3), orc, n * n, gpu_trace=tr)
 
 
-@pytest.mark.parametrize("n,bt", [(20, 64), (20, 0), (25, 160), (25, 320), (25, 0), (31, 0)])
-def test_block_shapes(n, bt):
-    """Several bits per thread (B = 1, 2, 4, 8) and ragged last rounds."""
+@pytest.mark.parametrize("cache", ["on", "off"])
+@pytest.mark.parametrize("n,bt", [(20, 64), (20, 0), (25, 96), (25, 160), (25, 320), (25, 0),
+                                  (31, 0), (40, 0)])
+def test_block_shapes(n, bt, cache):
+    """Several bits per thread (B = 1, 2, 3, 4, 6, 8) and ragged last rounds."""
     inst = inputs.euclid_instance(n, 0.5, False, index=n, workload="P25")
     kw = dict(replicas=4, I_max=3000, seed=3, **FAST)
-    _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, **kw)
+    _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, field_cache=cache, **kw)
     _, orc = oracle_run(inst, trace=True, **kw)
     compare(res, range(4), orc, n * n, gpu_trace=tr)
 
 
-def test_small_archive_and_replica_base():
+@pytest.mark.parametrize("cache", ["on", "off"])
+def test_small_archive_and_replica_base(cache):
     """Archive capacity below m (the full-archive branches) and a replica
     offset: rows of a shifted launch equal the oracle's replicas 5..7."""
     inst = inputs.euclid_instance(10, -0.7, False, index=3, workload="BATCH")
     kw = dict(I_max=4000, seed=99, archive_size=7, **FAST)
     for arc in ("explore", "exploit"):
-        _, _, res, _ = gpu_run(inst, replicas=3, replica_base=5, archive=arc, **kw)
+        _, _, res, _ = gpu_run(inst, replicas=3, replica_base=5, archive=arc, field_cache=cache,
+                               **kw)
         _, orc = oracle_run(inst, replicas=[5, 6, 7], archive=arc, **kw)
         compare(res, range(3), orc, 100)
 
@@ -117,15 +124,17 @@ def test_p25_full_config_sampled_replicas():
             assert a["c2"] == orc_mod.qap_cost(inst.F2, inst.D, a["perm"])
 
 
+@pytest.mark.parametrize("cache", ["on", "off"])
 @pytest.mark.parametrize("name", ["P50", "P75"])
-def test_large_configs_prefix(name):
+def test_large_configs_prefix(name, cache):
     """n = 50 / 75 workloads in their full launch shape (256 replicas); the
     schedule does not depend on I_max, so a shorter run is an exact prefix of
     the full one and the oracle recomputes two sampled replicas of it."""
     inst = inputs.workload_instance(name)
     run = inputs.WORKLOAD_RUN[name]
     I_max = 20000
-    _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=I_max, seed=run["seed"])
+    _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=I_max, seed=run["seed"],
+                           field_cache=cache)
     rows = [1, run["replicas"] - 1]
     _, orc = oracle_run(inst, replicas=rows, I_max=I_max, seed=run["seed"])
     compare(res, rows, orc, inst.n * inst.n)

@@ -52,6 +52,9 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--prefetch", type=int, default=0,
+                    help="field-cache prefetch distance + 1 (0: automatic)")
+    ap.add_argument("--field-cache", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--I-max", dest="I_max", type=int, default=None,
                     help="override the workload's iteration budget (profiling only)")
     return ap.parse_args(argv)
@@ -225,7 +228,8 @@ def main(argv=None):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(replicas=R, replica_base=base, I_max=I_max, seed=run["seed"],
-              block_threads=args.block_threads)
+              block_threads=args.block_threads, prefetch=args.prefetch,
+              field_cache=args.field_cache)
 
     def step():
         r = moda.anneal(g, stream=stream, **kw).wait()

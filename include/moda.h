@@ -104,6 +104,9 @@ typedef struct {
                             rebuilding them: 0 auto (when it fits in 60 % of
                             free device memory), 1 on (MODA_EUNSUPPORTED if it
                             does not fit), 2 off.  Results are identical. */
+  int32_t prefetch;      /* field-cache prefetch distance: 0 auto, k in 1..4
+                            copies a jump's target k - 1 iterations ahead
+                            (MODA_EUNSUPPORTED if it does not fit). */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */
@@ -149,8 +152,13 @@ moda_status moda_wait(moda_run run, int64_t timeout_ms);
  *                       word p / 32 at position p % 32
  *   x        [W]        state after the last iteration
  *   E_final  [2]        its energies
- *   stats    [4]        accepted flips, jumps to the archive, escapes with an
- *                       empty archive, offset raises
+ *   stats    [8]        accepted flips, jumps to the archive, escapes with an
+ *                       empty archive, offset raises; then, for profiling,
+ *                       jumps served by a prefetched field-cache record,
+ *                       jumps that read the record directly, and (only in
+ *                       builds with MODA_KERNEL_CLOCKS defined, else 0) SM
+ *                       clock cycles spent waiting for prefetched records
+ *                       and SM clock cycles of the iteration loop
  * Any pointer may be NULL.  MODA_EBUSY while the run executes. */
 moda_status moda_read_replica(moda_run run, int32_t r, int32_t *count,
                               int64_t *E, uint32_t *bits, uint32_t *x,

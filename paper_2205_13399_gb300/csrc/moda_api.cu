@@ -331,6 +331,8 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
                                    inst->device));
   if (p->field_cache < 0 || p->field_cache > 2)
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
+  if (p->prefetch < 0 || p->prefetch > moda::kMaxLookahead + 1)
+    return fail(MODA_EINVAL, "prefetch must be in [0, 4]");
   // Field cache: one record of the fields per archive slot, so a jump to
   // the archive reloads the member's fields instead of rebuilding them.
   // Used when the escape jumps to the archive and the records fit in (by
@@ -343,28 +345,33 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
     want_cache = cache_bytes <= free_b / 10 * 6;
   }
-  // Shared-memory placement, best first: archive energies and states on
-  // chip, then energies only, then neither; with the field cache if it
-  // fits, else without.
-  bool e_smem = false, b_smem = false, use_cache = false, placed = false;
+  // Shared-memory placement, best first: the field cache (if wanted), the
+  // archive energies and states on chip (then energies only, then
+  // neither), Delta E published in shared memory, and the prefetch
+  // distance (1, then 0 iterations, unless prescribed).
+  moda::Placement place{};
+  bool placed = false;
   moda::SmemLayout lay{};
+  const int la_hi = p->prefetch > 0 ? p->prefetch - 1 : 1;
+  const int la_lo = p->prefetch > 0 ? p->prefetch - 1 : 0;
   for (int c = want_cache ? 1 : 0; c >= 0 && !placed; --c)
-    for (int opt = 0; opt < 3 && !placed; ++opt) {
-      const bool es = opt <= 1, bs = opt == 0;
-      moda::SmemLayout l =
-          moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, es, bs, c == 1);
-      if ((int64_t)l.total <= dev_smem) {
-        lay = l;
-        e_smem = es;
-        b_smem = bs;
-        use_cache = c == 1;
-        placed = true;
-      }
-    }
+    for (int opt = 0; opt < 3 && !placed; ++opt)
+      for (int de = 1; de >= 0 && !placed; --de)
+        for (int la = c ? la_hi : 0; la >= (c ? la_lo : 0) && !placed; --la) {
+          const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1};
+          const moda::SmemLayout l =
+              moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, pl);
+          if ((int64_t)l.total <= dev_smem) {
+            lay = l;
+            place = pl;
+            placed = true;
+          }
+        }
   if (!placed)
     return fail(MODA_EUNSUPPORTED, "shared memory need exceeds the device limit");
-  if (p->field_cache == 1 && !use_cache)
+  if (p->field_cache == 1 && !place.field_cache)
     return fail(MODA_EUNSUPPORTED, "field cache does not fit");
+  const bool use_cache = place.field_cache;
 
   moda_run r = new (std::nothrow) moda_run_s;
   if (!r) return fail(MODA_ENOMEM, "host allocation");
@@ -391,7 +398,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   alloc((void **)&r->arch_count, R * sizeof(int32_t));
   alloc((void **)&r->x_final, R * W * sizeof(uint32_t));
   alloc((void **)&r->E_final, R * 2 * sizeof(int64_t));
-  alloc((void **)&r->stats, R * 4 * sizeof(int64_t));
+  alloc((void **)&r->stats, R * moda::kStats * sizeof(int64_t));
   alloc((void **)&r->error, sizeof(int32_t));
   if (p->trace && p->I_max > 0)
     alloc((void **)&r->trace, R * (size_t)p->I_max * 3 * sizeof(int64_t));
@@ -431,8 +438,10 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   a.archive = p->archive;
   a.escape = p->escape;
   a.magic = (uint32_t)(0xFFFFFFFFu / (uint32_t)inst->n) + 1u;
-  a.energies_in_smem = e_smem;
-  a.bits_in_smem = b_smem;
+  a.energies_in_smem = place.energies_in_smem;
+  a.bits_in_smem = place.bits_in_smem;
+  a.lookahead = place.lookahead;
+  a.de_in_smem = place.de_in_smem;
   a.nsched = sch.count;
   a.sch_delta = sch.delta;
   a.sch_lo = sch.lo;
@@ -515,7 +524,8 @@ moda_status moda_read_replica(moda_run r, int32_t rep, int32_t *count,
   if (E_final)
     MODA_CUDA(cudaMemcpy(E_final, r->E_final + first * 2, cnt * 2 * sizeof(int64_t), d2h));
   if (stats)
-    MODA_CUDA(cudaMemcpy(stats, r->stats + first * 4, cnt * 4 * sizeof(int64_t), d2h));
+    MODA_CUDA(cudaMemcpy(stats, r->stats + first * moda::kStats,
+                         cnt * moda::kStats * sizeof(int64_t), d2h));
   return MODA_OK;
 }
 

@@ -12,6 +12,8 @@ namespace moda {
 constexpr int kMaxN = 128;          // n <= 128: a bit index fits (i << 8) | u
 constexpr int kMaxThreads = 1024;
 constexpr int kTableSize = 65536;   // -ln(u) table, u quantised to 2^-16
+constexpr int kMaxLookahead = 3;    // field-cache prefetch distance
+constexpr int kStats = 8;           // counters per replica (see moda.h)
 
 // Purposes of a Philox draw (fourth counter word).
 enum : uint32_t { kTagAccept = 0, kTagSelect = 1, kTagRestart = 2,
@@ -25,7 +27,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
 }
 
 // Per-slot record of the field cache: the fields (L1, L2) of every bit as
-// int2, then R_i + C_u of every bit as uint16, each part padded to 16 B.
+// int2, then R_i + C_u of every bit as int32.
 struct SlotLayout {
   size_t fields, rc, bytes;
 };
@@ -34,7 +36,7 @@ __host__ __device__ inline SlotLayout slot_layout(int m) {
   const size_t m8 = align_up((size_t)m, 8);
   S.fields = 0;
   S.rc = 8 * m8;
-  S.bytes = 8 * m8 + 2 * m8;
+  S.bytes = 12 * m8;
   return S;
 }
 
@@ -54,6 +56,8 @@ struct AnnealArgs {
                             // reuse the last one
   int32_t energies_in_smem; // archive energies kept in shared memory
   int32_t bits_in_smem;     // archive states kept in shared memory
+  int32_t lookahead;        // field-cache prefetch distance (iterations)
+  int32_t de_in_smem;       // accepted bits publish Delta E in shared memory
   const double *sch_delta;  // [nsched] delta_t, t = 1..nsched
   const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
   const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
@@ -62,57 +66,69 @@ struct AnnealArgs {
   const int32_t *D;         // [n][n] symmetric distances, zero diagonal
   // Field cache, [R][s] records of slot_layout(m).bytes, or nullptr: the
   // fields of every archive member, written when the member is stored and
-  // read back (by a bulk copy started at the top of the iteration) when
-  // the replica jumps to it.
+  // brought back by a bulk copy (TMA), started up to `lookahead`
+  // iterations early, when the replica jumps to it.
   unsigned char *fcache;
   // outputs, one block per replica of this launch
   int64_t *arch_E;          // [R][s][2]
-  uint32_t *arch_bits;      // [R][s][W] (+ 32 bytes of padding at the end)
+  uint32_t *arch_bits;      // [R][s][W]
   int32_t *arch_count;      // [R]
   uint32_t *x_final;        // [R][W]
   int64_t *E_final;         // [R][2]
-  int64_t *stats;           // [R][4]
+  int64_t *stats;           // [R][kStats]
   int64_t *trace;           // [R][I_max][3] or nullptr
   int32_t *error;           // device status word, kErrNone = fine
 };
 
 // Byte offsets of the shared-memory carve-up of one annealing block.
 struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, RC, red, bc, init, mbar, pbuf, pbuf_bytes,
-      archE, archB, total;
+  size_t Fs, D, M, mask, amask, rnd, RC, red, bc, init, mbar, dE, pf, pf_slot,
+      pfE, pfW, archE, archB, total;
+};
+
+// Placement choices of one launch (decided on the host).
+struct Placement {
+  bool energies_in_smem;  // archive energies on chip
+  bool bits_in_smem;      // archive states on chip
+  bool field_cache;       // jumps reload cached fields
+  int lookahead;          // prefetch distance, iterations
+  bool de_in_smem;        // accepted bits publish Delta E in shared memory
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
                                                   int threads, int rounds,
-                                                  bool energies_in_smem,
-                                                  bool bits_in_smem,
-                                                  bool field_cache) {
+                                                  const Placement &P) {
   SmemLayout L;
   size_t o = 0;
   const size_t nn = (size_t)n * n;
   const size_t items = (size_t)rounds * (threads / 32);
+  const size_t bits = (size_t)rounds * threads;
   L.Fs = o;    o = align_up(o + 8 * nn, 16);                 // int2 pairs
   L.D = o;     o = align_up(o + 4 * nn, 16);
-  L.M = o;     o = align_up(o + 4 * nn, 16);                 // X * D
-  L.mask = o;  o = align_up(o + 2 * 4 * items, 16);          // two buffers
+  L.mask = o;  o = align_up(o + 4 * 4 * items, 16);  // accept, state x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
-  L.rnd = o;   o = align_up(o + 3 * 4 * 4, 16);                // three buffers
+  L.rnd = o;   o = align_up(o + (kMaxLookahead + 3) * 4 * 4, 16);
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
-  L.mbar = o;  o = align_up(o + 16, 16);
-  // Prefetch buffers (two): slot record, then the slot's energies and the
-  // 16-byte-aligned span of its state words when those live in HBM.
-  L.pbuf_bytes = 0;
-  if (field_cache) {
-    L.pbuf_bytes = slot_layout(m).bytes;
-    if (!energies_in_smem) L.pbuf_bytes += 16;
-    if (!bits_in_smem) L.pbuf_bytes += align_up(4 * (size_t)W, 16) + 16;
-  }
-  L.pbuf = o;  o = align_up(o + 2 * L.pbuf_bytes, 16);
-  L.archE = o; if (energies_in_smem) o = align_up(o + 16 * (size_t)s, 16);
-  L.archB = o; if (bits_in_smem) o = align_up(o + 4 * (size_t)s * W, 16);
+  L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
+  L.dE = o;    if (P.de_in_smem) o = align_up(o + 16 * bits, 16);
+  // Prefetch buffers (lookahead + 2: the one being filled, the one of the
+  // current iteration and the one a lagging warp may still read): one
+  // field-cache record, then the member's energies and the 16-byte-aligned
+  // span of its state words when those live in HBM.  M = X * D (only used
+  // by rebuilds, which never overlap a prefetch) shares this space.
+  L.pfE = slot_layout(m).bytes;
+  L.pfW = L.pfE + (P.energies_in_smem ? 0 : 16);
+  L.pf_slot = align_up(L.pfW + (P.bits_in_smem ? 0 : align_up(4 * (size_t)W, 16) + 16), 16);
+  L.pf = o;
+  size_t pf_bytes = P.field_cache ? L.pf_slot * (size_t)(P.lookahead + 2) : 0;
+  if (pf_bytes < 4 * nn) pf_bytes = 4 * nn;
+  L.M = o;
+  o = align_up(o + pf_bytes, 16);
+  L.archE = o; if (P.energies_in_smem) o = align_up(o + 16 * (size_t)s, 16);
+  L.archB = o; if (P.bits_in_smem) o = align_up(o + 4 * (size_t)s * W, 16);
   L.total = o;
   return L;
 }

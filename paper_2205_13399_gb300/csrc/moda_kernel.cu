@@ -21,24 +21,24 @@
 // column, s = +1 when the bit turns on.
 //
 // One iteration t (Alg. 3):
-//   0  if the replica could jump to the archive this iteration, the slot it
-//      would jump to is already known (the draw and |A| are), so one thread
-//      starts a bulk copy (TMA) of that member's cached fields into shared
-//      memory, completion tracked by an mbarrier.
+//   0  (field cache on, replica not in a run of flips) thread 0 starts a
+//      bulk copy (TMA, completion on an mbarrier) of the cached fields of
+//      the member that a jump at iteration t + lookahead would land on: its
+//      draw and |A| are known already; the copy is not used if that member
+//      is rewritten before then.
 //   A  every thread: Delta E and the parallel trial of its bits; warp
 //      ballots give accept masks in (round, warp, lane) order = ascending
-//      bit order.  One warp draws the next iteration's select / restart /
-//      exploit words meanwhile.
+//      bit order; accepted bits publish Delta E.  One warp draws a later
+//      iteration's select / restart / exploit words meanwhile.
 //   -- barrier --
 //   B  every warp, redundantly: count the accepted bits and rank-select one.
-//      Flip:    its owner publishes Delta E -- barrier -- every thread
-//               applies the flip to its registers and ballots "x dominates
-//               slot y" -- barrier -- every warp picks the target slot
-//               (Alg. 4 / Alg. 5) and stores its part of x (and of the
+//      Flip:    every thread applies it to its registers and ballots "x
+//               dominates slot y" -- barrier -- every warp picks the target
+//               slot (Alg. 4 / Alg. 5) and stores its part of x (and of the
 //               fields, into the cache).
-//      No flip: jump to a random archive member: wait for the prefetched
-//               fields (or rebuild them as L_k = Fs_k (X D)), or raise the
-//               energy offset by beta.
+//      No flip: jump to a random archive member: take the prefetched fields
+//               (or read them from the cache, or rebuild them as
+//               L_k = Fs_k (X D)), or raise the energy offset by beta.
 #include <cstdint>
 
 #include "moda_internal.h"
@@ -135,7 +135,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for phase `parity` of `bar` to complete, at most kWaitLimit polls.
+// Waits for the phase of parity `parity` of `bar` to complete, at most
+// kWaitLimit polls; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   for (int i = 0; i < kWaitLimit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
@@ -209,6 +210,14 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red,
 struct Bcast {
   int64_t dE1, dE2;  // Delta E of the flipped bit
   int32_t sgn;       // +1: the bit turns on, -1: off
+  int32_t fail;      // a bulk copy did not complete
+};
+
+// Prefetch bookkeeping entry for one target iteration.
+struct PfRec {
+  int32_t iter;    // iteration that issued the copy, 0 = none
+  int32_t slot;    // archive slot copied
+  int32_t parity;  // mbarrier phase parity that signals completion
   int32_t pad;
 };
 
@@ -221,9 +230,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const int lane = tid & 31, warp = tid >> 5, NW = T >> 5;
   const int items = B * NW;
   const bool fc = A.fcache != nullptr;
-  const SmemLayout lay =
-      smem_layout(n, m, W, s, T, B, A.energies_in_smem != 0,
-                  A.bits_in_smem != 0, fc);
+  const bool de_smem = A.de_in_smem != 0;
+  const int LA = A.lookahead;           // prefetch distance
+  // Prefetch buffers: target iteration tt uses buffer tt % NB.  The copy
+  // for t + LA starts before the barrier of iteration t, while a lagging
+  // warp may still read the buffer of t - 1, so NB = LA + 2.
+  const int NB = LA + 2;
+  const uint32_t RB = (uint32_t)LA + 3;  // draw ring: t % RB
+  const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
+                    de_smem};
+  const SmemLayout lay = smem_layout(n, m, W, s, T, B, P);
   const SlotLayout sl = slot_layout(m);
   int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
   int32_t *sD = reinterpret_cast<int32_t *>(smem + lay.D);
@@ -238,6 +254,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   Bcast *bc = reinterpret_cast<Bcast *>(smem + lay.bc);
   uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
   uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
+  longlong2 *sDE = reinterpret_cast<longlong2 *>(smem + lay.dE);
+  // Prefetch bookkeeping (after initialisation; shares the reduction
+  // space): sPf[target iteration % 8], and sWr[iteration % 8] = the archive
+  // slot that iteration wrote (-1 = none).
+  PfRec *sPf = reinterpret_cast<PfRec *>(smem + lay.red);
+  int32_t *sWr = reinterpret_cast<int32_t *>(smem + lay.red + 8 * sizeof(PfRec));
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
@@ -258,21 +280,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     sD[e] = A.D[e];
   }
   for (int e = tid; e < 4 * n; e += T) sRC[e] = 0;
-  if (tid == 0 && fc) {
-    mbar_init(&sBar[0], 1);
-    mbar_init(&sBar[1], 1);
-    fence_mbar_init();
+  if (tid == 0) {
+    bc->fail = 0;
+    if (fc) {
+      for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
+      fence_mbar_init();
+    }
   }
-  // Draws (select, restart, exploit) of iteration t live in sRnd[t % 3]:
-  // they are drawn one iteration ahead, while a slow warp may still read
-  // those of the previous iteration.
+  // Draws (select, restart, exploit) of iteration t live in sRnd[t % RB];
+  // they are drawn LA + 1 iterations ahead.
   if (warp == NW - 1 && lane < 3) {
-    uint32_t c[4] = {0u, 1u, rep, kTagSelect + (uint32_t)lane};
-    philox10(c, k0, k1);
-    sRnd[4 + lane] = c[0];
+    for (uint32_t q = 1; q <= (uint32_t)LA + 1; ++q) {
+      uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
+      philox10(c, k0, k1);
+      sRnd[(q % RB) * 4 + lane] = c[0];
+    }
   }
-  int *sFail = reinterpret_cast<int *>(&bc->pad);
-  if (tid == 0) *sFail = 0;
 
   // Own bit k (valid when k*T + tid < m): own[k] packs facility i (bits
   // 8..15), location u (bits 0..7) and rc = R_i + C_u (bits 16..31).
@@ -383,57 +406,83 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     E1 = s1 / 2 + A.w1 * (gp / 2);
     E2 = s2 / 2 + A.w2 * (gp / 2);
   }
+  if (tid < 8) {
+    sPf[tid] = PfRec{0, 0, 0, 0};
+    sWr[tid] = -1;
+  }
+  __syncthreads();
 
   int64_t Eoff = 0;
   int acount = 0;
-  int64_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
-  // Prefetch state (uniform across the block): buffer b has a copy in
-  // flight when pend & (1 << b); its mbarrier's next phase is ph >> b & 1.
+  uint32_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
+  uint32_t st_pf = 0, st_direct = 0;
+  long long st_wait = 0, loop_t0 = 0;
+#ifdef MODA_KERNEL_CLOCKS
+  loop_t0 = clock64();
+#endif
+  int flip_streak = 0;  // consecutive flip iterations: no prefetch while hot
+  // Thread 0's copy bookkeeping: buffer b has a copy in flight when
+  // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
   uint32_t pend = 0, ph = 0;
-  bool failed = false;
+  // Schedule entries, loaded one iteration ahead.
+  double delta_n = A.sch_delta[0];
+  int64_t lo_n = A.sch_lo[0], hi_n = A.sch_hi[0];
 
   for (int64_t it = 1; it <= A.I_max; ++it) {
     const uint32_t t = (uint32_t)it;
     const int buf = (int)(t & 1u);
-    uint32_t *mask = sMask + buf * items;
-    const uint32_t *rnd = sRnd + (t % 3u) * 4;
-    const int si = (int)((it <= A.nsched ? it : (int64_t)A.nsched) - 1);
-    const double delta = A.sch_delta[si];
-    const int64_t lo = A.sch_lo[si], hi = A.sch_hi[si];
+    uint32_t *mask = sMask + buf * items;        // accept ballots
+    uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
+    const uint32_t *rnd = sRnd + (t % RB) * 4;
+    const double delta = delta_n;
+    const int64_t lo = lo_n, hi = hi_n;
+    {
+      const int sn = (int)((it + 1 <= A.nsched ? it + 1 : (int64_t)A.nsched) - 1);
+      delta_n = A.sch_delta[sn];
+      lo_n = A.sch_lo[sn];
+      hi_n = A.sch_hi[sn];
+    }
 
-    // Step 0: prefetch the member a jump in this iteration would land on.
-    unsigned char *pb = smem + lay.pbuf + (size_t)buf * lay.pbuf_bytes;
-    const bool jump_possible = fc && A.escape == 0 && acount > 0;
-    if (jump_possible) {
-      if (pend & (1u << buf)) {  // retire the unused copy of iteration t-2
-        if (!mbar_wait(&sBar[buf], (ph >> buf) & 1u)) {
-          failed = true;
-          *sFail = 1;
-        }
-        ph ^= 1u << buf;
-        pend &= ~(1u << buf);
+    // Step 0 (thread 0): start the copy for the jump iteration t + LA would
+    // make.  A slot written in the previous iteration is left alone: its
+    // writes are ordered for the copy engine only by a later barrier.
+    if (fc && tid == 0) {
+      const int64_t tt = it + LA;
+      const int b = (int)(tt % NB);
+      bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= A.I_max;
+      int slot_p = 0;
+      if (issue) {
+        slot_p = pick(sRnd[((uint32_t)tt % RB) * 4 + 1], acount);
+        if (sWr[(it - 1) & 7] == slot_p) issue = false;
       }
-      if (tid == 0) {
-        const int slot = pick(rnd[1], acount);
-        const uint32_t bytes = (uint32_t)sl.bytes;
+      uint32_t par = 0;
+      if (issue) {
+        if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
+          if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
+          ph ^= 1u << b;
+          pend &= ~(1u << b);
+        }
+        unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
         uint32_t eb = 0, bb = 0, boff = 0;
         if (!A.energies_in_smem) eb = 16;
         if (!A.bits_in_smem) {
-          const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+          const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot_p * W);
           boff = (uint32_t)(b0 & 15);
           bb = (uint32_t)align_up(boff + 4 * (size_t)W, 16);
         }
         fence_proxy_async_shared();
-        mbar_expect_tx(&sBar[buf], bytes + eb + bb);
-        bulk_g2s(pb, gF + (size_t)slot * sl.bytes, bytes, &sBar[buf]);
-        if (eb)
-          bulk_g2s(pb + sl.bytes, gE + (size_t)slot * 2, 16, &sBar[buf]);
+        mbar_expect_tx(&sBar[b], (uint32_t)sl.bytes + eb + bb);
+        bulk_g2s(pb, gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes, &sBar[b]);
+        if (eb) bulk_g2s(pb + lay.pfE, gE + 2 * (size_t)slot_p, 16, &sBar[b]);
         if (bb)
-          bulk_g2s(pb + sl.bytes + eb,
-                   reinterpret_cast<const unsigned char *>(gBits + (size_t)slot * W) - boff,
-                   bb, &sBar[buf]);
+          bulk_g2s(pb + lay.pfW,
+                   reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
+                   bb, &sBar[b]);
+        par = (ph >> b) & 1u;
+        pend |= 1u << b;
       }
-      pend |= 1u << buf;
+      sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
+      sWr[it & 7] = -1;  // set to the written slot by a flip below
     }
 
     // Phase A: Delta E (Eq. cale) and the parallel trial of every bit.
@@ -445,8 +494,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int p = k * T + tid;
         const int sg = 1 - 2 * (int)xv;
         const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
-        int64_t f1 = (int64_t)(sg * L1[k]) + A.w1 * h;
-        int64_t f2 = (int64_t)(sg * L2[k]) + A.w2 * h;
+        const int64_t e1 = (int64_t)(sg * L1[k]) + A.w1 * h;
+        const int64_t e2 = (int64_t)(sg * L2[k]) + A.w2 * h;
+        int64_t f1 = e1, f2 = e2;
         if (A.escape == 1) {
           f1 -= Eoff;
           f2 -= Eoff;
@@ -461,17 +511,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           const uint32_t w = word_of(c, p & 3);
           acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
         }
+        if (acc && de_smem) sDE[p] = make_longlong2(e1, e2);
       }
       const uint32_t bal = __ballot_sync(kFull, acc);
       if (lane == 0) mask[k * NW + warp] = bal;
+      if (de_smem) {
+        const uint32_t xb = __ballot_sync(kFull, xv != 0);
+        if (lane == 0) xm[k * NW + warp] = xb;
+      }
     }
-    if (warp == NW - 1 && lane < 3) {  // draws of iteration t + 1
-      uint32_t c[4] = {0u, t + 1u, rep, kTagSelect + (uint32_t)lane};
+    if (warp == NW - 1 && lane < 3) {  // draws of iteration t + LA + 1
+      const uint32_t q = t + (uint32_t)LA + 1u;
+      uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
       philox10(c, k0, k1);
-      sRnd[((t + 1u) % 3u) * 4 + lane] = c[0];
+      sRnd[(q % RB) * 4 + lane] = c[0];
     }
     __syncthreads();
-    if (fc && *sFail) break;  // a bulk copy did not complete (uniform exit)
+    if (fc && bc->fail) break;  // a bulk copy did not complete (uniform)
 
     // Phase B: every warp reaches the same decision from shared memory.
     int incl, cnt;
@@ -481,21 +537,35 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       const int ps = warp_mask_select(mask, items, NW, T, lane, incl, cnt,
                                       pick(rnd[0], total));
       const int kk = ps / T;
-      if (ps - kk * T == tid) {  // the owner publishes Delta E of the flip
+      const int rr = ps - kk * T;
+      int64_t dE1, dE2;
+      int sg;
+      if (de_smem) {
+        // Delta E published by the accepted bit, its state bit from the
+        // state ballots of phase A.
+        const longlong2 de = sDE[ps];
+        dE1 = de.x;
+        dE2 = de.y;
+        sg = 1 - 2 * (int)((xm[kk * NW + (rr >> 5)] >> (rr & 31)) & 1u);
+      } else {
+        if (rr == tid) {  // the owner publishes Delta E and its sign
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-          if (k != kk) continue;
-          const int xv = (int)((xmask >> k) & 1u);
-          const int sg = 1 - 2 * xv;
-          const int h = sg * ((own[k] >> 16) - 1 - 2 * xv);
-          bc->dE1 = (int64_t)(sg * L1[k]) + A.w1 * h;
-          bc->dE2 = (int64_t)(sg * L2[k]) + A.w2 * h;
-          bc->sgn = sg;
+          for (int k = 0; k < B; ++k) {
+            if (k != kk) continue;
+            const int xv = (int)((xmask >> k) & 1u);
+            const int g = 1 - 2 * xv;
+            const int h = g * ((own[k] >> 16) - 1 - 2 * xv);
+            bc->dE1 = (int64_t)(g * L1[k]) + A.w1 * h;
+            bc->dE2 = (int64_t)(g * L2[k]) + A.w2 * h;
+            bc->sgn = g;
+          }
         }
+        __syncthreads();
+        dE1 = bc->dE1;
+        dE2 = bc->dE2;
+        sg = bc->sgn;
       }
-      __syncthreads();
-      const int64_t nE1 = E1 + bc->dE1, nE2 = E2 + bc->dE2;
-      const int sg = bc->sgn;
+      const int64_t nE1 = E1 + dE1, nE2 = E2 + dE2;
       const int j = (int)__umulhi((uint32_t)ps, A.magic);
       const int v = ps - j * n;
       // Apply the flip of (j, v) to the owned registers.
@@ -554,18 +624,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (fc) {
           unsigned char *rec = gF + (size_t)target * sl.bytes;
           int2 *rf = reinterpret_cast<int2 *>(rec + sl.fields);
-          uint16_t *rr = reinterpret_cast<uint16_t *>(rec + sl.rc);
+          int32_t *rr = reinterpret_cast<int32_t *>(rec + sl.rc);
 #pragma unroll
           for (int k = 0; k < B; ++k) {
             const int q = k * T + tid;
             if (q >= m) continue;
             rf[q] = make_int2(L1[k], L2[k]);
-            rr[q] = (uint16_t)(own[k] >> 16);
+            rr[q] = own[k] >> 16;
           }
           fence_proxy_async_global();  // later bulk copies read these
+          if (tid == 0) sWr[it & 7] = target;
         }
-        // The next iteration's bulk copy may read this slot.
-        if (fc) __syncthreads();
       }
       E1 = nE1;
       E2 = nE2;
@@ -577,26 +646,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // Alg. 3: jump to a random archive member.
         const int slot = pick(rnd[1], acount);
         if (fc) {
-          if (!mbar_wait(&sBar[buf], (ph >> buf) & 1u)) {
-            failed = true;
-            *sFail = 1;
-          }
-          ph ^= 1u << buf;
-          pend &= ~(1u << buf);
-          const int2 *rf = reinterpret_cast<const int2 *>(pb + sl.fields);
-          const uint16_t *rr = reinterpret_cast<const uint16_t *>(pb + sl.rc);
+          const int b = (int)(it % NB);
+          const unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
+          // The copy for this iteration is usable if it was started for
+          // this slot and no later iteration rewrote that slot.
+          const PfRec rec = sPf[it & 7];
+          bool ok = rec.iter != 0 && rec.slot == slot;
+          for (int64_t x = rec.iter; ok && x < it; ++x)
+            if (sWr[x & 7] == slot) ok = false;
+          const int2 *rf;
+          const int32_t *rr;
+          const uint32_t *wsrc;
           longlong2 se;
-          if (A.energies_in_smem)
+          if (ok) {
+#ifdef MODA_KERNEL_CLOCKS
+            const long long w0 = clock64();
+#endif
+            if (!mbar_wait(&sBar[b], (uint32_t)rec.parity)) bc->fail = 1;
+#ifdef MODA_KERNEL_CLOCKS
+            st_wait += clock64() - w0;
+#endif
+            ++st_pf;
+            if (tid == 0) {
+              ph ^= 1u << b;
+              pend &= ~(1u << b);
+            }
+            rf = reinterpret_cast<const int2 *>(pb + sl.fields);
+            rr = reinterpret_cast<const int32_t *>(pb + sl.rc);
+            se = A.energies_in_smem
+                     ? aE[slot]
+                     : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
+            if (A.bits_in_smem) {
+              wsrc = aBits + (size_t)slot * W;
+            } else {
+              const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+              wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
+            }
+          } else {  // read the record where it is
+            ++st_direct;
+            const unsigned char *recp = gF + (size_t)slot * sl.bytes;
+            rf = reinterpret_cast<const int2 *>(recp + sl.fields);
+            rr = reinterpret_cast<const int32_t *>(recp + sl.rc);
             se = aE[slot];
-          else
-            se = *reinterpret_cast<const longlong2 *>(pb + sl.bytes);
-          const uint32_t *words;
-          if (A.bits_in_smem) {
-            words = aBits + (size_t)slot * W;
-          } else {
-            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
-            words = reinterpret_cast<const uint32_t *>(
-                pb + sl.bytes + (A.energies_in_smem ? 0 : 16) + (b0 & 15));
+            wsrc = aBits + (size_t)slot * W;
           }
           E1 = se.x;
           E2 = se.y;
@@ -608,8 +700,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             const int2 f = rf[q];
             L1[k] = f.x;
             L2[k] = f.y;
-            own[k] = ((int)rr[q] << 16) | (own[k] & 0xFFFF);
-            xmask |= ((words[q >> 5] >> (q & 31)) & 1u) << k;
+            own[k] = (rr[q] << 16) | (own[k] & 0xFFFF);
+            xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
           }
         } else {
           const longlong2 se = aE[slot];
@@ -626,6 +718,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       Eoff += A.beta;
       ++st_off;
     }
+    flip_streak = total > 0 ? flip_streak + 1 : 0;
     if (A.trace != nullptr && tid == 0) {
       int64_t *tr = A.trace + ((size_t)rb * (size_t)A.I_max + (size_t)(it - 1)) * 3;
       tr[0] = E1;
@@ -635,13 +728,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 
   // No bulk copy may be in flight when the block exits.
-  for (int b = 0; b < 2; ++b)
-    if (pend & (1u << b)) {
-      if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) failed = true;
-    }
-  if (failed && tid == 0) atomicExch(A.error, kErrCopyTimeout);
-
+  if (fc && tid == 0) {
+    for (int b = 0; b < NB; ++b)
+      if ((pend >> b) & 1u)
+        if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
+  }
   __syncthreads();
+  if (tid == 0 && bc->fail) atomicExch(A.error, kErrCopyTimeout);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
@@ -659,13 +752,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     for (int e = tid; e < acount * W; e += T) gBits[e] = aBits[e];
   }
   if (tid == 0) {
+    int64_t *st = A.stats + (size_t)kStats * rb;
+    st[0] = st_flip;
+    st[1] = st_jump;
+    st[2] = st_empty;
+    st[3] = st_off;
+    st[4] = st_pf;
+    st[5] = st_direct;
+    st[6] = st_wait;  // cycle counters: builds with MODA_KERNEL_CLOCKS only
+#ifdef MODA_KERNEL_CLOCKS
+    st[7] = clock64() - loop_t0;
+#else
+    st[7] = 0;
+    (void)loop_t0;
+#endif
     A.arch_count[rb] = acount;
     A.E_final[2 * rb] = E1;
     A.E_final[2 * rb + 1] = E2;
-    A.stats[4 * rb + 0] = st_flip;
-    A.stats[4 * rb + 1] = st_jump;
-    A.stats[4 * rb + 2] = st_empty;
-    A.stats[4 * rb + 3] = st_off;
   }
 }
 

@@ -62,6 +62,7 @@ class Params(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("trace", ctypes.c_int32),
         ("field_cache", ctypes.c_int32),
+        ("prefetch", ctypes.c_int32),
     ]
 
 
@@ -173,7 +174,7 @@ class ReplicaResult:
     bits: np.ndarray    # [R, s, W] uint32
     x: np.ndarray       # [R, W] uint32
     E_final: np.ndarray  # [R, 2]
-    stats: np.ndarray   # [R, 4]
+    stats: np.ndarray   # [R, 8] (see moda_read_replica)
 
 
 def unpack_bits(words: np.ndarray, m: int) -> np.ndarray:
@@ -211,7 +212,7 @@ class Run:
             bits=np.zeros((R, s, W), dtype=np.uint32),
             x=np.zeros((R, W), dtype=np.uint32),
             E_final=np.zeros((R, 2), dtype=np.int64),
-            stats=np.zeros((R, 4), dtype=np.int64),
+            stats=np.zeros((R, 8), dtype=np.int64),
         )
         _check(_lib.moda_read_replica(self._h, int(replica), _ptr(out.count), _ptr(out.E),
                                       _ptr(out.bits), _ptr(out.x), _ptr(out.E_final),
@@ -256,13 +257,13 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
                 deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
-                trace: bool = False, field_cache: str = "auto") -> Params:
+                trace: bool = False, field_cache: str = "auto", prefetch: int = 0) -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
-                  int(bool(trace)), FIELD_CACHE[field_cache])
+                  int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch))
 
 
 def anneal(inst: Instance, params: Params | None = None, stream=None, **kw) -> Run:

@@ -189,6 +189,55 @@ void moda_destroy_run(moda_run run);
 /* Thread-local message of the last failed call on this thread. */
 const char *moda_last_error(void);
 
+/* ---- Annealing without device allocation ------------------------------
+ *
+ * The paper has no counterpart: this entry point serves callers that must
+ * not allocate device memory when they anneal -- a serving process that
+ * gives all of its device memory to its own pool, or code whose device
+ * memory belongs to a host framework's allocator -- so cudaMalloc (and any
+ * routine that allocates, torch's included) is off limits to them.
+ *
+ * moda_anneal_noalloc runs the same kernel as moda_anneal on the same
+ * inputs and gives the same results, but allocates nothing: the instance
+ * comes from host arrays (as in moda_create_instance), the results go to
+ * device buffers the caller owns (below), and the kernel's scratch (the
+ * field cache of moda_params.field_cache) plus the instance matrices, the
+ * cooling schedule and the -ln(u) table live in fixed-size device arrays of
+ * the library, held by every GPU that loads it until the process exits.
+ *
+ *   Limits (MODA_EUNSUPPORTED beyond them): n <= 128; replicas * s *
+ *   12 * ceil8(n^2) bytes <= 64 MiB (s = archive size); at most 65,536
+ *   schedule entries before delta reaches delta_f; params.trace = 0.
+ *   params.field_cache and params.prefetch are ignored (the cache is used
+ *   whenever the escape jumps to the archive).
+ *   Shared state: all calls share the library's arrays; two calls whose
+ *   device work overlaps (other streams or host threads) race and give
+ *   wrong results.  Serialise them, e.g. on one stream.
+ *   Set-up: the first call on a device (the device current on the calling
+ *   thread) looks up the arrays' device addresses and uploads the table;
+ *   make that first call before any stream capture.
+ *   Asynchrony: returns once the work is enqueued on cuda_stream; the
+ *   outputs are ready when that stream reaches this point.  The error word
+ *   is set to 0 by the call and to a nonzero code by a device-side failure.
+ */
+typedef struct {
+  int64_t *arch_E;      /* [replicas][s][2] archive energies */
+  uint32_t *arch_bits;  /* [replicas][s][W] archive states, W = ceil(n^2 / 32),
+                           plus 32 spare bytes at the end */
+  int32_t *arch_count;  /* [replicas] archive sizes */
+  uint32_t *x_final;    /* [replicas][W] final states */
+  int64_t *E_final;     /* [replicas][2] their energies */
+  int64_t *stats;       /* [replicas][8] counters as in moda_read_replica */
+  int32_t *error;       /* [1] device status word */
+} moda_device_outputs;
+
+moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
+                                const int16_t *F2, const int16_t *D,
+                                const moda_penalty *pen,
+                                const moda_params *params,
+                                const moda_device_outputs *out,
+                                void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -130,6 +130,10 @@ moda_status device_schedule(DeviceData &dd, double d0, double df, double xi,
 
 }  // namespace
 
+namespace moda {
+void set_last_error(const char *msg) { g_error = msg; }
+}  // namespace moda
+
 struct moda_instance_s {
   int32_t n = 0, m = 0, W = 0;
   int device = 0;

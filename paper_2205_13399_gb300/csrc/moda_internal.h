@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -135,6 +136,10 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
 
 // Bits per thread the kernel is instantiated for.
 bool supported_rounds(int b);
+
+// Sets the thread-local message that moda_last_error() returns.
+void set_last_error(const char *msg);
+inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }
 
 // Launch one block per replica on `stream`.  Returns the launch error.
 cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,

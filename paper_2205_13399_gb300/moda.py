@@ -30,7 +30,7 @@ ABI_FUNCTIONS = [
     "moda_create_instance", "moda_destroy_instance", "moda_instance_info",
     "moda_anneal", "moda_wait", "moda_read_replica", "moda_read_trace",
     "moda_read_archive", "moda_run_elapsed_ms", "moda_destroy_run",
-    "moda_last_error",
+    "moda_last_error", "moda_anneal_noalloc",
 ]
 
 
@@ -76,6 +76,19 @@ class Point(ctypes.Structure):
     ]
 
 
+class DeviceOutputs(ctypes.Structure):
+    """Device output buffers of moda_anneal_noalloc (caller-owned)."""
+    _fields_ = [
+        ("arch_E", ctypes.c_void_p),
+        ("arch_bits", ctypes.c_void_p),
+        ("arch_count", ctypes.c_void_p),
+        ("x_final", ctypes.c_void_p),
+        ("E_final", ctypes.c_void_p),
+        ("stats", ctypes.c_void_p),
+        ("error", ctypes.c_void_p),
+    ]
+
+
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libmoda is not built ({path}); run "
@@ -108,6 +121,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.moda_destroy_run.argtypes = [P]
     lib.moda_last_error.restype = ctypes.c_char_p
     lib.moda_last_error.argtypes = []
+    lib.moda_anneal_noalloc.restype = st
+    lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
+                                        ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
     return lib
 
 
@@ -264,6 +280,27 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
                   int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch))
+
+
+def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,
+                   w=None, **kw) -> None:
+    """``moda_anneal_noalloc``: anneal without any device allocation by the
+    library.  ``outputs`` maps arch_E, arch_bits, arch_count, x_final,
+    E_final, stats and error to caller-owned device buffers (anything with a
+    ``data_ptr()``, e.g. torch tensors, or int addresses) sized as in
+    include/moda.h.  Returns once the work is enqueued on ``stream``."""
+    if params is None:
+        params = make_params(**kw)
+    D = np.ascontiguousarray(np.asarray(D, dtype=np.int16))
+    n = int(D.shape[0])
+    F1 = np.ascontiguousarray(np.asarray(F1, dtype=np.int16))
+    F2 = np.ascontiguousarray(np.asarray(F2, dtype=np.int16))
+    addr = {k: (v if isinstance(v, int) else int(v.data_ptr())) for k, v in outputs.items()}
+    out = DeviceOutputs(addr["arch_E"], addr["arch_bits"], addr["arch_count"], addr["x_final"],
+                        addr["E_final"], addr["stats"], addr["error"])
+    pen = None if w is None else ctypes.byref(Penalty(1, int(w[0]), int(w[1])))
+    _check(_lib.moda_anneal_noalloc(n, _ptr(F1), _ptr(F2), _ptr(D), pen, ctypes.byref(params),
+                                    ctypes.byref(out), _stream_handle(stream)))
 
 
 def anneal(inst: Instance, params: Params | None = None, stream=None, **kw) -> Run:

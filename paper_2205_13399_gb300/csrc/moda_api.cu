@@ -138,6 +138,7 @@ struct moda_instance_s {
   int32_t n = 0, m = 0, W = 0;
   int device = 0;
   int64_t w1 = 0, w2 = 0;
+  int64_t b1 = 0, b2 = 0;  // bounds of the local fields
   std::vector<int32_t> Fs1, Fs2, D;  // host copies
   int32_t *dFs1 = nullptr, *dFs2 = nullptr, *dD = nullptr;
 };
@@ -242,6 +243,8 @@ moda_status moda_create_instance(int32_t n, const int16_t *F1,
     inst->w1 = b1;
     inst->w2 = b2;
   }
+  inst->b1 = b1;
+  inst->b2 = b2;
   cudaGetDevice(&inst->device);
   const size_t bytes = sizeof(int32_t) * nn;
   cudaError_t e = cudaMalloc(&inst->dFs1, bytes);
@@ -309,8 +312,8 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   static const int kRounds[] = {1, 2, 3, 4, 6, 8};
   int T = 0, B = 0;
   if (p->block_threads > 0) {
-    if (p->block_threads % 32 || p->block_threads > moda::kMaxThreads)
-      return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 1024");
+    if (p->block_threads % 32 || p->block_threads > moda::kMaxWorkers)
+      return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 992");
     T = p->block_threads;
     for (int b : kRounds)
       if ((int64_t)b * T >= m) {
@@ -320,7 +323,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     if (!B) return fail(MODA_EUNSUPPORTED, "block_threads too small for n");
   } else {
     for (int b : kRounds)
-      if ((int64_t)b * moda::kMaxThreads >= m) {
+      if ((int64_t)b * moda::kMaxWorkers >= m) {
         B = b;
         break;
       }
@@ -349,6 +352,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
     want_cache = cache_bytes <= free_b / 10 * 6;
   }
+  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Shared-memory placement, best first: the field cache (if wanted), the
   // archive energies and states on chip (then energies only, then
   // neither), Delta E published in shared memory, and the prefetch
@@ -362,7 +366,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     for (int opt = 0; opt < 3 && !placed; ++opt)
       for (int de = 1; de >= 0 && !placed; --de)
         for (int la = c ? la_hi : 0; la >= (c ? la_lo : 0) && !placed; --la) {
-          const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1};
+          const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1, narrow};
           const moda::SmemLayout l =
               moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, pl);
           if ((int64_t)l.total <= dev_smem) {
@@ -468,7 +472,7 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->error, 0, sizeof(int32_t), r->stream);
   if (e == cudaSuccess) e = cudaEventRecord(r->start, r->stream);
-  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, lay.total, r->stream);
+  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, place.narrow, lay.total, r->stream);
   if (e == cudaSuccess) e = cudaEventRecord(r->stop, r->stream);
   if (e != cudaSuccess) {
     free_run_buffers(r);

@@ -1,5 +1,6 @@
-// Internal declarations shared by the host library (moda_api.cu) and the
-// annealing kernels (moda_kernel.cu).  Not part of the public C ABI.
+// Internal declarations shared by the host library (moda_api.cu,
+// moda_noalloc.cu) and the annealing kernel (moda_kernel.cu).  Not part of
+// the public C ABI.
 #pragma once
 
 #include <cstddef>
@@ -11,7 +12,8 @@
 namespace moda {
 
 constexpr int kMaxN = 128;          // n <= 128: a bit index fits (i << 8) | u
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 1024;   // threads of a block, control warp included
+constexpr int kMaxWorkers = kMaxThreads - 32;
 constexpr int kTableSize = 65536;   // -ln(u) table, u quantised to 2^-16
 constexpr int kMaxLookahead = 3;    // field-cache prefetch distance
 constexpr int kStats = 8;           // counters per replica (see moda.h)
@@ -41,8 +43,8 @@ __host__ __device__ inline SlotLayout slot_layout(int m) {
   return S;
 }
 
-// Everything one launch of the single-instance annealing kernel needs.
-// All pointers are device pointers.
+// Everything one launch of the annealing kernel needs.  All pointers are
+// device pointers.
 struct AnnealArgs {
   int32_t n, m, W;          // W = ceil(m / 32) words per bit vector
   int32_t s;                // archive capacity
@@ -72,19 +74,13 @@ struct AnnealArgs {
   unsigned char *fcache;
   // outputs, one block per replica of this launch
   int64_t *arch_E;          // [R][s][2]
-  uint32_t *arch_bits;      // [R][s][W]
+  uint32_t *arch_bits;      // [R][s][W] (+ 32 spare bytes)
   int32_t *arch_count;      // [R]
   uint32_t *x_final;        // [R][W]
   int64_t *E_final;         // [R][2]
   int64_t *stats;           // [R][kStats]
   int64_t *trace;           // [R][I_max][3] or nullptr
   int32_t *error;           // device status word, kErrNone = fine
-};
-
-// Byte offsets of the shared-memory carve-up of one annealing block.
-struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, RC, red, bc, init, mbar, dE, pf, pf_slot,
-      pfE, pfW, archE, archB, total;
 };
 
 // Placement choices of one launch (decided on the host).
@@ -94,27 +90,37 @@ struct Placement {
   bool field_cache;       // jumps reload cached fields
   int lookahead;          // prefetch distance, iterations
   bool de_in_smem;        // accepted bits publish Delta E in shared memory
+  bool narrow;            // Delta E fits int32 (kernel variant)
+};
+
+// Byte offsets of the shared-memory carve-up of one annealing block with
+// `workers` bit-owning threads (plus one control warp).
+struct SmemLayout {
+  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, dec, init, mbar, dE, pf,
+      pf_slot, pfE, pfW, archE, archB, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
-                                                  int threads, int rounds,
+                                                  int workers, int rounds,
                                                   const Placement &P) {
   SmemLayout L;
   size_t o = 0;
   const size_t nn = (size_t)n * n;
-  const size_t items = (size_t)rounds * (threads / 32);
-  const size_t bits = (size_t)rounds * threads;
+  const size_t items = (size_t)rounds * (workers / 32);
+  const size_t bits = (size_t)rounds * workers;
   L.Fs = o;    o = align_up(o + 8 * nn, 16);                 // int2 pairs
   L.D = o;     o = align_up(o + 4 * nn, 16);
   L.mask = o;  o = align_up(o + 4 * 4 * items, 16);  // accept, state x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
   L.rnd = o;   o = align_up(o + (kMaxLookahead + 3) * 4 * 4, 16);
+  L.sch = o;   o = align_up(o + 2 * 32, 16);                 // two entries
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
+  L.dec = o;   o = align_up(o + 48, 16);
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
-  L.dE = o;    if (P.de_in_smem) o = align_up(o + 16 * bits, 16);
+  L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits, 16);
   // Prefetch buffers (lookahead + 2: the one being filled, the one of the
   // current iteration and the one a lagging warp may still read): one
   // field-cache record, then the member's energies and the 16-byte-aligned
@@ -134,15 +140,24 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   return L;
 }
 
+// True when |Delta E_1| + |Delta E_2| stays below 2^31 for every state:
+// |Delta E_k| <= B_k + w_k (2n + 1), B_k the bound of the fields.
+inline bool narrow_ok(int n, int64_t b1, int64_t b2, int64_t w1, int64_t w2) {
+  const long double e1 = (long double)b1 + (long double)w1 * (2 * n + 1);
+  const long double e2 = (long double)b2 + (long double)w2 * (2 * n + 1);
+  return e1 + e2 < 2147483647.0L;
+}
+
 // Bits per thread the kernel is instantiated for.
 bool supported_rounds(int b);
+
+// Launch one block of `workers` + 32 threads per replica on `stream`.
+cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
+                          int rounds, bool narrow, size_t smem_bytes,
+                          cudaStream_t stream);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);
 inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }
-
-// Launch one block per replica on `stream`.  Returns the launch error.
-cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,
-                          int rounds, size_t smem_bytes, cudaStream_t stream);
 
 }  // namespace moda

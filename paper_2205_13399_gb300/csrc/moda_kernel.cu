@@ -2,10 +2,10 @@
 // Alg. 3 of arXiv 2205.13399, for the bi-objective QAP: one thread block
 // runs one replica for all I_max iterations, its state held on chip.
 //
-// State of a replica.  Thread `tid` of a T-thread block owns the bits
-// p = k*T + tid, k < B ("rounds"), of the n*n-bit two-way one-hot state
-// (bit p = i*n + u: facility i at location u, Sec. 2.2) and keeps in
-// registers, per owned bit:
+// A block is Tw worker threads plus one control warp.  Worker `tid` owns
+// the bits p = k*Tw + tid, k < B ("rounds"), of the n*n-bit two-way
+// one-hot state (bit p = i*n + u: facility i at location u, Sec. 2.2) and
+// keeps in registers, per owned bit:
 //   x_p                 (a bit of `xmask`),
 //   rc_p = R_i + C_u    (row count of facility i plus column count of u),
 //   L1_p, L2_p          cost-only local fields
@@ -21,25 +21,29 @@
 // column, s = +1 when the bit turns on.
 //
 // One iteration t (Alg. 3):
-//   0  (field cache on, replica not in a run of flips) thread 0 starts a
-//      bulk copy (TMA, completion on an mbarrier) of the cached fields of
-//      the member that a jump at iteration t + lookahead would land on: its
-//      draw and |A| are known already; the copy is not used if that member
-//      is rewritten before then.
-//   A  every thread: Delta E and the parallel trial of its bits; warp
-//      ballots give accept masks in (round, warp, lane) order = ascending
-//      bit order; accepted bits publish Delta E.  One warp draws a later
-//      iteration's select / restart / exploit words meanwhile.
+//   workers   Delta E and the parallel trial of their bits; warp ballots
+//             give accept masks in (round, warp, lane) order = ascending
+//             bit order; accepted bits publish Delta E.
+//   control   meanwhile: the draws of a later iteration, the schedule
+//             entry of the next one, and (field cache on, replica not in a
+//             run of flips) a bulk copy (TMA, mbarrier) of the cached
+//             fields of the member that a jump at t + lookahead would land
+//             on -- its draw and |A| are known already; the copy is not
+//             used if that member is rewritten before then.
 //   -- barrier --
-//   B  every warp, redundantly: count the accepted bits and rank-select one.
-//      Flip:    every thread applies it to its registers and ballots "x
-//               dominates slot y" -- barrier -- every warp picks the target
-//               slot (Alg. 4 / Alg. 5) and stores its part of x (and of the
-//               fields, into the cache).
-//      No flip: jump to a random archive member: take the prefetched fields
-//               (or read them from the cache, or rebuild them as
-//               L_k = Fs_k (X D)), or raise the energy offset by beta.
+//   control   counts the accepted bits, rank-selects one ("one flip at
+//             random", ascending bit order) or settles the jump, and
+//             publishes the decision.
+//   -- barrier --
+//   all       Flip: workers apply it to their registers and ballot "x
+//             dominates slot y" -- barrier -- every warp picks the target
+//             slot (Alg. 4 / Alg. 5); workers store their part of x (and of
+//             the fields, into the cache).
+//             Jump: workers take the member's fields from the prefetch
+//             buffer, the cache, or rebuild them as L_k = Fs_k (X D).
+//             Otherwise: raise the energy offset by beta.
 #include <cstdint>
+#include <type_traits>
 
 #include "moda_internal.h"
 
@@ -166,10 +170,10 @@ __device__ __forceinline__ int warp_mask_total(const uint32_t *masks,
   return __shfl_sync(kFull, incl, 31);
 }
 
-// Flat index round*T + warp*32 + lane of the r-th set bit (r < total), in
+// Flat index round*Tw + warp*32 + lane of the r-th set bit (r < total), in
 // every lane.
 __device__ __forceinline__ int warp_mask_select(const uint32_t *masks,
-                                                int items, int nw, int T,
+                                                int items, int nw, int Tw,
                                                 int lane, int incl, int cnt,
                                                 int r) {
   const int per = (items + 31) >> 5;
@@ -185,7 +189,7 @@ __device__ __forceinline__ int warp_mask_select(const uint32_t *masks,
       if (rr < pc) {
         const int k = it / nw;
         const int w = it - k * nw;
-        found = k * T + w * 32 + nth_set_bit(mk, rr);
+        found = k * Tw + w * 32 + nth_set_bit(mk, rr);
         break;
       }
       rr -= pc;
@@ -208,9 +212,21 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red,
 }
 
 struct Bcast {
-  int64_t dE1, dE2;  // Delta E of the flipped bit
+  int64_t dE1, dE2;  // Delta E of the flipped bit (owner-published path)
   int32_t sgn;       // +1: the bit turns on, -1: off
   int32_t fail;      // a bulk copy did not complete
+};
+
+// The control warp's decision for one iteration.
+enum : int32_t { kNone = 0, kFlip = 1, kJump = 2 };
+struct Decision {
+  int32_t kind;
+  int32_t ps;      // flipped bit
+  int32_t sgn;     // +1: it turns on, -1: off (0: the owner publishes)
+  int32_t slot;    // archive slot jumped to
+  int32_t buf;     // prefetch buffer holding it, -1: read the cache record
+  int32_t parity;  // that buffer's mbarrier phase parity
+  int64_t dE1, dE2;
 };
 
 // Prefetch bookkeeping entry for one target iteration.
@@ -221,25 +237,37 @@ struct PfRec {
   int32_t pad;
 };
 
-template <int B>
+struct SchEntry {
+  double delta;
+  int64_t lo, hi;
+  int64_t pad;
+};
+
+// NARROW: Delta E and the acceptance penalty in int32 (the host checked
+// |Delta E_1| + |Delta E_2| < 2^31 for every state); otherwise int64.
+template <int B, bool NARROW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
+  using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = A.n, m = A.m, W = A.W, s = A.s;
   const int T = blockDim.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5, NW = T >> 5;
-  const int items = B * NW;
+  const int Tw = T - 32;                 // worker threads
+  const int lane = tid & 31, warp = tid >> 5, NWB = Tw >> 5;
+  const bool worker = tid < Tw;
+  const bool control = !worker;          // the last warp
+  const int items = B * NWB;
   const bool fc = A.fcache != nullptr;
   const bool de_smem = A.de_in_smem != 0;
-  const int LA = A.lookahead;           // prefetch distance
+  const int LA = A.lookahead;            // prefetch distance
   // Prefetch buffers: target iteration tt uses buffer tt % NB.  The copy
   // for t + LA starts before the barrier of iteration t, while a lagging
   // warp may still read the buffer of t - 1, so NB = LA + 2.
   const int NB = LA + 2;
   const uint32_t RB = (uint32_t)LA + 3;  // draw ring: t % RB
   const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
-                    de_smem};
-  const SmemLayout lay = smem_layout(n, m, W, s, T, B, P);
+                    de_smem, NARROW};
+  const SmemLayout lay = smem_layout(n, m, W, s, Tw, B, P);
   const SlotLayout sl = slot_layout(m);
   int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
   int32_t *sD = reinterpret_cast<int32_t *>(smem + lay.D);
@@ -247,17 +275,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   uint32_t *sMask = reinterpret_cast<uint32_t *>(smem + lay.mask);
   uint32_t *sAmask = reinterpret_cast<uint32_t *>(smem + lay.amask);
   uint32_t *sRnd = reinterpret_cast<uint32_t *>(smem + lay.rnd);
+  SchEntry *sSch = reinterpret_cast<SchEntry *>(smem + lay.sch);
   // Row and column counts of the last rebuilt state, two buffers used in
   // turn (rebuild q fills buffer q % 2 and clears the other one).
   int32_t *sRC = reinterpret_cast<int32_t *>(smem + lay.RC);
   int64_t *sRed = reinterpret_cast<int64_t *>(smem + lay.red);
   Bcast *bc = reinterpret_cast<Bcast *>(smem + lay.bc);
+  Decision *dec = reinterpret_cast<Decision *>(smem + lay.dec);
   uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
   uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
-  longlong2 *sDE = reinterpret_cast<longlong2 *>(smem + lay.dE);
-  // Prefetch bookkeeping (after initialisation; shares the reduction
-  // space): sPf[target iteration % 8], and sWr[iteration % 8] = the archive
-  // slot that iteration wrote (-1 = none).
+  dE_t *sDE = reinterpret_cast<dE_t *>(smem + lay.dE);  // [bits][2]
+  // Prefetch bookkeeping of the control warp (after initialisation; shares
+  // the reduction space): sPf[target iteration % 8], and sWr[iteration % 8]
+  // = the archive slot that iteration wrote (-1 = none).
   PfRec *sPf = reinterpret_cast<PfRec *>(smem + lay.red);
   int32_t *sWr = reinterpret_cast<int32_t *>(smem + lay.red + 8 * sizeof(PfRec));
 
@@ -280,32 +310,37 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     sD[e] = A.D[e];
   }
   for (int e = tid; e < 4 * n; e += T) sRC[e] = 0;
-  if (tid == 0) {
-    bc->fail = 0;
-    if (fc) {
-      for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
-      fence_mbar_init();
+  if (control) {
+    if (lane == 0) {
+      bc->fail = 0;
+      if (fc) {
+        for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
+        fence_mbar_init();
+      }
+      const SchEntry e1{A.sch_delta[0], A.sch_lo[0], A.sch_hi[0], 0};
+      sSch[1] = e1;  // iteration 1
     }
-  }
-  // Draws (select, restart, exploit) of iteration t live in sRnd[t % RB];
-  // they are drawn LA + 1 iterations ahead.
-  if (warp == NW - 1 && lane < 3) {
-    for (uint32_t q = 1; q <= (uint32_t)LA + 1; ++q) {
-      uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
-      philox10(c, k0, k1);
-      sRnd[(q % RB) * 4 + lane] = c[0];
+    // Draws (select, restart, exploit) of iteration t live in sRnd[t % RB];
+    // they are drawn LA + 1 iterations ahead.
+    if (lane < 3) {
+      for (uint32_t q = 1; q <= (uint32_t)LA + 1; ++q) {
+        uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
+        philox10(c, k0, k1);
+        sRnd[(q % RB) * 4 + lane] = c[0];
+      }
     }
   }
 
-  // Own bit k (valid when k*T + tid < m): own[k] packs facility i (bits
-  // 8..15), location u (bits 0..7) and rc = R_i + C_u (bits 16..31).
+  // Own bit k is valid when worker && k*Tw + tid < m; own[k] packs facility
+  // i (bits 8..15), location u (bits 0..7) and rc = R_i + C_u (16..31).
   int own[B];
   int32_t L1[B], L2[B];
   uint32_t xmask = 0;
+  auto valid = [&](int k) { return worker && k * Tw + tid < m; };
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    const int p = k * T + tid;
-    own[k] = p < m ? (((p / n) << 8) | (p % n)) : 0;
+    const int p = k * Tw + tid;
+    own[k] = valid(k) ? (((p / n) << 8) | (p % n)) : 0;
     L1[k] = 0;
     L2[k] = 0;
   }
@@ -313,22 +348,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // of word (p / 32) % 4 of the draw (p / 128, 0, replica, init).
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    if (k * T + tid >= m) continue;
-    const int p = k * T + tid;
+    if (!valid(k)) continue;
+    const int p = k * Tw + tid;
     uint32_t c[4] = {(uint32_t)p >> 7, 0u, rep, kTagInit};
     philox10(c, k0, k1);
     xmask |= ((word_of(c, (p >> 5) & 3) >> (p & 31)) & 1u) << k;
   }
+  if (worker) {
 #pragma unroll
-  for (int k = 0; k < B; ++k) {
-    const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
-    if (lane == 0 && k * NW + warp < W) sInit[k * NW + warp] = wv;
+    for (int k = 0; k < B; ++k) {
+      const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+      if (lane == 0 && k * NWB + warp < W) sInit[k * NWB + warp] = wv;
+    }
   }
   __syncthreads();
 
   // Fields, counts and owned bits of the state held in `words`, in two
   // passes around one barrier: (1) M = X * D (M_ju = sum_v x_jv d_vu) and
-  // the row / column counts into shared memory; (2) every thread forms
+  // the row / column counts into shared memory; (2) every worker forms
   // L_k[(i,u)] = sum_j Fs^k_ij M_ju for its own bits.  Both passes are
   // exact int32 arithmetic (the instance check bounds every field).
   auto rebuild = [&](const uint32_t *words) {
@@ -357,8 +394,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     xmask = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      if (k * T + tid >= m) continue;
-      const int q = k * T + tid;
+      if (!valid(k)) continue;
+      const int q = k * Tw + tid;
       xmask |= ((words[q >> 5] >> (q & 31)) & 1u) << k;
     }
     __syncthreads();
@@ -366,7 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     for (int e = tid; e < 2 * n; e += T) sRC[(1 - rc_buf) * 2 * n + e] = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      if (k * T + tid >= m) continue;
+      if (!valid(k)) continue;
       const int i = (own[k] >> 8) & 255, u = own[k] & 255;
       int32_t a1 = 0, a2 = 0;
       const int2 *frow = sFs + i * n;  // Fs symmetric: row i = column i
@@ -392,7 +429,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     int64_t s1 = 0, s2 = 0, gp = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      if (k * T + tid >= m || !((xmask >> k) & 1u)) continue;
+      if (!valid(k) || !((xmask >> k) & 1u)) continue;
       s1 += L1[k];
       s2 += L2[k];
     }
@@ -400,9 +437,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       const int64_t dr = 1 - sRC[e], dc = 1 - sRC[n + e];
       gp += dr * dr + dc * dc;
     }
-    s1 = block_sum(s1, sRed, lane, warp, NW);
-    s2 = block_sum(s2, sRed, lane, warp, NW);
-    gp = block_sum(gp, sRed, lane, warp, NW);
+    s1 = block_sum(s1, sRed, lane, warp, T >> 5);
+    s2 = block_sum(s2, sRed, lane, warp, T >> 5);
+    gp = block_sum(gp, sRed, lane, warp, T >> 5);
     E1 = s1 / 2 + A.w1 * (gp / 2);
     E2 = s2 / 2 + A.w2 * (gp / 2);
   }
@@ -416,17 +453,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int acount = 0;
   uint32_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
   uint32_t st_pf = 0, st_direct = 0;
-  long long st_wait = 0, loop_t0 = 0;
-#ifdef MODA_KERNEL_CLOCKS
-  loop_t0 = clock64();
-#endif
   int flip_streak = 0;  // consecutive flip iterations: no prefetch while hot
-  // Thread 0's copy bookkeeping: buffer b has a copy in flight when
+  // Control lane 0's copy bookkeeping: buffer b has a copy in flight when
   // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
   uint32_t pend = 0, ph = 0;
-  // Schedule entries, loaded one iteration ahead.
-  double delta_n = A.sch_delta[0];
-  int64_t lo_n = A.sch_lo[0], hi_n = A.sch_hi[0];
 
   for (int64_t it = 1; it <= A.I_max; ++it) {
     const uint32_t t = (uint32_t)it;
@@ -434,121 +464,164 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     uint32_t *mask = sMask + buf * items;        // accept ballots
     uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
     const uint32_t *rnd = sRnd + (t % RB) * 4;
-    const double delta = delta_n;
-    const int64_t lo = lo_n, hi = hi_n;
-    {
-      const int sn = (int)((it + 1 <= A.nsched ? it + 1 : (int64_t)A.nsched) - 1);
-      delta_n = A.sch_delta[sn];
-      lo_n = A.sch_lo[sn];
-      hi_n = A.sch_hi[sn];
-    }
 
-    // Step 0 (thread 0): start the copy for the jump iteration t + LA would
-    // make.  A slot written in the previous iteration is left alone: its
-    // writes are ordered for the copy engine only by a later barrier.
-    if (fc && tid == 0) {
-      const int64_t tt = it + LA;
-      const int b = (int)(tt % NB);
-      bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= A.I_max;
-      int slot_p = 0;
-      if (issue) {
-        slot_p = pick(sRnd[((uint32_t)tt % RB) * 4 + 1], acount);
-        if (sWr[(it - 1) & 7] == slot_p) issue = false;
-      }
-      uint32_t par = 0;
-      if (issue) {
-        if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
-          if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
-          ph ^= 1u << b;
-          pend &= ~(1u << b);
-        }
-        unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
-        uint32_t eb = 0, bb = 0, boff = 0;
-        if (!A.energies_in_smem) eb = 16;
-        if (!A.bits_in_smem) {
-          const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot_p * W);
-          boff = (uint32_t)(b0 & 15);
-          bb = (uint32_t)align_up(boff + 4 * (size_t)W, 16);
-        }
-        fence_proxy_async_shared();
-        mbar_expect_tx(&sBar[b], (uint32_t)sl.bytes + eb + bb);
-        bulk_g2s(pb, gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes, &sBar[b]);
-        if (eb) bulk_g2s(pb + lay.pfE, gE + 2 * (size_t)slot_p, 16, &sBar[b]);
-        if (bb)
-          bulk_g2s(pb + lay.pfW,
-                   reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
-                   bb, &sBar[b]);
-        par = (ph >> b) & 1u;
-        pend |= 1u << b;
-      }
-      sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
-      sWr[it & 7] = -1;  // set to the written slot by a flip below
-    }
-
-    // Phase A: Delta E (Eq. cale) and the parallel trial of every bit.
+    if (worker) {
+      // ---- workers: Delta E (Eq. cale) and the parallel trial ----------
+      const SchEntry se = sSch[buf];
+      const double delta = se.delta;
+      const dE_t lo = NARROW ? (dE_t)(se.lo < 2147483647ll ? se.lo : 2147483647ll) : (dE_t)se.lo;
+      const dE_t hi = NARROW ? (dE_t)(se.hi < 2147483647ll ? se.hi : 2147483647ll) : (dE_t)se.hi;
+      const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      bool acc = false;
-      const uint32_t xv = (xmask >> k) & 1u;
-      if (k * T + tid < m) {
-        const int p = k * T + tid;
-        const int sg = 1 - 2 * (int)xv;
-        const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
-        const int64_t e1 = (int64_t)(sg * L1[k]) + A.w1 * h;
-        const int64_t e2 = (int64_t)(sg * L2[k]) + A.w2 * h;
-        int64_t f1 = e1, f2 = e2;
-        if (A.escape == 1) {
-          f1 -= Eoff;
-          f2 -= Eoff;
+      for (int k = 0; k < B; ++k) {
+        bool acc = false;
+        const uint32_t xv = (xmask >> k) & 1u;
+        if (k * Tw + tid < m) {
+          const int p = k * Tw + tid;
+          const int sg = 1 - 2 * (int)xv;
+          const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
+          const dE_t e1 = (dE_t)(sg * L1[k]) + (dE_t)A.w1 * (dE_t)h;
+          const dE_t e2 = (dE_t)(sg * L2[k]) + (dE_t)A.w2 * (dE_t)h;
+          dE_t a1, a2;
+          if (A.escape == 1) {  // the offset lowers Delta E (Alg. 1)
+            a1 = e1 > off ? e1 - off : 0;
+            a2 = e2 > off ? e2 - off : 0;
+          } else {
+            a1 = e1 > 0 ? e1 : 0;
+            a2 = e2 > 0 ? e2 : 0;
+          }
+          const dE_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
+          if (a <= lo) {
+            acc = true;
+          } else if (a <= hi) {
+            uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
+            philox10(c, k0, k1);
+            const uint32_t w = word_of(c, p & 3);
+            acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
+          }
+          if (acc && de_smem) {
+            sDE[2 * p] = e1;
+            sDE[2 * p + 1] = e2;
+          }
         }
-        const int64_t a1 = f1 > 0 ? f1 : 0, a2 = f2 > 0 ? f2 : 0;
-        const int64_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
-        if (a <= lo) {
-          acc = true;
-        } else if (a <= hi) {
-          uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
-          philox10(c, k0, k1);
-          const uint32_t w = word_of(c, p & 3);
-          acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
+        const uint32_t bal = __ballot_sync(kFull, acc);
+        if (lane == 0) mask[k * NWB + warp] = bal;
+        if (de_smem) {
+          const uint32_t xb = __ballot_sync(kFull, xv != 0);
+          if (lane == 0) xm[k * NWB + warp] = xb;
         }
-        if (acc && de_smem) sDE[p] = make_longlong2(e1, e2);
       }
-      const uint32_t bal = __ballot_sync(kFull, acc);
-      if (lane == 0) mask[k * NW + warp] = bal;
-      if (de_smem) {
-        const uint32_t xb = __ballot_sync(kFull, xv != 0);
-        if (lane == 0) xm[k * NW + warp] = xb;
+    } else {
+      // ---- control warp: schedule, draws, prefetch ----------------------
+      SchEntry nx{};
+      if (lane == 31) {  // schedule entry of iteration t + 1
+        const int sn = (int)((it + 1 <= A.nsched ? it + 1 : (int64_t)A.nsched) - 1);
+        nx.delta = A.sch_delta[sn];
+        nx.lo = A.sch_lo[sn];
+        nx.hi = A.sch_hi[sn];
       }
+      if (lane < 3) {  // draws of iteration t + LA + 1
+        const uint32_t q = t + (uint32_t)LA + 1u;
+        uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
+        philox10(c, k0, k1);
+        sRnd[(q % RB) * 4 + lane] = c[0];
+      }
+      if (fc && lane == 0) {
+        // Copy for the jump iteration t + LA would make.  A slot written in
+        // the previous iteration is left alone: its writes are ordered for
+        // the copy engine only by a later barrier.
+        const int64_t tt = it + LA;
+        const int b = (int)(tt % NB);
+        bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= A.I_max;
+        int slot_p = 0;
+        if (issue) {
+          slot_p = pick(sRnd[((uint32_t)tt % RB) * 4 + 1], acount);
+          if (sWr[(it - 1) & 7] == slot_p) issue = false;
+        }
+        uint32_t par = 0;
+        if (issue) {
+          if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
+            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
+            ph ^= 1u << b;
+            pend &= ~(1u << b);
+          }
+          unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
+          uint32_t eb = 0, bb = 0, boff = 0;
+          if (!A.energies_in_smem) eb = 16;
+          if (!A.bits_in_smem) {
+            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot_p * W);
+            boff = (uint32_t)(b0 & 15);
+            bb = (uint32_t)align_up(boff + 4 * (size_t)W, 16);
+          }
+          fence_proxy_async_shared();
+          mbar_expect_tx(&sBar[b], (uint32_t)sl.bytes + eb + bb);
+          bulk_g2s(pb, gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes, &sBar[b]);
+          if (eb) bulk_g2s(pb + lay.pfE, gE + 2 * (size_t)slot_p, 16, &sBar[b]);
+          if (bb)
+            bulk_g2s(pb + lay.pfW,
+                     reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
+                     bb, &sBar[b]);
+          par = (ph >> b) & 1u;
+          pend |= 1u << b;
+        }
+        sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
+        sWr[it & 7] = -1;  // set to the written slot by a flip below
+      }
+      if (lane == 31) sSch[1 - buf] = nx;
     }
-    if (warp == NW - 1 && lane < 3) {  // draws of iteration t + LA + 1
-      const uint32_t q = t + (uint32_t)LA + 1u;
-      uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
-      philox10(c, k0, k1);
-      sRnd[(q % RB) * 4 + lane] = c[0];
+    __syncthreads();
+
+    // ---- control warp: the decision ------------------------------------
+    if (control) {
+      int incl, cnt;
+      const int total = warp_mask_total(mask, items, lane, incl, cnt);
+      Decision d{kNone, 0, 0, 0, -1, 0, 0, 0};
+      if (total > 0) {
+        d.kind = kFlip;
+        d.ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, cnt, pick(rnd[0], total));
+        if (de_smem) {
+          const int kk = d.ps / Tw, rr = d.ps - kk * Tw;
+          d.dE1 = (int64_t)sDE[2 * d.ps];
+          d.dE2 = (int64_t)sDE[2 * d.ps + 1];
+          d.sgn = 1 - 2 * (int)((xm[kk * NWB + (rr >> 5)] >> (rr & 31)) & 1u);
+        }
+      } else if (A.escape == 0 && acount > 0) {
+        d.kind = kJump;
+        d.slot = pick(rnd[1], acount);
+        if (fc) {
+          // The copy for this iteration is usable if it was started for
+          // this slot and no later iteration rewrote that slot.
+          const PfRec rec = sPf[it & 7];
+          bool ok = rec.iter != 0 && rec.slot == d.slot;
+          for (int64_t x = rec.iter; ok && x < it; ++x)
+            if (sWr[x & 7] == d.slot) ok = false;
+          if (ok) {
+            const int b = (int)(it % NB);
+            if (!mbar_wait(&sBar[b], (uint32_t)rec.parity)) bc->fail = 1;
+            if (lane == 0) {
+              ph ^= 1u << b;
+              pend &= ~(1u << b);
+            }
+            d.buf = b;
+            d.parity = rec.parity;
+          }
+        }
+      }
+      if (lane == 0) *dec = d;
     }
     __syncthreads();
     if (fc && bc->fail) break;  // a bulk copy did not complete (uniform)
 
-    // Phase B: every warp reaches the same decision from shared memory.
-    int incl, cnt;
-    const int total = warp_mask_total(mask, items, lane, incl, cnt);
+    // ---- all: carry out the decision ------------------------------------
+    const Decision d = *dec;
     int64_t event = INT64_MIN;
-    if (total > 0) {
-      const int ps = warp_mask_select(mask, items, NW, T, lane, incl, cnt,
-                                      pick(rnd[0], total));
-      const int kk = ps / T;
-      const int rr = ps - kk * T;
-      int64_t dE1, dE2;
-      int sg;
-      if (de_smem) {
-        // Delta E published by the accepted bit, its state bit from the
-        // state ballots of phase A.
-        const longlong2 de = sDE[ps];
-        dE1 = de.x;
-        dE2 = de.y;
-        sg = 1 - 2 * (int)((xm[kk * NW + (rr >> 5)] >> (rr & 31)) & 1u);
-      } else {
-        if (rr == tid) {  // the owner publishes Delta E and its sign
+    if (d.kind == kFlip) {
+      const int ps = d.ps;
+      int64_t dE1 = d.dE1, dE2 = d.dE2;
+      int sg = d.sgn;
+      if (!de_smem) {
+        const int kk = ps / Tw;
+        if (ps - kk * Tw == tid) {  // the owner publishes Delta E and its sign
 #pragma unroll
           for (int k = 0; k < B; ++k) {
             if (k != kk) continue;
@@ -568,32 +641,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       const int64_t nE1 = E1 + dE1, nE2 = E2 + dE2;
       const int j = (int)__umulhi((uint32_t)ps, A.magic);
       const int v = ps - j * n;
-      // Apply the flip of (j, v) to the owned registers.
-#pragma unroll
-      for (int k = 0; k < B; ++k) {
-        if (k * T + tid >= m) continue;
-        const int i = (own[k] >> 8) & 255, u = own[k] & 255;
-        const int2 f = sFs[j * n + i];
-        const int32_t d = sg * sD[v * n + u];
-        L1[k] += f.x * d;
-        L2[k] += f.y * d;
-        own[k] += (sg * ((i == j) + (u == v))) * 65536;
-        if (k * T + tid == ps) xmask ^= 1u << k;
-      }
-      // Archive: ballots of "x dominates slot y" in slot order, and (for
-      // the exploitative update) whether some member dominates x.
       int anyd = 0;
+      if (worker) {
+        // Apply the flip of (j, v) to the owned registers.
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        const int y = k * T + tid;
-        bool dom = false;
-        if (y < acount) {
-          const longlong2 ye = aE[y];
-          dom = dominates(nE1, nE2, ye.x, ye.y);
-          if (dominates(ye.x, ye.y, nE1, nE2)) anyd = 1;
+        for (int k = 0; k < B; ++k) {
+          if (k * Tw + tid >= m) continue;
+          const int i = (own[k] >> 8) & 255, u = own[k] & 255;
+          const int2 f = sFs[j * n + i];
+          const int32_t dd = sg * sD[v * n + u];
+          L1[k] += f.x * dd;
+          L2[k] += f.y * dd;
+          own[k] += (sg * ((i == j) + (u == v))) * 65536;
+          if (k * Tw + tid == ps) xmask ^= 1u << k;
         }
-        const uint32_t bal = __ballot_sync(kFull, dom);
-        if (lane == 0) sAmask[k * NW + warp] = bal;
+        // Archive: ballots of "x dominates slot y" in slot order, and (for
+        // the exploitative update) whether some member dominates x.
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int y = k * Tw + tid;
+          bool dom = false;
+          if (y < acount) {
+            const longlong2 ye = aE[y];
+            dom = dominates(nE1, nE2, ye.x, ye.y);
+            if (dominates(ye.x, ye.y, nE1, nE2)) anyd = 1;
+          }
+          const uint32_t bal = __ballot_sync(kFull, dom);
+          if (lane == 0) sAmask[k * NWB + warp] = bal;
+        }
       }
       anyd = __syncthreads_or(anyd);
       int aincl, acnt;
@@ -602,38 +677,41 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       if (A.archive == 0) {
         // Alg. 4: replace the first dominated member, else append.
         if (nb > 0)
-          target = warp_mask_select(sAmask, items, NW, T, lane, aincl, acnt, 0);
+          target = warp_mask_select(sAmask, items, NWB, Tw, lane, aincl, acnt, 0);
         else if (acount < s)
           target = acount++;
       } else if (!anyd) {
         // Alg. 5: replace a random dominated member, else append.
         if (nb > 0)
-          target = warp_mask_select(sAmask, items, NW, T, lane, aincl, acnt,
+          target = warp_mask_select(sAmask, items, NWB, Tw, lane, aincl, acnt,
                                     pick(rnd[2], nb));
         else if (acount < s)
           target = acount++;
       }
       if (target >= 0) {
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-          const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
-          const int wi = k * NW + warp;
-          if (lane == 0 && wi < W) aBits[(size_t)target * W + wi] = wv;
-        }
-        if (tid == 0) aE[target] = make_longlong2(nE1, nE2);
-        if (fc) {
-          unsigned char *rec = gF + (size_t)target * sl.bytes;
-          int2 *rf = reinterpret_cast<int2 *>(rec + sl.fields);
-          int32_t *rr = reinterpret_cast<int32_t *>(rec + sl.rc);
+        if (worker) {
 #pragma unroll
           for (int k = 0; k < B; ++k) {
-            const int q = k * T + tid;
-            if (q >= m) continue;
-            rf[q] = make_int2(L1[k], L2[k]);
-            rr[q] = own[k] >> 16;
+            const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+            const int wi = k * NWB + warp;
+            if (lane == 0 && wi < W) aBits[(size_t)target * W + wi] = wv;
           }
-          fence_proxy_async_global();  // later bulk copies read these
-          if (tid == 0) sWr[it & 7] = target;
+          if (tid == 0) aE[target] = make_longlong2(nE1, nE2);
+          if (fc) {
+            unsigned char *recp = gF + (size_t)target * sl.bytes;
+            int2 *rf = reinterpret_cast<int2 *>(recp + sl.fields);
+            int32_t *rr = reinterpret_cast<int32_t *>(recp + sl.rc);
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+              const int q = k * Tw + tid;
+              if (q >= m) continue;
+              rf[q] = make_int2(L1[k], L2[k]);
+              rr[q] = own[k] >> 16;
+            }
+            fence_proxy_async_global();  // later bulk copies read these
+          }
+        } else if (fc && lane == 0) {
+          sWr[it & 7] = target;
         }
       }
       E1 = nE1;
@@ -641,84 +719,65 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       Eoff = 0;
       ++st_flip;
       event = ps;
-    } else if (A.escape == 0) {
-      if (acount > 0) {
-        // Alg. 3: jump to a random archive member.
-        const int slot = pick(rnd[1], acount);
-        if (fc) {
-          const int b = (int)(it % NB);
-          const unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
-          // The copy for this iteration is usable if it was started for
-          // this slot and no later iteration rewrote that slot.
-          const PfRec rec = sPf[it & 7];
-          bool ok = rec.iter != 0 && rec.slot == slot;
-          for (int64_t x = rec.iter; ok && x < it; ++x)
-            if (sWr[x & 7] == slot) ok = false;
-          const int2 *rf;
-          const int32_t *rr;
-          const uint32_t *wsrc;
-          longlong2 se;
-          if (ok) {
-#ifdef MODA_KERNEL_CLOCKS
-            const long long w0 = clock64();
-#endif
-            if (!mbar_wait(&sBar[b], (uint32_t)rec.parity)) bc->fail = 1;
-#ifdef MODA_KERNEL_CLOCKS
-            st_wait += clock64() - w0;
-#endif
-            ++st_pf;
-            if (tid == 0) {
-              ph ^= 1u << b;
-              pend &= ~(1u << b);
-            }
-            rf = reinterpret_cast<const int2 *>(pb + sl.fields);
-            rr = reinterpret_cast<const int32_t *>(pb + sl.rc);
-            se = A.energies_in_smem
-                     ? aE[slot]
-                     : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
-            if (A.bits_in_smem) {
-              wsrc = aBits + (size_t)slot * W;
-            } else {
-              const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
-              wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
-            }
-          } else {  // read the record where it is
-            ++st_direct;
-            const unsigned char *recp = gF + (size_t)slot * sl.bytes;
-            rf = reinterpret_cast<const int2 *>(recp + sl.fields);
-            rr = reinterpret_cast<const int32_t *>(recp + sl.rc);
-            se = aE[slot];
+    } else if (d.kind == kJump) {
+      // Alg. 3: jump to a random archive member.
+      const int slot = d.slot;
+      if (fc) {
+        const int2 *rf;
+        const int32_t *rr;
+        const uint32_t *wsrc;
+        longlong2 se;
+        if (d.buf >= 0) {
+          unsigned char *pb = smem + lay.pf + (size_t)d.buf * lay.pf_slot;
+          // the control warp saw the copy complete; this observes it too
+          if (worker) mbar_wait(&sBar[d.buf], (uint32_t)d.parity);
+          rf = reinterpret_cast<const int2 *>(pb + sl.fields);
+          rr = reinterpret_cast<const int32_t *>(pb + sl.rc);
+          se = A.energies_in_smem ? aE[slot]
+                                  : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
+          if (A.bits_in_smem) {
             wsrc = aBits + (size_t)slot * W;
+          } else {
+            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+            wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
           }
-          E1 = se.x;
-          E2 = se.y;
-          xmask = 0;
-#pragma unroll
-          for (int k = 0; k < B; ++k) {
-            const int q = k * T + tid;
-            if (q >= m) continue;
-            const int2 f = rf[q];
-            L1[k] = f.x;
-            L2[k] = f.y;
-            own[k] = (rr[q] << 16) | (own[k] & 0xFFFF);
-            xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
-          }
-        } else {
-          const longlong2 se = aE[slot];
-          E1 = se.x;
-          E2 = se.y;
-          rebuild(aBits + (size_t)slot * W);
+          ++st_pf;
+        } else {  // read the record where it is
+          const unsigned char *recp = gF + (size_t)slot * sl.bytes;
+          rf = reinterpret_cast<const int2 *>(recp + sl.fields);
+          rr = reinterpret_cast<const int32_t *>(recp + sl.rc);
+          se = aE[slot];
+          wsrc = aBits + (size_t)slot * W;
+          ++st_direct;
         }
-        ++st_jump;
-        event = -1 - (int64_t)slot;
+        E1 = se.x;
+        E2 = se.y;
+        xmask = 0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (!valid(k)) continue;
+          const int q = k * Tw + tid;
+          const int2 f = rf[q];
+          L1[k] = f.x;
+          L2[k] = f.y;
+          own[k] = (rr[q] << 16) | (own[k] & 0xFFFF);
+          xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
+        }
       } else {
-        ++st_empty;
+        const longlong2 se = aE[slot];
+        E1 = se.x;
+        E2 = se.y;
+        rebuild(aBits + (size_t)slot * W);
       }
+      ++st_jump;
+      event = -1 - (int64_t)slot;
+    } else if (A.escape == 0) {
+      ++st_empty;
     } else {
       Eoff += A.beta;
       ++st_off;
     }
-    flip_streak = total > 0 ? flip_streak + 1 : 0;
+    flip_streak = d.kind == kFlip ? flip_streak + 1 : 0;
     if (A.trace != nullptr && tid == 0) {
       int64_t *tr = A.trace + ((size_t)rb * (size_t)A.I_max + (size_t)(it - 1)) * 3;
       tr[0] = E1;
@@ -728,18 +787,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 
   // No bulk copy may be in flight when the block exits.
-  if (fc && tid == 0) {
+  if (fc && control && lane == 0) {
     for (int b = 0; b < NB; ++b)
       if ((pend >> b) & 1u)
         if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
   }
   __syncthreads();
   if (tid == 0 && bc->fail) atomicExch(A.error, kErrCopyTimeout);
+  if (worker) {
 #pragma unroll
-  for (int k = 0; k < B; ++k) {
-    const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
-    const int wi = k * NW + warp;
-    if (lane == 0 && wi < W) A.x_final[(size_t)rb * W + wi] = wv;
+    for (int k = 0; k < B; ++k) {
+      const uint32_t wv = __ballot_sync(kFull, (xmask >> k) & 1u);
+      const int wi = k * NWB + warp;
+      if (lane == 0 && wi < W) A.x_final[(size_t)rb * W + wi] = wv;
+    }
   }
   if (A.energies_in_smem) {
     for (int e = tid; e < acount; e += T) {
@@ -759,27 +820,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     st[3] = st_off;
     st[4] = st_pf;
     st[5] = st_direct;
-    st[6] = st_wait;  // cycle counters: builds with MODA_KERNEL_CLOCKS only
-#ifdef MODA_KERNEL_CLOCKS
-    st[7] = clock64() - loop_t0;
-#else
+    st[6] = 0;
     st[7] = 0;
-    (void)loop_t0;
-#endif
     A.arch_count[rb] = acount;
     A.E_final[2 * rb] = E1;
     A.E_final[2 * rb + 1] = E2;
   }
 }
 
-template <int B>
-cudaError_t launch_b(const AnnealArgs &args, int replicas, int threads,
-                     size_t smem, cudaStream_t stream) {
+template <int B, bool NARROW>
+cudaError_t launch_bn(const AnnealArgs &args, int replicas, int workers,
+                      size_t smem, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(
-      anneal_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      anneal_kernel<B, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  anneal_kernel<B><<<replicas, threads, smem, stream>>>(args);
+  anneal_kernel<B, NARROW><<<replicas, workers + 32, smem, stream>>>(args);
   return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_b(const AnnealArgs &args, int replicas, int workers, bool narrow,
+                     size_t smem, cudaStream_t stream) {
+  return narrow ? launch_bn<B, true>(args, replicas, workers, smem, stream)
+                : launch_bn<B, false>(args, replicas, workers, smem, stream);
 }
 
 }  // namespace
@@ -788,15 +851,16 @@ bool supported_rounds(int b) {
   return b == 1 || b == 2 || b == 3 || b == 4 || b == 6 || b == 8;
 }
 
-cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int threads,
-                          int rounds, size_t smem, cudaStream_t stream) {
+cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
+                          int rounds, bool narrow, size_t smem, cudaStream_t stream) {
+  if (workers % 32 || workers < 32 || workers > kMaxWorkers) return cudaErrorInvalidValue;
   switch (rounds) {
-    case 1: return launch_b<1>(args, replicas, threads, smem, stream);
-    case 2: return launch_b<2>(args, replicas, threads, smem, stream);
-    case 3: return launch_b<3>(args, replicas, threads, smem, stream);
-    case 4: return launch_b<4>(args, replicas, threads, smem, stream);
-    case 6: return launch_b<6>(args, replicas, threads, smem, stream);
-    case 8: return launch_b<8>(args, replicas, threads, smem, stream);
+    case 1: return launch_b<1>(args, replicas, workers, narrow, smem, stream);
+    case 2: return launch_b<2>(args, replicas, workers, narrow, smem, stream);
+    case 3: return launch_b<3>(args, replicas, workers, narrow, smem, stream);
+    case 4: return launch_b<4>(args, replicas, workers, narrow, smem, stream);
+    case 6: return launch_b<6>(args, replicas, workers, narrow, smem, stream);
+    case 8: return launch_b<8>(args, replicas, workers, narrow, smem, stream);
     default: return cudaErrorInvalidValue;
   }
 }

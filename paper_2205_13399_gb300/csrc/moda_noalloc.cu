@@ -172,14 +172,14 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   static const int kRounds[] = {1, 2, 3, 4, 6, 8};
   int T = 0, B = 0;
   for (int b : kRounds)
-    if ((int64_t)b * (p->block_threads > 0 ? p->block_threads : moda::kMaxThreads) >= m) {
+    if ((int64_t)b * (p->block_threads > 0 ? p->block_threads : moda::kMaxWorkers) >= m) {
       B = b;
       break;
     }
   if (!B) return nofail(MODA_EUNSUPPORTED, "n too large for the block size");
   if (p->block_threads > 0) {
-    if (p->block_threads % 32 || p->block_threads > moda::kMaxThreads)
-      return nofail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 1024");
+    if (p->block_threads % 32 || p->block_threads > moda::kMaxWorkers)
+      return nofail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 992");
     T = p->block_threads;
   } else {
     T = ((m + B - 1) / B + 31) / 32 * 32;
@@ -196,6 +196,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   if (cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
       cudaSuccess)
     return nofail(MODA_ECUDA, "device attribute query failed");
+  const bool narrow = moda::narrow_ok(n, f1max * dmax, f2max * dmax, w1, w2);
   // Shared-memory placement with the field cache on (escape by jumps) or off.
   const bool cache = p->escape == MODA_ESC_ARCHIVE;
   moda::Placement place{};
@@ -204,7 +205,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   for (int opt = 0; opt < 3 && !placed; ++opt)
     for (int de = 1; de >= 0 && !placed; --de)
       for (int la = cache ? 1 : 0; la >= 0 && !placed; --la) {
-        const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1};
+        const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1, narrow};
         const moda::SmemLayout l = moda::smem_layout(n, m, W, s, T, B, pl);
         if ((int64_t)l.total <= dev_smem) {
           place = pl;
@@ -285,7 +286,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   a.stats = out->stats;
   a.trace = nullptr;
   a.error = out->error;
-  e = moda::launch_anneal(a, p->replicas, T, B, lay.total, stream);
+  e = moda::launch_anneal(a, p->replicas, T, B, place.narrow, lay.total, stream);
   if (e != cudaSuccess) return nofail(MODA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return MODA_OK;
 }

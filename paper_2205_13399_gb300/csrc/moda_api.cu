@@ -340,19 +340,19 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kMaxLookahead + 1)
     return fail(MODA_EINVAL, "prefetch must be in [0, 4]");
+  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Field cache: one record of the fields per archive slot, so a jump to
   // the archive reloads the member's fields instead of rebuilding them.
   // Used when the escape jumps to the archive and the records fit in (by
   // default) 60 % of the free device memory.
   const size_t cache_bytes =
-      (size_t)p->replicas * s_cap * moda::slot_layout(m).bytes;
+      (size_t)p->replicas * s_cap * moda::slot_layout(m, narrow).bytes;
   bool want_cache = p->escape == MODA_ESC_ARCHIVE && p->field_cache != 2;
   if (want_cache && p->field_cache == 0) {
     size_t free_b = 0, total_b = 0;
     MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
     want_cache = cache_bytes <= free_b / 10 * 6;
   }
-  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Shared-memory placement, best first: the field cache (if wanted), the
   // archive energies and states on chip (then energies only, then
   // neither), Delta E published in shared memory, and the prefetch
@@ -361,7 +361,8 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   bool placed = false;
   moda::SmemLayout lay{};
   const int la_hi = p->prefetch > 0 ? p->prefetch - 1 : 1;
-  const int la_lo = p->prefetch > 0 ? p->prefetch - 1 : 0;
+  // (prefetch distance -1: the cache is read in place, no buffers)
+  const int la_lo = p->prefetch > 0 ? p->prefetch - 1 : -1;
   for (int c = want_cache ? 1 : 0; c >= 0 && !placed; --c)
     for (int opt = 0; opt < 3 && !placed; ++opt)
       for (int de = 1; de >= 0 && !placed; --de)

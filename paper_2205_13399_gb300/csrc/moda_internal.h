@@ -29,17 +29,14 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
   return (v + a - 1) / a * a;
 }
 
-// Per-slot record of the field cache: the fields (L1, L2) of every bit as
-// int2, then R_i + C_u of every bit as int32.
+// Per-slot record of the field cache: (Delta E_1, Delta E_2) of every bit
+// of the member's state, as int32 pairs (narrow variant) or int64 pairs.
 struct SlotLayout {
-  size_t fields, rc, bytes;
+  size_t bytes;
 };
-__host__ __device__ inline SlotLayout slot_layout(int m) {
+__host__ __device__ inline SlotLayout slot_layout(int m, bool narrow) {
   SlotLayout S;
-  const size_t m8 = align_up((size_t)m, 8);
-  S.fields = 0;
-  S.rc = 8 * m8;
-  S.bytes = 12 * m8;
+  S.bytes = (narrow ? 8 : 16) * align_up((size_t)m, 8);
   return S;
 }
 
@@ -67,10 +64,10 @@ struct AnnealArgs {
   const double *table;      // [65536] -ln((idx + 0.5) / 65536)
   const int32_t *Fs1, *Fs2; // [n][n] F_k + F_k^T (symmetric)
   const int32_t *D;         // [n][n] symmetric distances, zero diagonal
-  // Field cache, [R][s] records of slot_layout(m).bytes, or nullptr: the
-  // fields of every archive member, written when the member is stored and
-  // brought back by a bulk copy (TMA), started up to `lookahead`
-  // iterations early, when the replica jumps to it.
+  // Field cache, [R][s] records of slot_layout(m, narrow).bytes, or
+  // nullptr: Delta E of every bit of every archive member, written when
+  // the member is stored and brought back by a bulk copy (TMA), started up
+  // to `lookahead` iterations early, when the replica jumps to it.
   unsigned char *fcache;
   // outputs, one block per replica of this launch
   int64_t *arch_E;          // [R][s][2]
@@ -126,11 +123,12 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   // field-cache record, then the member's energies and the 16-byte-aligned
   // span of its state words when those live in HBM.  M = X * D (only used
   // by rebuilds, which never overlap a prefetch) shares this space.
-  L.pfE = slot_layout(m).bytes;
+  L.pfE = slot_layout(m, P.narrow).bytes;
   L.pfW = L.pfE + (P.energies_in_smem ? 0 : 16);
   L.pf_slot = align_up(L.pfW + (P.bits_in_smem ? 0 : align_up(4 * (size_t)W, 16) + 16), 16);
   L.pf = o;
-  size_t pf_bytes = P.field_cache ? L.pf_slot * (size_t)(P.lookahead + 2) : 0;
+  size_t pf_bytes = P.field_cache && P.lookahead >= 0
+                        ? L.pf_slot * (size_t)(P.lookahead + 2) : 0;
   if (pf_bytes < 4 * nn) pf_bytes = 4 * nn;
   L.M = o;
   o = align_up(o + pf_bytes, 16);

@@ -249,6 +249,7 @@ template <int B, bool NARROW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
+  using dE2_t = typename std::conditional<NARROW, int2, longlong2>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = A.n, m = A.m, W = A.W, s = A.s;
   const int T = blockDim.x, tid = threadIdx.x;
@@ -263,12 +264,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // Prefetch buffers: target iteration tt uses buffer tt % NB.  The copy
   // for t + LA starts before the barrier of iteration t, while a lagging
   // warp may still read the buffer of t - 1, so NB = LA + 2.
+  // LA = -1: the cache is read in place, nothing is prefetched.
   const int NB = LA + 2;
-  const uint32_t RB = (uint32_t)LA + 3;  // draw ring: t % RB
+  const bool pf = fc && LA >= 0;
+  const uint32_t RB = (uint32_t)(LA + 3);  // draw ring: t % RB
   const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
                     de_smem, NARROW};
   const SmemLayout lay = smem_layout(n, m, W, s, Tw, B, P);
-  const SlotLayout sl = slot_layout(m);
+  const SlotLayout sl = slot_layout(m, NARROW);
+  const dE_t w1 = (dE_t)A.w1, w2 = (dE_t)A.w2;
   int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
   int32_t *sD = reinterpret_cast<int32_t *>(smem + lay.D);
   int32_t *sM = reinterpret_cast<int32_t *>(smem + lay.M);
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   Decision *dec = reinterpret_cast<Decision *>(smem + lay.dec);
   uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
   uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
-  dE_t *sDE = reinterpret_cast<dE_t *>(smem + lay.dE);  // [bits][2]
+  dE2_t *sDE = reinterpret_cast<dE2_t *>(smem + lay.dE);  // [bits]
   // Prefetch bookkeeping of the control warp (after initialisation; shares
   // the reduction space): sPf[target iteration % 8], and sWr[iteration % 8]
   // = the archive slot that iteration wrote (-1 = none).
@@ -304,6 +308,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         ? reinterpret_cast<uint32_t *>(smem + lay.archB)
                         : gBits;
   int rc_buf = 0;
+  const uint32_t I_max = (uint32_t)A.I_max;
+  const uint32_t nsched = (uint32_t)A.nsched;
 
   for (int e = tid; e < n * n; e += T) {
     sFs[e] = make_int2(A.Fs1[e], A.Fs2[e]);
@@ -313,7 +319,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   if (control) {
     if (lane == 0) {
       bc->fail = 0;
-      if (fc) {
+      if (pf) {
         for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
         fence_mbar_init();
       }
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // Draws (select, restart, exploit) of iteration t live in sRnd[t % RB];
     // they are drawn LA + 1 iterations ahead.
     if (lane < 3) {
-      for (uint32_t q = 1; q <= (uint32_t)LA + 1; ++q) {
+      for (uint32_t q = 1; (int)q <= LA + 1; ++q) {
         uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
         philox10(c, k0, k1);
         sRnd[(q % RB) * 4 + lane] = c[0];
@@ -331,18 +337,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
   }
 
-  // Own bit k is valid when worker && k*Tw + tid < m; own[k] packs facility
-  // i (bits 8..15), location u (bits 0..7) and rc = R_i + C_u (16..31).
+  // Own bit k is valid when worker && k*Tw + tid < m: own[k] packs its
+  // facility i (bits 8..15) and location u (bits 0..7); D1[k], D2[k] hold
+  // Delta E_1, Delta E_2 of flipping it (Eq. cale), kept up to date.
   int own[B];
-  int32_t L1[B], L2[B];
+  dE_t D1[B], D2[B];
   uint32_t xmask = 0;
   auto valid = [&](int k) { return worker && k * Tw + tid < m; };
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const int p = k * Tw + tid;
     own[k] = valid(k) ? (((p / n) << 8) | (p % n)) : 0;
-    L1[k] = 0;
-    L2[k] = 0;
+    D1[k] = 0;
+    D2[k] = 0;
   }
   // Initial state (Alg. 3: "a random binary solution"): bit p is bit p % 32
   // of word (p / 32) % 4 of the draw (p / 128, 0, replica, init).
@@ -363,12 +370,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
   __syncthreads();
 
-  // Fields, counts and owned bits of the state held in `words`, in two
-  // passes around one barrier: (1) M = X * D (M_ju = sum_v x_jv d_vu) and
-  // the row / column counts into shared memory; (2) every worker forms
-  // L_k[(i,u)] = sum_j Fs^k_ij M_ju for its own bits.  Both passes are
-  // exact int32 arithmetic (the instance check bounds every field).
-  auto rebuild = [&](const uint32_t *words) {
+  // Delta E of every owned bit of the state held in `words`, from scratch,
+  // in two passes around one barrier: (1) M = X * D (M_ju = sum_v x_jv d_vu)
+  // and the row / column counts R, C into shared memory; (2) every worker
+  // forms the cost fields L_k[(i,u)] = sum_j Fs^k_ij M_ju and
+  //   Delta E_k = (1 - 2x)(L_k + w_k (R_i + C_u - 1 - 2x)).
+  // Fields are exact int32 (the instance check bounds them).  Returns the
+  // sum over set bits of L_1 and of L_2 (2 c_k) in s1, s2.
+  auto rebuild = [&](const uint32_t *words, int64_t &s1, int64_t &s2) {
     for (int e = tid; e < n * n; e += T) {
       const int j = (int)__umulhi((uint32_t)e, A.magic);
       const int u = e - j * n;
@@ -401,10 +410,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __syncthreads();
     const int32_t *cR = sRC + rc_buf * 2 * n, *cC = cR + n;
     for (int e = tid; e < 2 * n; e += T) sRC[(1 - rc_buf) * 2 * n + e] = 0;
+    s1 = 0;
+    s2 = 0;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       if (!valid(k)) continue;
-      const int i = (own[k] >> 8) & 255, u = own[k] & 255;
+      const int i = own[k] >> 8, u = own[k] & 255;
       int32_t a1 = 0, a2 = 0;
       const int2 *frow = sFs + i * n;  // Fs symmetric: row i = column i
 #pragma unroll 5
@@ -414,25 +425,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         a1 += f.x * mm;
         a2 += f.y * mm;
       }
-      L1[k] = a1;
-      L2[k] = a2;
-      own[k] = ((cR[i] + cC[u]) << 16) | (i << 8) | u;
+      const int xv = (int)((xmask >> k) & 1u);
+      const dE_t g = (dE_t)(1 - 2 * xv);
+      const dE_t h = (dE_t)(cR[i] + cC[u] - 1 - 2 * xv);
+      D1[k] = g * ((dE_t)a1 + w1 * h);
+      D2[k] = g * ((dE_t)a2 + w2 * h);
+      if (xv) {
+        s1 += a1;
+        s2 += a2;
+      }
     }
     rc_buf ^= 1;
   };
-  rebuild(sInit);
-
-  // E_k = c_k + w_k g / 2 with c_k = (sum_p x_p L_k[p]) / 2 and g from the
-  // row and column counts.
   int64_t E1, E2;
   {
-    int64_t s1 = 0, s2 = 0, gp = 0;
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (!valid(k) || !((xmask >> k) & 1u)) continue;
-      s1 += L1[k];
-      s2 += L2[k];
-    }
+    // E_k = c_k + w_k g / 2 with c_k = (sum_p x_p L_k[p]) / 2 and g from
+    // the row and column counts.
+    int64_t s1, s2, gp = 0;
+    rebuild(sInit, s1, s2);
     for (int e = tid; e < n; e += T) {
       const int64_t dr = 1 - sRC[e], dc = 1 - sRC[n + e];
       gp += dr * dr + dc * dc;
@@ -458,32 +468,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
   uint32_t pend = 0, ph = 0;
 
-  for (int64_t it = 1; it <= A.I_max; ++it) {
-    const uint32_t t = (uint32_t)it;
+  for (uint32_t t = 1; t <= I_max; ++t) {
     const int buf = (int)(t & 1u);
     uint32_t *mask = sMask + buf * items;        // accept ballots
     uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
     const uint32_t *rnd = sRnd + (t % RB) * 4;
 
     if (worker) {
-      // ---- workers: Delta E (Eq. cale) and the parallel trial ----------
+      // ---- workers: the parallel trial of their bits --------------------
       const SchEntry se = sSch[buf];
       const double delta = se.delta;
       const dE_t lo = NARROW ? (dE_t)(se.lo < 2147483647ll ? se.lo : 2147483647ll) : (dE_t)se.lo;
       const dE_t hi = NARROW ? (dE_t)(se.hi < 2147483647ll ? se.hi : 2147483647ll) : (dE_t)se.hi;
-      const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         bool acc = false;
-        const uint32_t xv = (xmask >> k) & 1u;
         if (k * Tw + tid < m) {
-          const int p = k * Tw + tid;
-          const int sg = 1 - 2 * (int)xv;
-          const int h = sg * ((own[k] >> 16) - 1 - 2 * (int)xv);
-          const dE_t e1 = (dE_t)(sg * L1[k]) + (dE_t)A.w1 * (dE_t)h;
-          const dE_t e2 = (dE_t)(sg * L2[k]) + (dE_t)A.w2 * (dE_t)h;
+          const dE_t e1 = D1[k], e2 = D2[k];
           dE_t a1, a2;
           if (A.escape == 1) {  // the offset lowers Delta E (Alg. 1)
+            const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
             a1 = e1 > off ? e1 - off : 0;
             a2 = e2 > off ? e2 - off : 0;
           } else {
@@ -494,20 +498,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           if (a <= lo) {
             acc = true;
           } else if (a <= hi) {
+            const int p = k * Tw + tid;
             uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
             philox10(c, k0, k1);
             const uint32_t w = word_of(c, p & 3);
             acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
           }
           if (acc && de_smem) {
-            sDE[2 * p] = e1;
-            sDE[2 * p + 1] = e2;
+            dE2_t v;
+            v.x = e1;
+            v.y = e2;
+            sDE[k * Tw + tid] = v;
           }
         }
         const uint32_t bal = __ballot_sync(kFull, acc);
         if (lane == 0) mask[k * NWB + warp] = bal;
         if (de_smem) {
-          const uint32_t xb = __ballot_sync(kFull, xv != 0);
+          const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
           if (lane == 0) xm[k * NWB + warp] = xb;
         }
       }
@@ -515,28 +522,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       // ---- control warp: schedule, draws, prefetch ----------------------
       SchEntry nx{};
       if (lane == 31) {  // schedule entry of iteration t + 1
-        const int sn = (int)((it + 1 <= A.nsched ? it + 1 : (int64_t)A.nsched) - 1);
+        const uint32_t sn = (t + 1 <= nsched ? t + 1 : nsched) - 1;
         nx.delta = A.sch_delta[sn];
         nx.lo = A.sch_lo[sn];
         nx.hi = A.sch_hi[sn];
       }
       if (lane < 3) {  // draws of iteration t + LA + 1
-        const uint32_t q = t + (uint32_t)LA + 1u;
+        const uint32_t q = (uint32_t)((int64_t)t + LA + 1);
         uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
         philox10(c, k0, k1);
         sRnd[(q % RB) * 4 + lane] = c[0];
       }
-      if (fc && lane == 0) {
+      if (pf && lane == 0) {
         // Copy for the jump iteration t + LA would make.  A slot written in
         // the previous iteration is left alone: its writes are ordered for
         // the copy engine only by a later barrier.
-        const int64_t tt = it + LA;
-        const int b = (int)(tt % NB);
-        bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= A.I_max;
+        const uint32_t tt = t + (uint32_t)LA;
+        const int b = (int)(tt % (uint32_t)NB);
+        bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= I_max;
         int slot_p = 0;
         if (issue) {
-          slot_p = pick(sRnd[((uint32_t)tt % RB) * 4 + 1], acount);
-          if (sWr[(it - 1) & 7] == slot_p) issue = false;
+          slot_p = pick(sRnd[(tt % RB) * 4 + 1], acount);
+          if (sWr[(t - 1) & 7] == slot_p) issue = false;
         }
         uint32_t par = 0;
         if (issue) {
@@ -565,7 +572,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           pend |= 1u << b;
         }
         sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
-        sWr[it & 7] = -1;  // set to the written slot by a flip below
+        sWr[t & 7] = -1;  // set to the written slot by a flip below
       }
       if (lane == 31) sSch[1 - buf] = nx;
     }
@@ -573,30 +580,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
     // ---- control warp: the decision ------------------------------------
     if (control) {
-      int incl, cnt;
-      const int total = warp_mask_total(mask, items, lane, incl, cnt);
+      int cnt = 0;
+      for (int q = lane; q < items; q += 32) cnt += __popc(mask[q]);
+      const int total = __reduce_add_sync(kFull, cnt);
       Decision d{kNone, 0, 0, 0, -1, 0, 0, 0};
       if (total > 0) {
+        int incl, c2;
+        warp_mask_total(mask, items, lane, incl, c2);
         d.kind = kFlip;
-        d.ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, cnt, pick(rnd[0], total));
+        d.ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, c2, pick(rnd[0], total));
         if (de_smem) {
           const int kk = d.ps / Tw, rr = d.ps - kk * Tw;
-          d.dE1 = (int64_t)sDE[2 * d.ps];
-          d.dE2 = (int64_t)sDE[2 * d.ps + 1];
+          const dE2_t v = sDE[d.ps];
+          d.dE1 = (int64_t)v.x;
+          d.dE2 = (int64_t)v.y;
           d.sgn = 1 - 2 * (int)((xm[kk * NWB + (rr >> 5)] >> (rr & 31)) & 1u);
         }
       } else if (A.escape == 0 && acount > 0) {
         d.kind = kJump;
         d.slot = pick(rnd[1], acount);
-        if (fc) {
-          // The copy for this iteration is usable if it was started for
-          // this slot and no later iteration rewrote that slot.
-          const PfRec rec = sPf[it & 7];
-          bool ok = rec.iter != 0 && rec.slot == d.slot;
-          for (int64_t x = rec.iter; ok && x < it; ++x)
+        if (pf) {
+          // The copy for this iteration is usable if it was started LA
+          // iterations ago for this slot and no iteration since rewrote it.
+          const PfRec rec = sPf[t & 7];
+          bool ok = rec.iter != 0 && rec.slot == d.slot && (uint32_t)rec.iter + LA == t;
+          for (uint32_t x = (uint32_t)rec.iter; ok && x < t; ++x)
             if (sWr[x & 7] == d.slot) ok = false;
           if (ok) {
-            const int b = (int)(it % NB);
+            const int b = (int)(t % (uint32_t)NB);
             if (!mbar_wait(&sBar[b], (uint32_t)rec.parity)) bc->fail = 1;
             if (lane == 0) {
               ph ^= 1u << b;
@@ -625,12 +636,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
           for (int k = 0; k < B; ++k) {
             if (k != kk) continue;
-            const int xv = (int)((xmask >> k) & 1u);
-            const int g = 1 - 2 * xv;
-            const int h = g * ((own[k] >> 16) - 1 - 2 * xv);
-            bc->dE1 = (int64_t)(g * L1[k]) + A.w1 * h;
-            bc->dE2 = (int64_t)(g * L2[k]) + A.w2 * h;
-            bc->sgn = g;
+            bc->dE1 = (int64_t)D1[k];
+            bc->dE2 = (int64_t)D2[k];
+            bc->sgn = 1 - 2 * (int)((xmask >> k) & 1u);
           }
         }
         __syncthreads();
@@ -643,17 +651,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       const int v = ps - j * n;
       int anyd = 0;
       if (worker) {
-        // Apply the flip of (j, v) to the owned registers.
+        // Delta E after flipping (j, v): the flipped bit's changes sign;
+        // every other bit q = (i, u) gains (1 - 2 x_q) s P_qp with
+        // P_qp = Fs^k_ij d_uv + w_k [i == j or u == v] (Eq. cale, Y / Z).
 #pragma unroll
         for (int k = 0; k < B; ++k) {
           if (k * Tw + tid >= m) continue;
-          const int i = (own[k] >> 8) & 255, u = own[k] & 255;
+          if (k * Tw + tid == ps) {
+            D1[k] = -D1[k];
+            D2[k] = -D2[k];
+            xmask ^= 1u << k;
+            continue;
+          }
+          const int i = own[k] >> 8, u = own[k] & 255;
           const int2 f = sFs[j * n + i];
-          const int32_t dd = sg * sD[v * n + u];
-          L1[k] += f.x * dd;
-          L2[k] += f.y * dd;
-          own[k] += (sg * ((i == j) + (u == v))) * 65536;
-          if (k * Tw + tid == ps) xmask ^= 1u << k;
+          const int32_t dd = sD[v * n + u];
+          const bool coupled = (i == j) | (u == v);
+          const int gs = sg * (1 - 2 * (int)((xmask >> k) & 1u));
+          D1[k] += (dE_t)gs * ((dE_t)(f.x * dd) + (coupled ? w1 : (dE_t)0));
+          D2[k] += (dE_t)gs * ((dE_t)(f.y * dd) + (coupled ? w2 : (dE_t)0));
         }
         // Archive: ballots of "x dominates slot y" in slot order, and (for
         // the exploitative update) whether some member dominates x.
@@ -698,20 +714,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           }
           if (tid == 0) aE[target] = make_longlong2(nE1, nE2);
           if (fc) {
-            unsigned char *recp = gF + (size_t)target * sl.bytes;
-            int2 *rf = reinterpret_cast<int2 *>(recp + sl.fields);
-            int32_t *rr = reinterpret_cast<int32_t *>(recp + sl.rc);
+            dE2_t *rf = reinterpret_cast<dE2_t *>(gF + (size_t)target * sl.bytes);
 #pragma unroll
             for (int k = 0; k < B; ++k) {
               const int q = k * Tw + tid;
               if (q >= m) continue;
-              rf[q] = make_int2(L1[k], L2[k]);
-              rr[q] = own[k] >> 16;
+              dE2_t v2;
+              v2.x = D1[k];
+              v2.y = D2[k];
+              rf[q] = v2;
             }
             fence_proxy_async_global();  // later bulk copies read these
           }
-        } else if (fc && lane == 0) {
-          sWr[it & 7] = target;
+        } else if (pf && lane == 0) {
+          sWr[t & 7] = target;
         }
       }
       E1 = nE1;
@@ -723,16 +739,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       // Alg. 3: jump to a random archive member.
       const int slot = d.slot;
       if (fc) {
-        const int2 *rf;
-        const int32_t *rr;
+        const dE2_t *rf;
         const uint32_t *wsrc;
         longlong2 se;
         if (d.buf >= 0) {
           unsigned char *pb = smem + lay.pf + (size_t)d.buf * lay.pf_slot;
           // the control warp saw the copy complete; this observes it too
           if (worker) mbar_wait(&sBar[d.buf], (uint32_t)d.parity);
-          rf = reinterpret_cast<const int2 *>(pb + sl.fields);
-          rr = reinterpret_cast<const int32_t *>(pb + sl.rc);
+          rf = reinterpret_cast<const dE2_t *>(pb);
           se = A.energies_in_smem ? aE[slot]
                                   : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
           if (A.bits_in_smem) {
@@ -743,9 +757,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           }
           ++st_pf;
         } else {  // read the record where it is
-          const unsigned char *recp = gF + (size_t)slot * sl.bytes;
-          rf = reinterpret_cast<const int2 *>(recp + sl.fields);
-          rr = reinterpret_cast<const int32_t *>(recp + sl.rc);
+          rf = reinterpret_cast<const dE2_t *>(gF + (size_t)slot * sl.bytes);
           se = aE[slot];
           wsrc = aBits + (size_t)slot * W;
           ++st_direct;
@@ -757,17 +769,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         for (int k = 0; k < B; ++k) {
           if (!valid(k)) continue;
           const int q = k * Tw + tid;
-          const int2 f = rf[q];
-          L1[k] = f.x;
-          L2[k] = f.y;
-          own[k] = (rr[q] << 16) | (own[k] & 0xFFFF);
+          const dE2_t v2 = rf[q];
+          D1[k] = v2.x;
+          D2[k] = v2.y;
           xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
         }
       } else {
         const longlong2 se = aE[slot];
         E1 = se.x;
         E2 = se.y;
-        rebuild(aBits + (size_t)slot * W);
+        int64_t s1, s2;
+        rebuild(aBits + (size_t)slot * W, s1, s2);
       }
       ++st_jump;
       event = -1 - (int64_t)slot;
@@ -779,7 +791,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     flip_streak = d.kind == kFlip ? flip_streak + 1 : 0;
     if (A.trace != nullptr && tid == 0) {
-      int64_t *tr = A.trace + ((size_t)rb * (size_t)A.I_max + (size_t)(it - 1)) * 3;
+      int64_t *tr = A.trace + ((size_t)rb * (size_t)I_max + (size_t)(t - 1)) * 3;
       tr[0] = E1;
       tr[1] = E2;
       tr[2] = event;
@@ -787,7 +799,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 
   // No bulk copy may be in flight when the block exits.
-  if (fc && control && lane == 0) {
+  if (pf && control && lane == 0) {
     for (int b = 0; b < NB; ++b)
       if ((pend >> b) & 1u)
         if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;

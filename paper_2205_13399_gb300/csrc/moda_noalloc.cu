@@ -135,10 +135,6 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   if (pen && (pen->kind < 0 || pen->kind > 1 || (pen->kind == 1 && (pen->w1 < 0 || pen->w2 < 0))))
     return nofail(MODA_EINVAL, "bad penalty");
   const int s = p->archive_size > 0 ? p->archive_size : m;
-  const size_t rec = moda::slot_layout(m).bytes;
-  if ((size_t)p->replicas * (size_t)s * rec > kScratchBytes)
-    return nofail(MODA_EUNSUPPORTED,
-                  "replicas * archive slots * field record exceed the 64 MiB scratch array");
 
   std::lock_guard<std::mutex> lock(g_mutex);
   // Instance: the same checks and symmetrised flows as moda_create_instance.
@@ -197,6 +193,10 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
       cudaSuccess)
     return nofail(MODA_ECUDA, "device attribute query failed");
   const bool narrow = moda::narrow_ok(n, f1max * dmax, f2max * dmax, w1, w2);
+  const size_t rec = moda::slot_layout(m, narrow).bytes;
+  if ((size_t)p->replicas * (size_t)s * rec > kScratchBytes)
+    return nofail(MODA_EUNSUPPORTED,
+                  "replicas * archive slots * field record exceed the 64 MiB scratch array");
   // Shared-memory placement with the field cache on (escape by jumps) or off.
   const bool cache = p->escape == MODA_ESC_ARCHIVE;
   moda::Placement place{};
@@ -204,7 +204,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   bool placed = false;
   for (int opt = 0; opt < 3 && !placed; ++opt)
     for (int de = 1; de >= 0 && !placed; --de)
-      for (int la = cache ? 1 : 0; la >= 0 && !placed; --la) {
+      for (int la = cache ? 1 : 0; la >= (cache ? -1 : 0) && !placed; --la) {
         const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1, narrow};
         const moda::SmemLayout l = moda::smem_layout(n, m, W, s, T, B, pl);
         if ((int64_t)l.total <= dev_smem) {

@@ -93,7 +93,7 @@ struct Placement {
 // Byte offsets of the shared-memory carve-up of one annealing block with
 // `workers` bit-owning threads (plus one control warp).
 struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, dec, init, mbar, dE, pf,
+  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, init, mbar, dE, pf,
       pf_slot, pfE, pfW, archE, archB, total;
 };
 
@@ -109,12 +109,12 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.D = o;     o = align_up(o + 4 * nn, 16);
   L.mask = o;  o = align_up(o + 4 * 4 * items, 16);  // accept, state x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
-  L.rnd = o;   o = align_up(o + (kMaxLookahead + 3) * 4 * 4, 16);
-  L.sch = o;   o = align_up(o + 2 * 32, 16);                 // two entries
+  L.rnd = o;   o = align_up(o + 32 * 4 * 4, 16);             // 32 iterations
+  L.sch = o;   o = align_up(o + 32 * 32, 16);                // 32 entries
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
-  L.dec = o;   o = align_up(o + 48, 16);
+  L.jr = o;    o = align_up(o + 8 * 16, 16);                 // 8 entries
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
   L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits, 16);

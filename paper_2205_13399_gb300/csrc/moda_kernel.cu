@@ -52,6 +52,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;  // bounded mbarrier polls
+constexpr uint32_t kRing = 32;        // draw / schedule ring, iterations
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplies with a Weyl-sequence key schedule.
@@ -170,6 +171,29 @@ __device__ __forceinline__ int warp_mask_total(const uint32_t *masks,
   return __shfl_sync(kFull, incl, 31);
 }
 
+// The same chunking as warp_mask_total without the scan: the lane's own
+// count in `cnt`, the total in every lane.
+__device__ __forceinline__ int warp_mask_count(const uint32_t *masks,
+                                               int items, int lane, int &cnt) {
+  const int per = (items + 31) >> 5;
+  cnt = 0;
+  for (int q = 0; q < per; ++q) {
+    const int it = lane * per + q;
+    if (it < items) cnt += __popc(masks[it]);
+  }
+  return (int)__reduce_add_sync(kFull, (unsigned)cnt);
+}
+
+// Inclusive prefix sum of `v` over the lanes.
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int u = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+
 // Flat index round*Tw + warp*32 + lane of the r-th set bit (r < total), in
 // every lane.
 __device__ __forceinline__ int warp_mask_select(const uint32_t *masks,
@@ -214,20 +238,11 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red,
 struct Bcast {
   int64_t dE1, dE2;  // Delta E of the flipped bit (owner-published path)
   int32_t sgn;       // +1: the bit turns on, -1: off
-  int32_t fail;      // a bulk copy did not complete
+  int32_t pad;
 };
 
-// The control warp's decision for one iteration.
+// Kinds of iteration outcome (Alg. 3).
 enum : int32_t { kNone = 0, kFlip = 1, kJump = 2 };
-struct Decision {
-  int32_t kind;
-  int32_t ps;      // flipped bit
-  int32_t sgn;     // +1: it turns on, -1: off (0: the owner publishes)
-  int32_t slot;    // archive slot jumped to
-  int32_t buf;     // prefetch buffer holding it, -1: read the cache record
-  int32_t parity;  // that buffer's mbarrier phase parity
-  int64_t dE1, dE2;
-};
 
 // Prefetch bookkeeping entry for one target iteration.
 struct PfRec {
@@ -237,10 +252,21 @@ struct PfRec {
   int32_t pad;
 };
 
+// Schedule entry of one iteration: delta_t and the thresholds, also
+// clamped to int32 for the narrow variant.
 struct SchEntry {
   double delta;
   int64_t lo, hi;
-  int64_t pad;
+  int32_t lo32, hi32;
+};
+
+// What iteration t does when no bit is accepted (Alg. 3), settled by the
+// control warp before the iteration's barrier.
+struct JumpRec {
+  int32_t kind;     // kJump or kNone
+  int32_t slot;     // archive slot jumped to
+  int32_t pbuf;     // prefetch buffer holding it, -1: read the cache record
+  uint32_t parity;  // that buffer's mbarrier phase parity
 };
 
 // NARROW: Delta E and the acceptance penalty in int32 (the host checked
@@ -267,7 +293,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // LA = -1: the cache is read in place, nothing is prefetched.
   const int NB = LA + 2;
   const bool pf = fc && LA >= 0;
-  const uint32_t RB = (uint32_t)(LA + 3);  // draw ring: t % RB
   const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
                     de_smem, NARROW};
   const SmemLayout lay = smem_layout(n, m, W, s, Tw, B, P);
@@ -278,6 +303,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int32_t *sM = reinterpret_cast<int32_t *>(smem + lay.M);
   uint32_t *sMask = reinterpret_cast<uint32_t *>(smem + lay.mask);
   uint32_t *sAmask = reinterpret_cast<uint32_t *>(smem + lay.amask);
+  // Rings of kRing iterations: sRnd[(t % kRing) * 4 + j] holds the draw of
+  // tag kTagSelect + j of iteration t, sSch[t % kRing] its schedule entry.
   uint32_t *sRnd = reinterpret_cast<uint32_t *>(smem + lay.rnd);
   SchEntry *sSch = reinterpret_cast<SchEntry *>(smem + lay.sch);
   // Row and column counts of the last rebuilt state, two buffers used in
@@ -285,7 +312,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int32_t *sRC = reinterpret_cast<int32_t *>(smem + lay.RC);
   int64_t *sRed = reinterpret_cast<int64_t *>(smem + lay.red);
   Bcast *bc = reinterpret_cast<Bcast *>(smem + lay.bc);
-  Decision *dec = reinterpret_cast<Decision *>(smem + lay.dec);
   uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
   uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
   dE2_t *sDE = reinterpret_cast<dE2_t *>(smem + lay.dE);  // [bits]
@@ -294,6 +320,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // = the archive slot that iteration wrote (-1 = none).
   PfRec *sPf = reinterpret_cast<PfRec *>(smem + lay.red);
   int32_t *sWr = reinterpret_cast<int32_t *>(smem + lay.red + 8 * sizeof(PfRec));
+  JumpRec *sJr = reinterpret_cast<JumpRec *>(smem + lay.jr);  // [t % 8]
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
@@ -316,25 +343,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     sD[e] = A.D[e];
   }
   for (int e = tid; e < 4 * n; e += T) sRC[e] = 0;
+  // Control warp: draws (select, restart, exploit) and schedule entries of
+  // iterations first .. first + 7 into the rings, all lanes on one path:
+  // lane l < 24 draws tag kTagSelect + l % 3 of iteration first + l / 3,
+  // lane l < 8 copies the schedule entry of iteration first + l.
+  auto fill_rings = [&](uint32_t first) {
+    const uint32_t it = first + (uint32_t)(lane & 7);
+    const uint32_t sn = (it <= nsched ? it : nsched) - 1;
+    const double sd = A.sch_delta[sn];
+    const int64_t slo = A.sch_lo[sn], shi = A.sch_hi[sn];
+    const uint32_t q = first + (uint32_t)(lane < 24 ? lane / 3 : 7);
+    const uint32_t tag = (uint32_t)(lane % 3);
+    uint32_t c[4] = {0u, q, rep, kTagSelect + tag};
+    philox10(c, k0, k1);
+    if (lane < 24) sRnd[(q % kRing) * 4 + tag] = c[0];
+    if (lane < 8)
+      sSch[it % kRing] = SchEntry{sd, slo, shi, (int32_t)(slo < 2147483647ll ? slo : 2147483647ll),
+                                  (int32_t)(shi < 2147483647ll ? shi : 2147483647ll)};
+  };
   if (control) {
-    if (lane == 0) {
-      bc->fail = 0;
-      if (pf) {
-        for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
-        fence_mbar_init();
-      }
-      const SchEntry e1{A.sch_delta[0], A.sch_lo[0], A.sch_hi[0], 0};
-      sSch[1] = e1;  // iteration 1
+    if (lane == 0 && pf) {
+      for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
+      fence_mbar_init();
     }
-    // Draws (select, restart, exploit) of iteration t live in sRnd[t % RB];
-    // they are drawn LA + 1 iterations ahead.
-    if (lane < 3) {
-      for (uint32_t q = 1; (int)q <= LA + 1; ++q) {
-        uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
-        philox10(c, k0, k1);
-        sRnd[(q % RB) * 4 + lane] = c[0];
-      }
-    }
+    fill_rings(1);  // iterations 1..8; iteration t = 8i + 1 fills t+8..t+15
   }
 
   // Own bit k is valid when worker && k*Tw + tid < m: own[k] packs its
@@ -461,25 +493,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
   int64_t Eoff = 0;
   int acount = 0;
+  int fail = 0;  // a bounded wait gave up (OR-reduced at every iteration)
   uint32_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
   uint32_t st_pf = 0, st_direct = 0;
   int flip_streak = 0;  // consecutive flip iterations: no prefetch while hot
   // Control lane 0's copy bookkeeping: buffer b has a copy in flight when
   // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
   uint32_t pend = 0, ph = 0;
+  JumpRec jr{kNone, 0, -1, 0};
+  // schedule entry of the current iteration, in registers
+  double cur_delta;
+  dE_t cur_lo, cur_hi;
+  {
+    const SchEntry e = sSch[1];
+    cur_delta = e.delta;
+    cur_lo = NARROW ? (dE_t)e.lo32 : (dE_t)e.lo;
+    cur_hi = NARROW ? (dE_t)e.hi32 : (dE_t)e.hi;
+  }
 
   for (uint32_t t = 1; t <= I_max; ++t) {
     const int buf = (int)(t & 1u);
     uint32_t *mask = sMask + buf * items;        // accept ballots
     uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
-    const uint32_t *rnd = sRnd + (t % RB) * 4;
 
     if (worker) {
       // ---- workers: the parallel trial of their bits --------------------
-      const SchEntry se = sSch[buf];
-      const double delta = se.delta;
-      const dE_t lo = NARROW ? (dE_t)(se.lo < 2147483647ll ? se.lo : 2147483647ll) : (dE_t)se.lo;
-      const dE_t hi = NARROW ? (dE_t)(se.hi < 2147483647ll ? se.hi : 2147483647ll) : (dE_t)se.hi;
+      const double delta = cur_delta;
+      const dE_t lo = cur_lo, hi = cur_hi;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         bool acc = false;
@@ -519,20 +559,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
       }
     } else {
-      // ---- control warp: schedule, draws, prefetch ----------------------
-      SchEntry nx{};
-      if (lane == 31) {  // schedule entry of iteration t + 1
-        const uint32_t sn = (t + 1 <= nsched ? t + 1 : nsched) - 1;
-        nx.delta = A.sch_delta[sn];
-        nx.lo = A.sch_lo[sn];
-        nx.hi = A.sch_hi[sn];
-      }
-      if (lane < 3) {  // draws of iteration t + LA + 1
-        const uint32_t q = (uint32_t)((int64_t)t + LA + 1);
-        uint32_t c[4] = {0u, q, rep, kTagSelect + (uint32_t)lane};
-        philox10(c, k0, k1);
-        sRnd[(q % RB) * 4 + lane] = c[0];
-      }
+      // ---- control warp: draws, schedule and prefetch -------------------
+      if (t % 8u == 1u) fill_rings(t + 8);
       if (pf && lane == 0) {
         // Copy for the jump iteration t + LA would make.  A slot written in
         // the previous iteration is left alone: its writes are ordered for
@@ -542,13 +570,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= I_max;
         int slot_p = 0;
         if (issue) {
-          slot_p = pick(sRnd[(tt % RB) * 4 + 1], acount);
+          slot_p = pick(sRnd[(tt % kRing) * 4 + 1], acount);
           if (sWr[(t - 1) & 7] == slot_p) issue = false;
         }
         uint32_t par = 0;
         if (issue) {
           if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
-            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
+            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
             ph ^= 1u << b;
             pend &= ~(1u << b);
           }
@@ -574,63 +602,65 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
         sWr[t & 7] = -1;  // set to the written slot by a flip below
       }
-      if (lane == 31) sSch[1 - buf] = nx;
-    }
-    __syncthreads();
-
-    // ---- control warp: the decision ------------------------------------
-    if (control) {
-      int cnt = 0;
-      for (int q = lane; q < items; q += 32) cnt += __popc(mask[q]);
-      const int total = __reduce_add_sync(kFull, cnt);
-      Decision d{kNone, 0, 0, 0, -1, 0, 0, 0};
-      if (total > 0) {
-        int incl, c2;
-        warp_mask_total(mask, items, lane, incl, c2);
-        d.kind = kFlip;
-        d.ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, c2, pick(rnd[0], total));
-        if (de_smem) {
-          const int kk = d.ps / Tw, rr = d.ps - kk * Tw;
-          const dE2_t v = sDE[d.ps];
-          d.dE1 = (int64_t)v.x;
-          d.dE2 = (int64_t)v.y;
-          d.sgn = 1 - 2 * (int)((xm[kk * NWB + (rr >> 5)] >> (rr & 31)) & 1u);
-        }
-      } else if (A.escape == 0 && acount > 0) {
-        d.kind = kJump;
-        d.slot = pick(rnd[1], acount);
+      __syncwarp();
+      // The jump iteration t makes if it accepts no bit (its draw and |A|
+      // are known now).  Its copy is usable if it was started LA iterations
+      // ago for this slot and no iteration since rewrote that slot.
+      jr = JumpRec{kNone, 0, -1, 0};
+      if (A.escape == 0 && acount > 0) {
+        jr.kind = kJump;
+        jr.slot = pick(sRnd[(t % kRing) * 4 + 1], acount);
         if (pf) {
-          // The copy for this iteration is usable if it was started LA
-          // iterations ago for this slot and no iteration since rewrote it.
           const PfRec rec = sPf[t & 7];
-          bool ok = rec.iter != 0 && rec.slot == d.slot && (uint32_t)rec.iter + LA == t;
+          bool ok = rec.iter != 0 && rec.slot == jr.slot && (uint32_t)rec.iter + LA == t;
           for (uint32_t x = (uint32_t)rec.iter; ok && x < t; ++x)
-            if (sWr[x & 7] == d.slot) ok = false;
+            if (sWr[x & 7] == jr.slot) ok = false;
           if (ok) {
-            const int b = (int)(t % (uint32_t)NB);
-            if (!mbar_wait(&sBar[b], (uint32_t)rec.parity)) bc->fail = 1;
-            if (lane == 0) {
-              ph ^= 1u << b;
-              pend &= ~(1u << b);
-            }
-            d.buf = b;
-            d.parity = rec.parity;
+            jr.pbuf = (int)(t % (uint32_t)NB);
+            jr.parity = (uint32_t)rec.parity;
           }
         }
       }
-      if (lane == 0) *dec = d;
+      if (lane == 0) sJr[t & 7] = jr;
     }
-    __syncthreads();
-    if (fc && bc->fail) break;  // a bulk copy did not complete (uniform)
+    if (__syncthreads_or(fail)) break;  // a bounded wait gave up (uniform)
+    // schedule entry of the next iteration, loaded early
+    const SchEntry nse = sSch[(t + 1) % kRing];
+
+    // ---- every warp: the decision (the same in all of them) -------------
+    const uint32_t *rnd = sRnd + (t % kRing) * 4;
+    int kind, ps = 0;
+    {
+      int cnt;
+      const int total = warp_mask_count(mask, items, lane, cnt);
+      if (total > 0) {
+        kind = kFlip;
+        if (worker) {
+          const int incl = warp_incl_scan(cnt, lane);
+          ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, cnt, pick(rnd[0], total));
+        }
+      } else {
+        if (worker) jr = sJr[t & 7];
+        kind = jr.kind;
+        if (control && lane == 0 && jr.pbuf >= 0) {  // the copy is consumed
+          ph ^= 1u << jr.pbuf;
+          pend &= ~(1u << jr.pbuf);
+        }
+      }
+    }
 
     // ---- all: carry out the decision ------------------------------------
-    const Decision d = *dec;
     int64_t event = INT64_MIN;
-    if (d.kind == kFlip) {
-      const int ps = d.ps;
-      int64_t dE1 = d.dE1, dE2 = d.dE2;
-      int sg = d.sgn;
-      if (!de_smem) {
+    if (kind == kFlip) {
+      int64_t dE1, dE2;
+      int sg;
+      if (de_smem) {
+        const dE2_t v = sDE[ps];
+        dE1 = (int64_t)v.x;
+        dE2 = (int64_t)v.y;
+        // ballot word of bit ps: (round, warp) = ps / 32 because Tw % 32 == 0
+        sg = 1 - 2 * (int)((xm[ps >> 5] >> (ps & 31)) & 1u);
+      } else {
         const int kk = ps / Tw;
         if (ps - kk * Tw == tid) {  // the owner publishes Delta E and its sign
 #pragma unroll
@@ -735,45 +765,45 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       Eoff = 0;
       ++st_flip;
       event = ps;
-    } else if (d.kind == kJump) {
+    } else if (kind == kJump) {
       // Alg. 3: jump to a random archive member.
-      const int slot = d.slot;
+      const int slot = jr.slot, pbuf = jr.pbuf;
       if (fc) {
-        const dE2_t *rf;
-        const uint32_t *wsrc;
-        longlong2 se;
-        if (d.buf >= 0) {
-          unsigned char *pb = smem + lay.pf + (size_t)d.buf * lay.pf_slot;
-          // the control warp saw the copy complete; this observes it too
-          if (worker) mbar_wait(&sBar[d.buf], (uint32_t)d.parity);
-          rf = reinterpret_cast<const dE2_t *>(pb);
-          se = A.energies_in_smem ? aE[slot]
-                                  : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
-          if (A.bits_in_smem) {
+        if (worker) {
+          const dE2_t *rf;
+          const uint32_t *wsrc;
+          longlong2 se;
+          if (pbuf >= 0) {
+            unsigned char *pb = smem + lay.pf + (size_t)pbuf * lay.pf_slot;
+            if (!mbar_wait(&sBar[pbuf], jr.parity)) fail = 1;
+            rf = reinterpret_cast<const dE2_t *>(pb);
+            se = A.energies_in_smem ? aE[slot]
+                                    : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
+            if (A.bits_in_smem) {
+              wsrc = aBits + (size_t)slot * W;
+            } else {
+              const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
+              wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
+            }
+          } else {  // read the record where it is
+            rf = reinterpret_cast<const dE2_t *>(gF + (size_t)slot * sl.bytes);
+            se = aE[slot];
             wsrc = aBits + (size_t)slot * W;
-          } else {
-            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
-            wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
           }
-          ++st_pf;
-        } else {  // read the record where it is
-          rf = reinterpret_cast<const dE2_t *>(gF + (size_t)slot * sl.bytes);
-          se = aE[slot];
-          wsrc = aBits + (size_t)slot * W;
-          ++st_direct;
-        }
-        E1 = se.x;
-        E2 = se.y;
-        xmask = 0;
+          E1 = se.x;
+          E2 = se.y;
+          xmask = 0;
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-          if (!valid(k)) continue;
-          const int q = k * Tw + tid;
-          const dE2_t v2 = rf[q];
-          D1[k] = v2.x;
-          D2[k] = v2.y;
-          xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
+          for (int k = 0; k < B; ++k) {
+            if (!valid(k)) continue;
+            const int q = k * Tw + tid;
+            const dE2_t v2 = rf[q];
+            D1[k] = v2.x;
+            D2[k] = v2.y;
+            xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
+          }
         }
+        if (pbuf >= 0) ++st_pf; else ++st_direct;
       } else {
         const longlong2 se = aE[slot];
         E1 = se.x;
@@ -789,7 +819,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       Eoff += A.beta;
       ++st_off;
     }
-    flip_streak = d.kind == kFlip ? flip_streak + 1 : 0;
+    flip_streak = kind == kFlip ? flip_streak + 1 : 0;
+    cur_delta = nse.delta;
+    cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
+    cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;
     if (A.trace != nullptr && tid == 0) {
       int64_t *tr = A.trace + ((size_t)rb * (size_t)I_max + (size_t)(t - 1)) * 3;
       tr[0] = E1;
@@ -797,15 +830,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       tr[2] = event;
     }
   }
-
   // No bulk copy may be in flight when the block exits.
   if (pf && control && lane == 0) {
     for (int b = 0; b < NB; ++b)
       if ((pend >> b) & 1u)
-        if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) bc->fail = 1;
+        if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
   }
-  __syncthreads();
-  if (tid == 0 && bc->fail) atomicExch(A.error, kErrCopyTimeout);
+  if (__syncthreads_or(fail) && tid == 0) atomicExch(A.error, kErrCopyTimeout);
   if (worker) {
 #pragma unroll
     for (int k = 0; k < B; ++k) {

@@ -62,6 +62,7 @@ typedef enum {
 
 typedef struct moda_instance_s *moda_instance;
 typedef struct moda_run_s *moda_run;
+typedef struct moda_server_s *moda_server;
 
 /* Sec. 3.3: strict = product of the per-objective probabilities
  * (Eq. pacceptms); lenient = their maximum (Eq. pacceptml). */
@@ -140,6 +141,19 @@ moda_status moda_instance_info(moda_instance inst, int32_t *n, int64_t *w1,
 moda_status moda_anneal(moda_instance inst, const moda_params *params,
                         void *cuda_stream, moda_run *out);
 
+/* Many anneals in one launch.  The paper solves each instance by a run of
+ * Alg. 3 (Sec. 4 runs its instances one after another); nothing in a run
+ * depends on another, so this call enqueues `count` of them -- request i is
+ * exactly moda_anneal(insts[i], &params[i]) -- as one CUDA graph launch on
+ * `cuda_stream` whose runs share no dependency, so the GPU runs the thread
+ * blocks of many instances side by side instead of one small grid at a
+ * time.  All instances live on one device.  outs[i] receives run i (owned
+ * by the caller, moda_destroy_run); each has its own device buffers and
+ * gives the same results as the plain call.  On failure nothing is
+ * enqueued, no run is returned and the message names the request. */
+moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *params,
+                              int32_t count, void *cuda_stream, moda_run *outs);
+
 /* Wait for a run: MODA_OK when it finished, MODA_ETIMEOUT when timeout_ms
  * (>= 0; < 0 waits forever) passed first, MODA_ECUDA on a device error. */
 moda_status moda_wait(moda_run run, int64_t timeout_ms);
@@ -185,6 +199,40 @@ moda_status moda_read_archive(moda_run run, int32_t r, moda_point *pts,
 moda_status moda_run_elapsed_ms(moda_run run, float *ms);
 
 void moda_destroy_run(moda_run run);
+
+/* ---- Serving ---------------------------------------------------------
+ *
+ * A queue of anneal requests served as they arrive (not in the paper:
+ * serving many bi-objective QAP solves on one GPU).  A native thread of the
+ * server admits waiting requests in arrival order while the device buffers
+ * of the runs in flight (the bytes moda_anneal would allocate for each) fit
+ * `hbm_budget`, and launches each admitted request at once on a stream of
+ * its own (or on `cuda_stream` if not NULL, which orders them), so new
+ * requests join the ones already running instead of waiting for a batch.
+ * A request whose buffers exceed the budget even when alone runs alone
+ * without the field cache (identical results) if that fits, else fails
+ * with MODA_ENOMEM.  Each request's results equal those of moda_anneal on
+ * the same instance and params.
+ *
+ *   hbm_budget  bytes for the buffers of runs in flight; 0 = the free
+ *               device memory at creation less max(1/8 of it, 1 GiB)
+ *   ticket      identifies a request; moda_server_poll sets *done to the
+ *               finished run (then owned by the caller, and no longer
+ *               counted against the budget) or to NULL while it waits or
+ *               runs; a failed request returns its error once.
+ *   instances   must outlive their requests.
+ *   destroy     cancels requests not yet started (their poll would fail),
+ *               waits for those running and frees finished runs nobody
+ *               polled. */
+moda_status moda_server_create(size_t hbm_budget, void *cuda_stream, moda_server *out);
+moda_status moda_server_submit(moda_server srv, moda_instance inst,
+                               const moda_params *params, int64_t *ticket);
+moda_status moda_server_poll(moda_server srv, int64_t ticket, moda_run *done);
+/* Queue state: requests waiting, requests running, bytes of their buffers
+ * and the budget (any pointer may be NULL). */
+moda_status moda_server_info(moda_server srv, int64_t *pending, int64_t *running,
+                             size_t *bytes_in_use, size_t *budget);
+void moda_server_destroy(moda_server srv);
 
 /* Thread-local message of the last failed call on this thread. */
 const char *moda_last_error(void);

@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -159,6 +162,7 @@ struct moda_run_s {
   int32_t *error = nullptr;
   unsigned char *fcache = nullptr;
   bool checked = false;
+  size_t bytes = 0;  // device memory held by the run's buffers
 };
 
 namespace {
@@ -173,6 +177,14 @@ void free_run_buffers(moda_run r) {
 }
 
 bool run_done(moda_run r) { return cudaEventQuery(r->stop) == cudaSuccess; }
+
+// A prepared launch: kernel arguments and launch shape.
+struct Prepared {
+  moda::AnnealArgs args;
+  int workers, rounds;
+  bool narrow;
+  size_t smem;
+};
 
 }  // namespace
 
@@ -285,9 +297,15 @@ moda_status moda_instance_info(moda_instance inst, int32_t *n, int64_t *w1,
   return MODA_OK;
 }
 
-moda_status moda_anneal(moda_instance inst, const moda_params *p,
-                        void *cuda_stream, moda_run *out) {
-  if (!out) return fail(MODA_EINVAL, "out is NULL");
+}  // extern "C"
+
+namespace {
+
+// Validates a request, chooses the block shape and shared-memory placement,
+// allocates the run's buffers and fills the kernel arguments; nothing is
+// enqueued.  On failure nothing is left allocated.
+moda_status prepare_run(moda_instance inst, const moda_params *p,
+                        cudaStream_t stream, moda_run *out, Prepared *pl) {
   *out = nullptr;
   if (!inst || !p) return fail(MODA_EINVAL, "NULL instance or params");
   const int m = inst->m;
@@ -390,13 +408,15 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   r->s = p->archive_size > 0 ? p->archive_size : m;
   r->threads = T;
   r->bpt = B;
-  r->stream = static_cast<cudaStream_t>(cuda_stream);
+  r->stream = stream;
 
   const size_t R = r->R, s = r->s, W = inst->W;
   moda_status st = MODA_OK;
-  auto alloc = [&](void **ptr, size_t bytes) {
+  size_t bytes = 0;
+  auto alloc = [&](void **ptr, size_t nb) {
     if (st != MODA_OK) return;
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    bytes += nb;
+    cudaError_t e = cudaMalloc(ptr, nb);
     if (e != cudaSuccess) st = fail(MODA_ENOMEM, std::string("device allocation: ") +
                                                      cudaGetErrorString(e));
   };
@@ -471,14 +491,50 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
 
   cudaError_t e = cudaEventCreate(&r->start);
   if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
-  if (e == cudaSuccess) e = cudaMemsetAsync(r->error, 0, sizeof(int32_t), r->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(r->start, r->stream);
-  if (e == cudaSuccess) e = moda::launch_anneal(a, r->R, T, B, place.narrow, lay.total, r->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(r->stop, r->stream);
   if (e != cudaSuccess) {
     free_run_buffers(r);
     delete r;
-    return cuda_fail(e, "launch");
+    return cuda_fail(e, "event");
+  }
+  pl->args = a;
+  pl->workers = T;
+  pl->rounds = B;
+  pl->narrow = place.narrow;
+  pl->smem = lay.total;
+  r->bytes = bytes;
+  *out = r;
+  return MODA_OK;
+}
+
+// Enqueues a prepared run on its stream: clear the status word, start
+// event, kernel, stop event.
+moda_status enqueue_run(moda_run r, const Prepared &pl) {
+  cudaError_t e = cudaMemsetAsync(r->error, 0, sizeof(int32_t), r->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(r->start, r->stream);
+  if (e == cudaSuccess)
+    e = moda::launch_anneal(pl.args, r->R, pl.workers, pl.rounds, pl.narrow, pl.smem, r->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(r->stop, r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launch");
+  return MODA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+moda_status moda_anneal(moda_instance inst, const moda_params *p,
+                        void *cuda_stream, moda_run *out) {
+  if (!out) return fail(MODA_EINVAL, "out is NULL");
+  *out = nullptr;
+  Prepared pl{};
+  moda_run r = nullptr;
+  moda_status st = prepare_run(inst, p, static_cast<cudaStream_t>(cuda_stream), &r, &pl);
+  if (st != MODA_OK) return st;
+  st = enqueue_run(r, pl);
+  if (st != MODA_OK) {
+    free_run_buffers(r);
+    delete r;
+    return st;
   }
   *out = r;
   return MODA_OK;
@@ -644,6 +700,332 @@ void moda_destroy_run(moda_run r) {
   free_run_buffers(r);
   cudaSetDevice(prev);
   delete r;
+}
+
+
+// ---- many instances in one graph launch ---------------------------------
+
+moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *params,
+                              int32_t count, void *cuda_stream, moda_run *outs) {
+  if (!insts || !params || !outs || count < 1)
+    return fail(MODA_EINVAL, "need instances, params, outs and count >= 1");
+  for (int32_t i = 0; i < count; ++i) outs[i] = nullptr;
+  for (int32_t i = 0; i < count; ++i)
+    if (!insts[i] || insts[i]->device != insts[0]->device)
+      return fail(MODA_EINVAL, "every instance must exist and live on one device");
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<moda_run> runs(count, nullptr);
+  std::vector<Prepared> pls(count);
+  auto release = [&]() {
+    for (moda_run r : runs)
+      if (r) {
+        free_run_buffers(r);
+        delete r;
+      }
+  };
+  for (int32_t i = 0; i < count; ++i) {
+    moda_status st = prepare_run(insts[i], &params[i], stream, &runs[i], &pls[i]);
+    if (st != MODA_OK) {
+      const std::string msg = "request " + std::to_string(i) + ": " + g_error;
+      release();
+      return fail(st, msg);
+    }
+  }
+  // One chain per run (start event, status word cleared, kernel, stop
+  // event); the chains share no edge, so blocks of many runs share the GPU.
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
+    moda_run r = runs[i];
+    const Prepared &pl = pls[i];
+    cudaGraphNode_t n0, n1, n2, n3;
+    const void *func = nullptr;
+    e = moda::anneal_function(pl.rounds, pl.narrow, pl.smem, &func);
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, r->start);
+    if (e == cudaSuccess) {
+      cudaMemsetParams mp{};
+      mp.dst = r->error;
+      mp.value = 0;
+      mp.elementSize = sizeof(int32_t);
+      mp.width = 1;
+      mp.height = 1;
+      e = cudaGraphAddMemsetNode(&n1, g, &n0, 1, &mp);
+    }
+    if (e == cudaSuccess) {
+      void *kargs[1] = {const_cast<moda::AnnealArgs *>(&pl.args)};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void *>(func);
+      kp.gridDim = dim3((unsigned)r->R);
+      kp.blockDim = dim3((unsigned)(pl.workers + 32));
+      kp.sharedMemBytes = (unsigned)pl.smem;
+      kp.kernelParams = kargs;
+      kp.extra = nullptr;
+      e = cudaGraphAddKernelNode(&n2, g, &n1, 1, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n3, g, &n2, 1, r->stop);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, stream);
+  // both may go while the launch runs: an executable graph in flight is
+  // freed when it completes
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(stream);
+    release();
+    return cuda_fail(e, "batch graph");
+  }
+  for (int32_t i = 0; i < count; ++i) outs[i] = runs[i];
+  return MODA_OK;
+}
+
+}  // extern "C"
+
+// ---- serving ------------------------------------------------------------
+
+namespace {
+
+// Device bytes a run of `p` on `inst` allocates, with or without the field
+// cache (the same buffers as prepare_run).
+size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
+  const size_t R = (size_t)p.replicas, m = (size_t)inst->m, W = (size_t)inst->W;
+  const size_t s = p.archive_size > 0 ? (size_t)p.archive_size : m;
+  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
+  size_t b = R * s * 2 * sizeof(int64_t) + R * s * W * sizeof(uint32_t) + 32 +
+             R * sizeof(int32_t) + R * W * sizeof(uint32_t) + R * 2 * sizeof(int64_t) +
+             R * moda::kStats * sizeof(int64_t) + sizeof(int32_t);
+  if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2)
+    b += R * s * moda::slot_layout((int)m, narrow).bytes;
+  if (p.trace && p.I_max > 0) b += R * (size_t)p.I_max * 3 * sizeof(int64_t);
+  return b;
+}
+
+struct Request {
+  int64_t ticket = 0;
+  moda_instance inst = nullptr;
+  moda_params prm{};
+  enum State { kPending, kRunning, kDone, kFailed } state = kPending;
+  moda_run run = nullptr;
+  size_t bytes = 0;
+  moda_status err = MODA_OK;
+  std::string msg;
+};
+
+}  // namespace
+
+struct moda_server_s {
+  int device = 0;
+  size_t budget = 0, in_use = 0;
+  cudaStream_t user_stream = nullptr;
+  std::vector<cudaStream_t> streams;
+  size_t next_stream = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Request>> pending;
+  std::vector<std::shared_ptr<Request>> running;
+  std::map<int64_t, std::shared_ptr<Request>> tickets;
+  std::thread worker;
+  bool stopping = false;
+  int64_t next_ticket = 1;
+  int64_t admitted = 0, completed = 0;
+};
+
+namespace {
+
+constexpr int kServerStreams = 32;
+
+// The server's thread: retires finished runs (their bytes return to the
+// budget) and admits waiting requests in arrival order while their buffers
+// fit the budget, each on a stream of its own, so a request starts as soon
+// as memory allows, beside those already running.
+void server_loop(moda_server_s *S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lock(S->mu);
+  for (;;) {
+    for (size_t i = 0; i < S->running.size();) {
+      auto &q = S->running[i];
+      const cudaError_t e = cudaEventQuery(q->run->stop);
+      if (e == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      if (e != cudaSuccess) {
+        q->state = Request::kFailed;
+        q->err = MODA_ECUDA;
+        q->msg = std::string("run: ") + cudaGetErrorString(e);
+      } else {
+        q->state = Request::kDone;
+      }
+      S->in_use -= q->bytes;
+      ++S->completed;
+      S->running.erase(S->running.begin() + (long)i);
+    }
+    while (!S->pending.empty()) {
+      std::shared_ptr<Request> q = S->pending.front();
+      if (S->stopping) {  // not started: cancelled
+        q->state = Request::kFailed;
+        q->err = MODA_EINVAL;
+        q->msg = "server destroyed before the request started";
+        S->pending.pop_front();
+        continue;
+      }
+      moda_params prm = q->prm;
+      const size_t full = run_bytes(q->inst, prm, true);
+      const size_t lean = run_bytes(q->inst, prm, false);
+      if (S->in_use + full > S->budget) {
+        if (!S->running.empty()) break;  // wait for memory
+        if (lean > S->budget) {
+          q->state = Request::kFailed;
+          q->err = MODA_ENOMEM;
+          q->msg = "request needs " + std::to_string(lean) + " bytes, budget " +
+                   std::to_string(S->budget);
+          S->pending.pop_front();
+          continue;
+        }
+        prm.field_cache = 2;  // alone and without the cache it fits
+      }
+      S->pending.pop_front();
+      cudaStream_t st = S->user_stream;
+      if (!st) {
+        st = S->streams[S->next_stream];
+        S->next_stream = (S->next_stream + 1) % S->streams.size();
+      }
+      Prepared pl{};
+      moda_run r = nullptr;
+      moda_status rs = prepare_run(q->inst, &prm, st, &r, &pl);
+      if (rs == MODA_OK) {
+        rs = enqueue_run(r, pl);
+        if (rs != MODA_OK) {
+          free_run_buffers(r);
+          delete r;
+          r = nullptr;
+        }
+      }
+      if (rs != MODA_OK) {
+        q->state = Request::kFailed;
+        q->err = rs;
+        q->msg = g_error;
+        continue;
+      }
+      q->run = r;
+      q->bytes = r->bytes;
+      q->state = Request::kRunning;
+      S->in_use += r->bytes;
+      ++S->admitted;
+      S->running.push_back(q);
+    }
+    if (S->stopping && S->pending.empty() && S->running.empty()) break;
+    S->cv.wait_for(lock, std::chrono::microseconds(S->running.empty() ? 2000 : 100));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+moda_status moda_server_create(size_t hbm_budget, void *cuda_stream, moda_server *out) {
+  if (!out) return fail(MODA_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto *S = new (std::nothrow) moda_server_s;
+  if (!S) return fail(MODA_ENOMEM, "host allocation");
+  cudaGetDevice(&S->device);
+  S->budget = hbm_budget;
+  if (S->budget == 0) {  // free memory less a reserve of 1/8 (at least 1 GiB)
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+      delete S;
+      return cuda_fail(e, "cudaMemGetInfo");
+    }
+    const size_t reserve = std::max<size_t>(free_b / 8, size_t(1) << 30);
+    S->budget = free_b > reserve ? free_b - reserve : 0;
+  }
+  S->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  if (!S->user_stream) {
+    for (int i = 0; i < kServerStreams; ++i) {
+      cudaStream_t st = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+        delete S;
+        return cuda_fail(e, "stream");
+      }
+      S->streams.push_back(st);
+    }
+  }
+  try {
+    S->worker = std::thread(server_loop, S);
+  } catch (...) {
+    for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+    delete S;
+    return fail(MODA_ENOMEM, "server thread");
+  }
+  *out = S;
+  return MODA_OK;
+}
+
+moda_status moda_server_submit(moda_server S, moda_instance inst, const moda_params *p,
+                               int64_t *ticket) {
+  if (!S || !inst || !p || !ticket) return fail(MODA_EINVAL, "NULL argument");
+  if (inst->device != S->device) return fail(MODA_EINVAL, "instance on another device");
+  auto q = std::make_shared<Request>();
+  q->inst = inst;
+  q->prm = *p;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stopping) return fail(MODA_EINVAL, "server is shutting down");
+    q->ticket = S->next_ticket++;
+    S->pending.push_back(q);
+    S->tickets[q->ticket] = q;
+    *ticket = q->ticket;
+  }
+  S->cv.notify_one();
+  return MODA_OK;
+}
+
+moda_status moda_server_poll(moda_server S, int64_t ticket, moda_run *done) {
+  if (!S || !done) return fail(MODA_EINVAL, "NULL argument");
+  *done = nullptr;
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->tickets.find(ticket);
+  if (it == S->tickets.end()) return fail(MODA_EINVAL, "unknown ticket");
+  std::shared_ptr<Request> q = it->second;
+  if (q->state == Request::kDone) {
+    *done = q->run;
+    S->tickets.erase(it);
+    return MODA_OK;
+  }
+  if (q->state == Request::kFailed) {
+    S->tickets.erase(it);
+    return fail(q->err, q->msg);
+  }
+  return MODA_OK;
+}
+
+moda_status moda_server_info(moda_server S, int64_t *pending, int64_t *running,
+                             size_t *bytes_in_use, size_t *budget) {
+  if (!S) return fail(MODA_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(S->mu);
+  if (pending) *pending = (int64_t)S->pending.size();
+  if (running) *running = (int64_t)S->running.size();
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  if (budget) *budget = S->budget;
+  return MODA_OK;
+}
+
+void moda_server_destroy(moda_server S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stopping = true;
+  }
+  S->cv.notify_one();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto &kv : S->tickets)
+    if (kv.second->state == Request::kDone && kv.second->run) moda_destroy_run(kv.second->run);
+  for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+  delete S;
 }
 
 }  // extern "C"

@@ -154,6 +154,12 @@ cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
                           int rounds, bool narrow, size_t smem_bytes,
                           cudaStream_t stream);
 
+// The kernel for `rounds` bits per thread (one block of workers + 32
+// threads per replica, `smem` bytes of dynamic shared memory, which this
+// call allows), for launching from a CUDA graph node with one AnnealArgs
+// argument.
+cudaError_t anneal_function(int rounds, bool narrow, size_t smem, const void **func);
+
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);
 inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }

@@ -522,34 +522,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       const dE_t lo = cur_lo, hi = cur_hi;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        bool acc = false;
-        if (k * Tw + tid < m) {
-          const dE_t e1 = D1[k], e2 = D2[k];
-          dE_t a1, a2;
-          if (A.escape == 1) {  // the offset lowers Delta E (Alg. 1)
-            const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
-            a1 = e1 > off ? e1 - off : 0;
-            a2 = e2 > off ? e2 - off : 0;
-          } else {
-            a1 = e1 > 0 ? e1 : 0;
-            a2 = e2 > 0 ? e2 : 0;
-          }
-          const dE_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
-          if (a <= lo) {
-            acc = true;
-          } else if (a <= hi) {
-            const int p = k * Tw + tid;
-            uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
-            philox10(c, k0, k1);
-            const uint32_t w = word_of(c, p & 3);
-            acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
-          }
-          if (acc && de_smem) {
-            dE2_t v;
-            v.x = e1;
-            v.y = e2;
-            sDE[k * Tw + tid] = v;
-          }
+        const dE_t e1 = D1[k], e2 = D2[k];
+        dE_t a1, a2;
+        if (A.escape == 1) {  // the offset lowers Delta E (Alg. 1)
+          const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
+          a1 = e1 > off ? e1 - off : 0;
+          a2 = e2 > off ? e2 - off : 0;
+        } else {
+          a1 = e1 > 0 ? e1 : 0;
+          a2 = e2 > 0 ? e2 : 0;
+        }
+        const dE_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
+        const bool in = k * Tw + tid < m;
+        bool acc = in && a <= lo;
+        // a in (lo, hi]: the draw decides (warp-uniform branch; cold
+        // iterations rarely take it)
+        const bool need = in && a > lo && a <= hi;
+        if (__any_sync(kFull, need)) {
+          const int p = k * Tw + tid;
+          uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
+          philox10(c, k0, k1);
+          const uint32_t w = word_of(c, p & 3);
+          if (need) acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
+        }
+        if (acc && de_smem) {
+          dE2_t v;
+          v.x = e1;
+          v.y = e2;
+          sDE[k * Tw + tid] = v;
         }
         const uint32_t bal = __ballot_sync(kFull, acc);
         if (lane == 0) mask[k * NWB + warp] = bal;
@@ -888,10 +888,31 @@ cudaError_t launch_b(const AnnealArgs &args, int replicas, int workers, bool nar
                 : launch_bn<B, false>(args, replicas, workers, smem, stream);
 }
 
+template <int B>
+cudaError_t function_b(bool narrow, size_t smem, const void **func) {
+  const void *f = narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true>)
+                         : reinterpret_cast<const void *>(anneal_kernel<B, false>);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) *func = f;
+  return e;
+}
+
 }  // namespace
 
 bool supported_rounds(int b) {
   return b == 1 || b == 2 || b == 3 || b == 4 || b == 6 || b == 8;
+}
+
+cudaError_t anneal_function(int rounds, bool narrow, size_t smem, const void **func) {
+  switch (rounds) {
+    case 1: return function_b<1>(narrow, smem, func);
+    case 2: return function_b<2>(narrow, smem, func);
+    case 3: return function_b<3>(narrow, smem, func);
+    case 4: return function_b<4>(narrow, smem, func);
+    case 6: return function_b<6>(narrow, smem, func);
+    case 8: return function_b<8>(narrow, smem, func);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,

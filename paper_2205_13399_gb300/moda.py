@@ -30,7 +30,9 @@ ABI_FUNCTIONS = [
     "moda_create_instance", "moda_destroy_instance", "moda_instance_info",
     "moda_anneal", "moda_wait", "moda_read_replica", "moda_read_trace",
     "moda_read_archive", "moda_run_elapsed_ms", "moda_destroy_run",
-    "moda_last_error", "moda_anneal_noalloc",
+    "moda_last_error", "moda_anneal_noalloc", "moda_anneal_batch",
+    "moda_server_create", "moda_server_submit", "moda_server_poll", "moda_server_info",
+    "moda_server_destroy",
 ]
 
 
@@ -121,6 +123,21 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.moda_destroy_run.argtypes = [P]
     lib.moda_last_error.restype = ctypes.c_char_p
     lib.moda_last_error.argtypes = []
+    lib.moda_anneal_batch.restype = st
+    lib.moda_anneal_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Params), i32, P,
+                                      ctypes.POINTER(P)]
+    sz = ctypes.c_size_t
+    lib.moda_server_create.restype = st
+    lib.moda_server_create.argtypes = [sz, P, ctypes.POINTER(P)]
+    lib.moda_server_submit.restype = st
+    lib.moda_server_submit.argtypes = [P, P, ctypes.POINTER(Params), ctypes.POINTER(i64)]
+    lib.moda_server_poll.restype = st
+    lib.moda_server_poll.argtypes = [P, i64, ctypes.POINTER(P)]
+    lib.moda_server_info.restype = st
+    lib.moda_server_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(sz), ctypes.POINTER(sz)]
+    lib.moda_server_destroy.restype = None
+    lib.moda_server_destroy.argtypes = [P]
     lib.moda_anneal_noalloc.restype = st
     lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
                                         ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
@@ -313,3 +330,64 @@ def anneal(inst: Instance, params: Params | None = None, stream=None, **kw) -> R
     _check(_lib.moda_anneal(inst._h, ctypes.byref(params), _stream_handle(stream),
                             ctypes.byref(h)))
     return Run(inst, h, params)
+
+
+def anneal_batch(instances, params_list, stream=None) -> list[Run]:
+    """``moda_anneal_batch``: run i is ``anneal(instances[i], params_list[i])``;
+    all of them are enqueued as one CUDA graph launch on ``stream``."""
+    k = len(instances)
+    if k != len(params_list) or k == 0:
+        raise ValueError("need as many params as instances (at least one)")
+    hs = (ctypes.c_void_p * k)(*[inst._h for inst in instances])
+    ps = (Params * k)(*params_list)
+    outs = (ctypes.c_void_p * k)()
+    _check(_lib.moda_anneal_batch(hs, ps, k, _stream_handle(stream), outs))
+    return [Run(instances[i], ctypes.c_void_p(outs[i]), params_list[i]) for i in range(k)]
+
+
+class Server:
+    """``moda_server_*``: requests are admitted in arrival order while their
+    device buffers fit ``hbm_budget`` bytes (0: free memory less a reserve)
+    and run beside those already running."""
+
+    def __init__(self, hbm_budget: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        _check(_lib.moda_server_create(int(hbm_budget), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self._req = {}
+
+    def submit(self, inst: Instance, params: Params | None = None, **kw) -> int:
+        if params is None:
+            params = make_params(**kw)
+        t = ctypes.c_int64()
+        _check(_lib.moda_server_submit(self._h, inst._h, ctypes.byref(params), ctypes.byref(t)))
+        self._req[t.value] = (inst, params)
+        return t.value
+
+    def poll(self, ticket: int):
+        """The finished Run of ``ticket``, or None while it waits or runs."""
+        h = ctypes.c_void_p()
+        st = _lib.moda_server_poll(self._h, int(ticket), ctypes.byref(h))
+        if st != OK:
+            self._req.pop(int(ticket), None)
+            _check(st)
+        if not h.value:
+            return None
+        inst, params = self._req.pop(int(ticket))
+        return Run(inst, h, params)
+
+    def info(self) -> dict:
+        pe, ru = ctypes.c_int64(), ctypes.c_int64()
+        used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.moda_server_info(self._h, ctypes.byref(pe), ctypes.byref(ru),
+                                     ctypes.byref(used), ctypes.byref(budget)))
+        return dict(pending=pe.value, running=ru.value, bytes_in_use=used.value,
+                    budget=budget.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.moda_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

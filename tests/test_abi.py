@@ -106,3 +106,24 @@ def test_null_arguments(lib):
     assert lib.moda_wait(None, ctypes.c_int64(0)) == 1
     lib.moda_last_error.restype = ctypes.c_char_p
     assert lib.moda_last_error()
+
+
+def test_batch_and_server_null_arguments(lib):
+    """Argument checks of the batch and serving entry points need no GPU."""
+    P = ctypes.c_void_p
+    out = ctypes.c_void_p()
+    lib.moda_anneal_batch.restype = ctypes.c_int
+    assert lib.moda_anneal_batch(None, None, 0, None, None) == 1
+    lib.moda_server_create.restype = ctypes.c_int
+    lib.moda_server_create.argtypes = [ctypes.c_size_t, P, P]
+    assert lib.moda_server_create(0, None, None) == 1
+    lib.moda_server_submit.restype = ctypes.c_int
+    t = ctypes.c_int64()
+    assert lib.moda_server_submit(None, None, None, ctypes.byref(t)) == 1
+    lib.moda_server_poll.restype = ctypes.c_int
+    lib.moda_server_poll.argtypes = [P, ctypes.c_int64, P]
+    assert lib.moda_server_poll(None, 1, ctypes.byref(out)) == 1
+    lib.moda_server_info.restype = ctypes.c_int
+    assert lib.moda_server_info(None, None, None, None, None) == 1
+    lib.moda_server_destroy.restype = None
+    lib.moda_server_destroy(None)

@@ -48,7 +48,13 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["moda", "reference"], default="moda")
-    ap.add_argument("--workload", default="P25", choices=["P8", "P25", "P50", "P75"])
+    ap.add_argument("--workload", default="P25",
+                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE"])
+    ap.add_argument("--instances", type=int, default=512, help="BATCH: instances")
+    ap.add_argument("--seq-instances", type=int, default=24,
+                    help="BATCH / SERVE: requests also run one at a time for comparison")
+    ap.add_argument("--requests", type=int, default=256, help="SERVE: requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="SERVE: arrivals per second")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
@@ -158,6 +164,26 @@ def cpu_baseline(workload: str, budget_threads: int | None = None):
                       f"{dt:.1f} s wall"}, dt
 
 
+def int_peak(sm_max_mhz, sms):
+    """Measured INT32 lane-op peak (moda_probe_int_peak) with the derived one."""
+    from paper_2205_13399_gb300 import moda
+    measured, _ = moda.probe_int_peak(20000)
+    smem, _ = moda.probe_smem_peak(20000)
+    derived = sms * INT_LANES_PER_SM * sm_max_mhz * 1e6
+    return measured, derived, smem
+
+
+def roofline_line(ops, seconds, sms, sm_max_mhz, per_unit):
+    measured, derived, smem = int_peak(sm_max_mhz, sms)
+    achieved = ops / seconds
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": measured / 1e12,
+            "unit": "Tops/s", "frac": achieved / measured, "traffic": None,
+            "kernel": "anneal_kernel", "per_unit": per_unit,
+            "peak_source": "measured: moda_probe_int_peak (INT32 lane-ops/s, all SMs)",
+            "peak_derived": derived / 1e12,
+            "smem_peak_GBps": smem / 1e9}
+
+
 def workload_config(workload, inst, run, extra=None):
     cfg = {"workload": f"{workload}: bi-objective QAP n={inst.n} ({inst.n * inst.n}-bit QUBO), "
                        f"{run['replicas']} replicas, I_max={run['I_max']}",
@@ -203,6 +229,172 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """512 instances of uneven size (n uniform in [10, 75]), 32 replicas
+    each, in one moda_anneal_batch graph launch per step; a subset also runs
+    as plain launches one after another for comparison."""
+    import torch
+    from paper_2205_13399_gb300 import inputs, moda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    I_max = args.I_max if args.I_max is not None else 100_000
+    qis = inputs.batch_instances(args.instances)
+    insts = [moda.Instance(q.F1, q.F2, q.D) for q in qis]
+    params = [moda.make_params(replicas=32, I_max=I_max, seed=k) for k in range(len(qis))]
+    warm = [moda.make_params(replicas=32, I_max=min(I_max, 1000), seed=k)
+            for k in range(len(qis))]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def batch(ps, subset=None):
+        ii = insts if subset is None else insts[:subset]
+        pp = ps if subset is None else ps[:subset]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        runs = moda.anneal_batch(ii, pp, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        for r in runs:
+            r.wait()
+            r.close()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        batch(warm)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ms.append(batch(params))
+    clk = clocks.stop()
+    rep_steps = sum(p.replicas for p in params) * I_max
+    value = rep_steps * args.steps / (sum(ms) / 1e3)
+    k = min(args.seq_instances, len(insts))
+    seq_ms = 0.0
+    for i in range(k):
+        r = moda.anneal(insts[i], params[i], stream=stream).wait()
+        seq_ms += r.elapsed_ms()
+        r.close()
+    sub_ms = batch(params, subset=k)
+    sub_steps = sum(p.replicas for p in params[:k]) * I_max
+    # end to end: instance upload, the batch, merged fronts read back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ii = [moda.Instance(q.F1, q.F2, q.D) for q in qis]
+    runs = moda.anneal_batch(ii, params, stream=stream)
+    npts = 0
+    for r in runs:
+        npts += len(r.wait().read_archive(-1, perms=False))
+        r.close()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(3 * q.n * q.n * 4 for q in qis)
+    d2h = npts * 40
+    props = torch.cuda.get_device_properties(dev)
+    ops = sum(p.replicas * I_max * q.n * q.n for p, q in zip(params, qis)) * OPS_PER_BIT_TRIAL
+    roofline = roofline_line(ops, statistics.mean(ms) / 1e3, props.multi_processor_count,
+                             clk.get("sm_max_mhz") or 2070.0,
+                             f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial")
+    ns = [q.n for q in qis]
+    line = {
+        "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"BATCH: {len(qis)} bi-objective QAP instances, n uniform in "
+                               f"[{min(ns)}, {max(ns)}], 32 replicas each, I_max={I_max}, "
+                               "one CUDA graph launch per step",
+                   "instances": len(qis), "replicas_each": 32, "I_max": I_max,
+                   "mean_bits": statistics.mean(n * n for n in ns),
+                   "warmup_I_max": min(I_max, 1000),
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "bit_trials_per_s": value * statistics.mean(n * n for n in ns),
+        "vs_sequential": {"instances": k, "batched_ms": sub_ms, "sequential_ms": seq_ms,
+                          "speedup": seq_ms / sub_ms},
+        "e2e": {"value": rep_steps / e2e_s, "unit": "replica-steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": 1},
+        "gpu_launches": len(qis) * args.steps, "roofline": roofline, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals (``--rate`` per second) of solves with n in {20, 30,
+    50, 75} and I_max in {10^4, 10^5}, 32 replicas each, through the serving
+    queue; latency is arrival to the poll that returns the finished run."""
+    import numpy as np
+    import torch
+    from paper_2205_13399_gb300 import inputs, moda
+    reqs = inputs.serving_requests(args.requests, rate_per_s=args.rate)
+    warm = inputs.serving_requests(max(args.warmup, 1) * 4, rate_per_s=args.rate,
+                                   index0=10_000_000)
+
+    def serve(rs):
+        srv = moda.Server()
+        t0 = time.perf_counter()
+        pending, lat, done_t = {}, [], []
+        nxt = 0
+        while nxt < len(rs) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(rs) and rs[nxt].arrival_s <= now:
+                q = rs[nxt]
+                inst = moda.Instance(q.instance.F1, q.instance.F2, q.instance.D)
+                t = srv.submit(inst, replicas=32, I_max=q.I_max, seed=q.seed)
+                pending[t] = (q, inst)
+                nxt += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    q, inst = pending.pop(t)
+                    r.read_archive(-1, perms=False)
+                    fin = time.perf_counter() - t0
+                    lat.append(fin - q.arrival_s)
+                    done_t.append(fin)
+                    r.close()
+            time.sleep(0.0005)
+        srv.close()
+        return np.array(lat), max(done_t)
+
+    for _ in range(args.warmup):
+        serve(warm[:4])
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    lat, span = serve(reqs)
+    clk = clocks.stop()
+    value = len(reqs) / span
+    k = min(args.seq_instances, len(reqs))
+    t0 = time.perf_counter()
+    for q in reqs[:k]:
+        inst = moda.Instance(q.instance.F1, q.instance.F2, q.instance.D)
+        r = moda.anneal(inst, replicas=32, I_max=q.I_max, seed=q.seed).wait()
+        r.read_archive(-1, perms=False)
+        r.close()
+    seq = k / (time.perf_counter() - t0)
+    work = sum(32 * q.I_max for q in reqs)
+    line = {
+        "metric": "bQAP solves/s", "value": value, "unit": "solves/s", "n_gpus": 1,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": span * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"SERVE: {len(reqs)} requests, Poisson {args.rate:g}/s, n in "
+                               "{20, 30, 50, 75}, I_max in {1e4, 1e5}, 32 replicas each",
+                   "requests": len(reqs), "rate_per_s": args.rate,
+                   "admission": "HBM budget = free memory less max(1/8, 1 GiB)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                       "p99": float(np.percentile(lat, 99) * 1e3),
+                       "max": float(lat.max() * 1e3)},
+        "replica_steps_per_s": work / span,
+        "vs_one_at_a_time": {"requests": k, "solves_per_s": seq, "speedup": value / seq},
+        "e2e": {"value": value, "unit": "solves/s",
+                "h2d_bytes_per_step": sum(3 * q.instance.n ** 2 * 4 for q in reqs),
+                "d2h_bytes_per_step": None, "note": "serving is end to end by construction"},
+        "gpu_launches": len(reqs), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -210,6 +402,11 @@ def main(argv=None):
     world, rank, local = dist_env()
     import numpy as np
     import torch
+    if args.workload in ("BATCH", "SERVE"):
+        if world > 1:
+            raise SystemExit("BATCH and SERVE run on one GPU")
+        torch.cuda.set_device(local)
+        return run_batch(args) if args.workload == "BATCH" else run_serve(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -280,18 +477,11 @@ def main(argv=None):
 
     # Roofline of the annealing kernel: integer issue bound.
     props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
     sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_ops = sms * INT_LANES_PER_SM * sm_max_mhz * 1e6
     ops_per_launch = R * I_max * m * OPS_PER_BIT_TRIAL
-    mean_launch_s = statistics.mean(kernel_ms) / 1e3
-    achieved = ops_per_launch / mean_launch_s
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
-                "kernel": "anneal_kernel",
-                "per_unit": f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial",
-                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} INT32 lanes x "
-                               f"{sm_max_mhz:.0f} MHz (derived; no measured INT peak)"}
+    roofline = roofline_line(ops_per_launch, statistics.mean(kernel_ms) / 1e3,
+                             props.multi_processor_count, sm_max_mhz,
+                             f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial")
 
     line = {
         "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s",

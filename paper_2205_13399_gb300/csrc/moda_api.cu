@@ -303,9 +303,12 @@ namespace {
 
 // Validates a request, chooses the block shape and shared-memory placement,
 // allocates the run's buffers and fills the kernel arguments; nothing is
-// enqueued.  On failure nothing is left allocated.
+// enqueued.  On failure nothing is left allocated.  `budgeted`: the caller
+// has already budgeted device memory for the field cache, so an automatic
+// field cache is used without the free-memory check.
 moda_status prepare_run(moda_instance inst, const moda_params *p,
-                        cudaStream_t stream, moda_run *out, Prepared *pl) {
+                        cudaStream_t stream, moda_run *out, Prepared *pl,
+                        bool budgeted = false) {
   *out = nullptr;
   if (!inst || !p) return fail(MODA_EINVAL, "NULL instance or params");
   const int m = inst->m;
@@ -366,7 +369,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   const size_t cache_bytes =
       (size_t)p->replicas * s_cap * moda::slot_layout(m, narrow).bytes;
   bool want_cache = p->escape == MODA_ESC_ARCHIVE && p->field_cache != 2;
-  if (want_cache && p->field_cache == 0) {
+  if (want_cache && p->field_cache == 0 && !budgeted) {
     size_t free_b = 0, total_b = 0;
     MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
     want_cache = cache_bytes <= free_b / 10 * 6;
@@ -504,6 +507,21 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   r->bytes = bytes;
   *out = r;
   return MODA_OK;
+}
+
+// Device bytes a run of `p` on `inst` allocates, with or without the field
+// cache (the same buffers as prepare_run).
+size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
+  const size_t R = (size_t)p.replicas, m = (size_t)inst->m, W = (size_t)inst->W;
+  const size_t s = p.archive_size > 0 ? (size_t)p.archive_size : m;
+  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
+  size_t b = R * s * 2 * sizeof(int64_t) + R * s * W * sizeof(uint32_t) + 32 +
+             R * sizeof(int32_t) + R * W * sizeof(uint32_t) + R * 2 * sizeof(int64_t) +
+             R * moda::kStats * sizeof(int64_t) + sizeof(int32_t);
+  if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2)
+    b += R * s * moda::slot_layout((int)m, narrow).bytes;
+  if (p.trace && p.I_max > 0) b += R * (size_t)p.I_max * 3 * sizeof(int64_t);
+  return b;
 }
 
 // Enqueues a prepared run on its stream: clear the status word, start
@@ -714,6 +732,33 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     if (!insts[i] || insts[i]->device != insts[0]->device)
       return fail(MODA_EINVAL, "every instance must exist and live on one device");
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // Device memory for the whole batch: every run's own buffers first; then
+  // field caches (automatic ones) in order of size, smallest first, while
+  // they fit in 60 % of the free memory.
+  std::vector<moda_params> prm(params, params + count);
+  {
+    cudaSetDevice(insts[0]->device);
+    size_t free_b = 0, total_b = 0;
+    MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t lean = 0;
+    for (int32_t i = 0; i < count; ++i) lean += run_bytes(insts[i], prm[i], false);
+    if (lean > free_b / 10 * 9)
+      return fail(MODA_ENOMEM, "the batch needs " + std::to_string(lean) +
+                                   " bytes of run buffers; " + std::to_string(free_b) + " free");
+    size_t budget = free_b / 10 * 6 > lean ? free_b / 10 * 6 - lean : 0;
+    std::vector<std::pair<size_t, int32_t>> want;
+    for (int32_t i = 0; i < count; ++i)
+      if (prm[i].field_cache == 0 && prm[i].escape == MODA_ESC_ARCHIVE)
+        want.emplace_back(run_bytes(insts[i], prm[i], true) - run_bytes(insts[i], prm[i], false),
+                          i);
+    std::sort(want.begin(), want.end());
+    for (const auto &w : want) {
+      if (w.first <= budget)
+        budget -= w.first;
+      else
+        prm[w.second].field_cache = 2;
+    }
+  }
   std::vector<moda_run> runs(count, nullptr);
   std::vector<Prepared> pls(count);
   auto release = [&]() {
@@ -724,7 +769,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       }
   };
   for (int32_t i = 0; i < count; ++i) {
-    moda_status st = prepare_run(insts[i], &params[i], stream, &runs[i], &pls[i]);
+    moda_status st = prepare_run(insts[i], &prm[i], stream, &runs[i], &pls[i], true);
     if (st != MODA_OK) {
       const std::string msg = "request " + std::to_string(i) + ": " + g_error;
       release();
@@ -785,21 +830,6 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
 // ---- serving ------------------------------------------------------------
 
 namespace {
-
-// Device bytes a run of `p` on `inst` allocates, with or without the field
-// cache (the same buffers as prepare_run).
-size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
-  const size_t R = (size_t)p.replicas, m = (size_t)inst->m, W = (size_t)inst->W;
-  const size_t s = p.archive_size > 0 ? (size_t)p.archive_size : m;
-  const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
-  size_t b = R * s * 2 * sizeof(int64_t) + R * s * W * sizeof(uint32_t) + 32 +
-             R * sizeof(int32_t) + R * W * sizeof(uint32_t) + R * 2 * sizeof(int64_t) +
-             R * moda::kStats * sizeof(int64_t) + sizeof(int32_t);
-  if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2)
-    b += R * s * moda::slot_layout((int)m, narrow).bytes;
-  if (p.trace && p.I_max > 0) b += R * (size_t)p.I_max * 3 * sizeof(int64_t);
-  return b;
-}
 
 struct Request {
   int64_t ticket = 0;

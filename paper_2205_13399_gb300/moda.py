@@ -32,7 +32,7 @@ ABI_FUNCTIONS = [
     "moda_read_archive", "moda_run_elapsed_ms", "moda_destroy_run",
     "moda_last_error", "moda_anneal_noalloc", "moda_anneal_batch",
     "moda_server_create", "moda_server_submit", "moda_server_poll", "moda_server_info",
-    "moda_server_destroy",
+    "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak",
 ]
 
 
@@ -138,6 +138,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(sz), ctypes.POINTER(sz)]
     lib.moda_server_destroy.restype = None
     lib.moda_server_destroy.argtypes = [P]
+    for name in ("moda_probe_int_peak", "moda_probe_smem_peak"):
+        f = getattr(lib, name)
+        f.restype = st
+        f.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
     lib.moda_anneal_noalloc.restype = st
     lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
                                         ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
@@ -391,3 +395,19 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def probe_int_peak(iters: int = 20000, stream=None) -> tuple[float, float]:
+    """``moda_probe_int_peak``: (INT32 lane operations per second, kernel ms)."""
+    v, ms = ctypes.c_double(), ctypes.c_float()
+    _check(_lib.moda_probe_int_peak(int(iters), _stream_handle(stream), ctypes.byref(v),
+                                    ctypes.byref(ms)))
+    return float(v.value), float(ms.value)
+
+
+def probe_smem_peak(iters: int = 20000, stream=None) -> tuple[float, float]:
+    """``moda_probe_smem_peak``: (shared-memory load bytes per second, kernel ms)."""
+    v, ms = ctypes.c_double(), ctypes.c_float()
+    _check(_lib.moda_probe_smem_peak(int(iters), _stream_handle(stream), ctypes.byref(v),
+                                     ctypes.byref(ms)))
+    return float(v.value), float(ms.value)

@@ -209,17 +209,18 @@ void moda_destroy_run(moda_run run);
  * `hbm_budget`, and launches each admitted request at once on a stream of
  * its own (or on `cuda_stream` if not NULL, which orders them), so new
  * requests join the ones already running instead of waiting for a batch.
- * A request whose buffers exceed the budget even when alone runs alone
- * without the field cache (identical results) if that fits, else fails
- * with MODA_ENOMEM.  Each request's results equal those of moda_anneal on
+ * A request whose buffers with the field cache do not fit runs without it
+ * (identical results) once nothing else is running, if that fits; it fails
+ * with MODA_ENOMEM when it cannot fit even then.  A request whose device
+ * allocation fails while other runs hold memory waits for them.  Each request's results equal those of moda_anneal on
  * the same instance and params.
  *
  *   hbm_budget  bytes for the buffers of runs in flight; 0 = the free
  *               device memory at creation less max(1/8 of it, 1 GiB)
  *   ticket      identifies a request; moda_server_poll sets *done to the
- *               finished run (then owned by the caller, and no longer
- *               counted against the budget) or to NULL while it waits or
- *               runs; a failed request returns its error once.
+ *               finished run (then owned by the caller; its buffers count
+ *               against the budget until moda_destroy_run) or to NULL while
+ *               it waits or runs; a failed request returns its error once.
  *   instances   must outlive their requests.
  *   destroy     cancels requests not yet started (their poll would fail),
  *               waits for those running and frees finished runs nobody

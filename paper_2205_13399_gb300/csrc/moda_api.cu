@@ -9,6 +9,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -146,6 +147,11 @@ struct moda_instance_s {
   int32_t *dFs1 = nullptr, *dFs2 = nullptr, *dD = nullptr;
 };
 
+// Device bytes a server has admitted and not yet seen freed.
+struct ServerAccount {
+  std::atomic<size_t> in_use{0};
+};
+
 struct moda_run_s {
   moda_instance inst = nullptr;
   moda_params prm{};
@@ -163,6 +169,7 @@ struct moda_run_s {
   unsigned char *fcache = nullptr;
   bool checked = false;
   size_t bytes = 0;  // device memory held by the run's buffers
+  std::shared_ptr<ServerAccount> acct;  // serving: released on destroy
 };
 
 namespace {
@@ -716,6 +723,7 @@ void moda_destroy_run(moda_run r) {
   cudaSetDevice(r->inst->device);
   if (r->stop) cudaEventSynchronize(r->stop);
   free_run_buffers(r);
+  if (r->acct) r->acct->in_use -= r->bytes;
   cudaSetDevice(prev);
   delete r;
 }
@@ -846,7 +854,10 @@ struct Request {
 
 struct moda_server_s {
   int device = 0;
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0;
+  // bytes of admitted runs until they are destroyed (by the caller after a
+  // poll, or by the server)
+  std::shared_ptr<ServerAccount> acct = std::make_shared<ServerAccount>();
   cudaStream_t user_stream = nullptr;
   std::vector<cudaStream_t> streams;
   size_t next_stream = 0;
@@ -887,7 +898,6 @@ void server_loop(moda_server_s *S) {
       } else {
         q->state = Request::kDone;
       }
-      S->in_use -= q->bytes;
       ++S->completed;
       S->running.erase(S->running.begin() + (long)i);
     }
@@ -903,9 +913,11 @@ void server_loop(moda_server_s *S) {
       moda_params prm = q->prm;
       const size_t full = run_bytes(q->inst, prm, true);
       const size_t lean = run_bytes(q->inst, prm, false);
-      if (S->in_use + full > S->budget) {
+      const size_t in_use = S->acct->in_use.load();
+      if (in_use + full > S->budget) {
         if (!S->running.empty()) break;  // wait for memory
-        if (lean > S->budget) {
+        if (in_use + lean > S->budget) {
+          if (in_use > 0) break;  // wait for the caller's runs to be destroyed
           q->state = Request::kFailed;
           q->err = MODA_ENOMEM;
           q->msg = "request needs " + std::to_string(lean) + " bytes, budget " +
@@ -913,7 +925,7 @@ void server_loop(moda_server_s *S) {
           S->pending.pop_front();
           continue;
         }
-        prm.field_cache = 2;  // alone and without the cache it fits
+        prm.field_cache = 2;  // alone on the GPU and without the cache it fits
       }
       S->pending.pop_front();
       cudaStream_t st = S->user_stream;
@@ -932,6 +944,10 @@ void server_loop(moda_server_s *S) {
           r = nullptr;
         }
       }
+      if (rs == MODA_ENOMEM && (!S->running.empty() || S->acct->in_use.load() > 0)) {
+        S->pending.push_front(q);  // memory held elsewhere: retry when it frees
+        break;
+      }
       if (rs != MODA_OK) {
         q->state = Request::kFailed;
         q->err = rs;
@@ -941,7 +957,8 @@ void server_loop(moda_server_s *S) {
       q->run = r;
       q->bytes = r->bytes;
       q->state = Request::kRunning;
-      S->in_use += r->bytes;
+      r->acct = S->acct;
+      S->acct->in_use += r->bytes;
       ++S->admitted;
       S->running.push_back(q);
     }
@@ -1039,7 +1056,7 @@ moda_status moda_server_info(moda_server S, int64_t *pending, int64_t *running,
   std::lock_guard<std::mutex> lock(S->mu);
   if (pending) *pending = (int64_t)S->pending.size();
   if (running) *running = (int64_t)S->running.size();
-  if (bytes_in_use) *bytes_in_use = S->in_use;
+  if (bytes_in_use) *bytes_in_use = S->acct->in_use.load();
   if (budget) *budget = S->budget;
   return MODA_OK;
 }

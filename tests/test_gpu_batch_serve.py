@@ -87,7 +87,9 @@ def test_batch_rejects_a_bad_request_without_enqueueing():
         moda.anneal_batch([inst for _, inst, _ in reqs], params)
 
 
-def _drain(srv, tickets, timeout_s=120.0, watch=None):
+def _drain(srv, tickets, timeout_s=120.0, watch=None, on_done=None):
+    """Poll until every ticket finished; ``on_done(ticket, run)`` sees each
+    finished run at once (it may close it, returning its memory)."""
     done = {}
     t0 = time.time()
     while len(done) < len(tickets):
@@ -96,6 +98,8 @@ def _drain(srv, tickets, timeout_s=120.0, watch=None):
                 r = srv.poll(t)
                 if r is not None:
                     done[t] = r
+                    if on_done is not None:
+                        on_done(t, r)
         if watch is not None:
             watch(srv.info())
         assert time.time() - t0 < timeout_s, "server did not finish"
@@ -129,10 +133,15 @@ def test_server_admits_within_the_budget():
     srv = moda.Server(hbm_budget=1 << 21)
     seen = []
     tickets = [srv.submit(inst, **kw) for kw in kws]
-    done = _drain(srv, tickets, watch=lambda i: seen.append(i["running"]))
+    kw_of = dict(zip(tickets, kws))
+
+    def check(t, run):  # compare, then free: the budget counts a run until then
+        _same(run, _plain(inst, kw_of[t]))
+        run.close()
+
+    _drain(srv, tickets, watch=lambda i: seen.append(i["running"]), on_done=check)
     assert max(seen) <= 1
-    for t, kw in zip(tickets, kws):
-        _same(done[t], _plain(inst, kw))
+    assert srv.info()["bytes_in_use"] == 0
     srv.close()
 
 

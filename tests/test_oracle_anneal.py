@@ -251,3 +251,33 @@ def test_nondominated_filter():
     pts = [(5, 5), (4, 6), (5, 5), (6, 6), (3, 9), (4, 6)]
     keep = oracle.nondominated(pts)
     assert keep == [0, 1, 4]
+
+
+# --------------------------------------------------------------------------
+# selection: "choose one flip at random" among the accepted bits (Alg. 3)
+# --------------------------------------------------------------------------
+
+def test_selection_uniform():
+    """With delta so large that every bit is accepted at iteration 1, the
+    flipped bit is the rank floor(u * m / 2^32) of the tag-1 word u of
+    (0, 1, replica, 1) in ascending bit order, and over many replicas every
+    bit is chosen equally often (chi-square, m - 1 degrees of freedom)."""
+    n, m, R = 4, 16, 4000
+    rng = np.random.default_rng(5)
+    F = rng.integers(0, 9, (n, n))
+    np.fill_diagonal(F, 0)
+    D = np.triu(rng.integers(1, 9, (n, n)), 1)
+    D = D + D.T
+    inst = oracle.Instance(F, F.T.copy(), D)
+    seed = 0x1234_5678_9ABC
+    out = oracle.run(inst, I_max=1, replicas=R, seed=seed, delta0=1e12, deltaf=1.0,
+                     xi=1e-3, trace=True, threads=4)
+    flipped = out["trace"][:, 0, 2]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for r in range(0, R, 97):
+        u = int(oracle.philox([0, 1, r, 1], key)[0])
+        assert flipped[r] == (u * m) >> 32
+    counts = np.bincount(flipped, minlength=m)
+    exp = R / m
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < (m - 1) + 6 * math.sqrt(2 * (m - 1))

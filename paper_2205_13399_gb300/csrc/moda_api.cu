@@ -935,7 +935,8 @@ void server_loop(moda_server_s *S) {
       }
       Prepared pl{};
       moda_run r = nullptr;
-      moda_status rs = prepare_run(q->inst, &prm, st, &r, &pl);
+      // the cache was budgeted above (prm.field_cache == 2 when it does not fit)
+      moda_status rs = prepare_run(q->inst, &prm, st, &r, &pl, true);
       if (rs == MODA_OK) {
         rs = enqueue_run(r, pl);
         if (rs != MODA_OK) {

@@ -114,7 +114,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
-  L.jr = o;    o = align_up(o + 8 * 16, 16);                 // 8 entries
+  L.jr = o;    o = align_up(o + 8 * 32, 16);                 // 8 entries
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
   L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits, 16);

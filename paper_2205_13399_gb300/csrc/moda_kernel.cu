@@ -267,6 +267,9 @@ struct JumpRec {
   int32_t slot;     // archive slot jumped to
   int32_t pbuf;     // prefetch buffer holding it, -1: read the cache record
   uint32_t parity;  // that buffer's mbarrier phase parity
+  // pbuf >= 0: shared-memory byte offsets of the member's Delta E record,
+  // its energies, its first state word and the buffer's mbarrier
+  uint32_t rf, se, ws, bar;
 };
 
 // NARROW: Delta E and the acceptance penalty in int32 (the host checked
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const bool worker = tid < Tw;
   const bool control = !worker;          // the last warp
   const int items = B * NWB;
+  const int per = (items + 31) >> 5;     // ballot words per lane in scans
   const bool fc = A.fcache != nullptr;
   const bool de_smem = A.de_in_smem != 0;
   const int LA = A.lookahead;            // prefetch distance
@@ -606,7 +610,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       // The jump iteration t makes if it accepts no bit (its draw and |A|
       // are known now).  Its copy is usable if it was started LA iterations
       // ago for this slot and no iteration since rewrote that slot.
-      jr = JumpRec{kNone, 0, -1, 0};
+      jr = JumpRec{kNone, 0, -1, 0, 0, 0, 0, 0};
       if (A.escape == 0 && acount > 0) {
         jr.kind = kJump;
         jr.slot = pick(sRnd[(t % kRing) * 4 + 1], acount);
@@ -616,8 +620,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           for (uint32_t x = (uint32_t)rec.iter; ok && x < t; ++x)
             if (sWr[x & 7] == jr.slot) ok = false;
           if (ok) {
-            jr.pbuf = (int)(t % (uint32_t)NB);
+            const int b = (int)(t % (uint32_t)NB);
+            const uint32_t pb = (uint32_t)(lay.pf + (size_t)b * lay.pf_slot);
+            jr.pbuf = b;
             jr.parity = (uint32_t)rec.parity;
+            jr.rf = pb;
+            jr.se = A.energies_in_smem ? (uint32_t)(lay.archE + 16 * (size_t)jr.slot)
+                                       : pb + (uint32_t)lay.pfE;
+            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)jr.slot * W);
+            jr.ws = A.bits_in_smem ? (uint32_t)(lay.archB + 4 * (size_t)jr.slot * W)
+                                   : pb + (uint32_t)lay.pfW + (uint32_t)(b0 & 15);
+            jr.bar = (uint32_t)(lay.mbar + 8 * (size_t)b);
           }
         }
       }
@@ -631,8 +644,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const uint32_t *rnd = sRnd + (t % kRing) * 4;
     int kind, ps = 0;
     {
-      int cnt;
-      const int total = warp_mask_count(mask, items, lane, cnt);
+      int cnt = 0;
+#pragma unroll
+      for (int q = 0; q < B; ++q) {  // items <= B * 31, so per <= B
+        const int it = lane * per + q;
+        if (q < per && it < items) cnt += __popc(mask[it]);
+      }
+      const int total = (int)__reduce_add_sync(kFull, (unsigned)cnt);
       if (total > 0) {
         kind = kFlip;
         if (worker) {
@@ -650,7 +668,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
 
     // ---- all: carry out the decision ------------------------------------
-    int64_t event = INT64_MIN;
     if (kind == kFlip) {
       int64_t dE1, dE2;
       int sg;
@@ -763,47 +780,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       E1 = nE1;
       E2 = nE2;
       Eoff = 0;
-      ++st_flip;
-      event = ps;
+      if (control) ++st_flip;
     } else if (kind == kJump) {
       // Alg. 3: jump to a random archive member.
       const int slot = jr.slot, pbuf = jr.pbuf;
       if (fc) {
         if (worker) {
-          const dE2_t *rf;
-          const uint32_t *wsrc;
-          longlong2 se;
-          if (pbuf >= 0) {
-            unsigned char *pb = smem + lay.pf + (size_t)pbuf * lay.pf_slot;
-            if (!mbar_wait(&sBar[pbuf], jr.parity)) fail = 1;
-            rf = reinterpret_cast<const dE2_t *>(pb);
-            se = A.energies_in_smem ? aE[slot]
-                                    : *reinterpret_cast<const longlong2 *>(pb + lay.pfE);
-            if (A.bits_in_smem) {
-              wsrc = aBits + (size_t)slot * W;
-            } else {
-              const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot * W);
-              wsrc = reinterpret_cast<const uint32_t *>(pb + lay.pfW + (b0 & 15));
+          if (pbuf >= 0) {  // from the prefetch buffer (shared memory)
+            if (!mbar_wait(reinterpret_cast<uint64_t *>(smem + jr.bar), jr.parity)) fail = 1;
+            const dE2_t *rf = reinterpret_cast<const dE2_t *>(smem + jr.rf);
+            const uint32_t *ws = reinterpret_cast<const uint32_t *>(smem + jr.ws);
+            const longlong2 se = *reinterpret_cast<const longlong2 *>(smem + jr.se);
+            E1 = se.x;
+            E2 = se.y;
+            xmask = 0;
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+              if (!valid(k)) continue;
+              const dE2_t v2 = rf[k * Tw + tid];
+              D1[k] = v2.x;
+              D2[k] = v2.y;
+              xmask |= ((ws[k * NWB + warp] >> lane) & 1u) << k;
             }
           } else {  // read the record where it is
-            rf = reinterpret_cast<const dE2_t *>(gF + (size_t)slot * sl.bytes);
-            se = aE[slot];
-            wsrc = aBits + (size_t)slot * W;
-          }
-          E1 = se.x;
-          E2 = se.y;
-          xmask = 0;
+            const dE2_t *rf = reinterpret_cast<const dE2_t *>(gF + (size_t)slot * sl.bytes);
+            const uint32_t *wsrc = aBits + (size_t)slot * W;
+            const longlong2 se = aE[slot];
+            E1 = se.x;
+            E2 = se.y;
+            xmask = 0;
 #pragma unroll
-          for (int k = 0; k < B; ++k) {
-            if (!valid(k)) continue;
-            const int q = k * Tw + tid;
-            const dE2_t v2 = rf[q];
-            D1[k] = v2.x;
-            D2[k] = v2.y;
-            xmask |= ((wsrc[q >> 5] >> (q & 31)) & 1u) << k;
+            for (int k = 0; k < B; ++k) {
+              if (!valid(k)) continue;
+              const dE2_t v2 = rf[k * Tw + tid];
+              D1[k] = v2.x;
+              D2[k] = v2.y;
+              xmask |= ((wsrc[k * NWB + warp] >> lane) & 1u) << k;
+            }
           }
+        } else if (pbuf >= 0) {
+          ++st_pf;
+        } else {
+          ++st_direct;
         }
-        if (pbuf >= 0) ++st_pf; else ++st_direct;
       } else {
         const longlong2 se = aE[slot];
         E1 = se.x;
@@ -811,15 +830,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         int64_t s1, s2;
         rebuild(aBits + (size_t)slot * W, s1, s2);
       }
-      ++st_jump;
-      event = -1 - (int64_t)slot;
+      if (control) ++st_jump;
     } else if (A.escape == 0) {
-      ++st_empty;
+      if (control) ++st_empty;
     } else {
       Eoff += A.beta;
-      ++st_off;
+      if (control) ++st_off;
     }
-    flip_streak = kind == kFlip ? flip_streak + 1 : 0;
+    if (control) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
     cur_delta = nse.delta;
     cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
     cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;
@@ -827,7 +845,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       int64_t *tr = A.trace + ((size_t)rb * (size_t)I_max + (size_t)(t - 1)) * 3;
       tr[0] = E1;
       tr[1] = E2;
-      tr[2] = event;
+      tr[2] = kind == kFlip ? (int64_t)ps : kind == kJump ? -1 - (int64_t)jr.slot : INT64_MIN;
     }
   }
   // No bulk copy may be in flight when the block exits.
@@ -855,7 +873,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   if (A.bits_in_smem) {
     for (int e = tid; e < acount * W; e += T) gBits[e] = aBits[e];
   }
-  if (tid == 0) {
+  if (tid == Tw) {  // the control warp counted the outcomes
     int64_t *st = A.stats + (size_t)kStats * rb;
     st[0] = st_flip;
     st[1] = st_jump;
@@ -866,6 +884,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     st[6] = 0;
     st[7] = 0;
     A.arch_count[rb] = acount;
+  }
+  if (tid == 0) {  // workers track the energies
     A.E_final[2 * rb] = E1;
     A.E_final[2 * rb + 1] = E2;
   }

@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["moda", "reference"], default="moda")
     ap.add_argument("--workload", default="P25",
-                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE"])
+                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE", "SBDA"])
     ap.add_argument("--instances", type=int, default=512, help="BATCH: instances")
     ap.add_argument("--seq-instances", type=int, default=24,
                     help="BATCH / SERVE: requests also run one at a time for comparison")
@@ -334,6 +334,7 @@ def run_serve(args):
         srv = moda.Server()
         t0 = time.perf_counter()
         pending, lat, done_t = {}, [], []
+        kernel_ms = []
         nxt = 0
         while nxt < len(rs) or pending:
             now = time.perf_counter() - t0
@@ -348,29 +349,35 @@ def run_serve(args):
                 if r is not None:
                     q, inst = pending.pop(t)
                     r.read_archive(-1, perms=False)
+                    kernel_ms.append(r.elapsed_ms())
                     fin = time.perf_counter() - t0
                     lat.append(fin - q.arrival_s)
                     done_t.append(fin)
                     r.close()
             time.sleep(0.0005)
         srv.close()
-        return np.array(lat), max(done_t)
+        return np.array(lat), max(done_t), kernel_ms
 
     for _ in range(args.warmup):
         serve(warm[:4])
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    lat, span = serve(reqs)
+    lat, span, _ = serve(reqs)
     clk = clocks.stop()
     value = len(reqs) / span
+    # the first k requests both ways: served (as they arrive) and one at a
+    # time, each solve waited for before the next starts
     k = min(args.seq_instances, len(reqs))
+    _, span_k, served_ms = serve(reqs[:k])
     t0 = time.perf_counter()
+    alone_ms = []
     for q in reqs[:k]:
         inst = moda.Instance(q.instance.F1, q.instance.F2, q.instance.D)
         r = moda.anneal(inst, replicas=32, I_max=q.I_max, seed=q.seed).wait()
         r.read_archive(-1, perms=False)
+        alone_ms.append(r.elapsed_ms())
         r.close()
-    seq = k / (time.perf_counter() - t0)
+    seq_span = time.perf_counter() - t0
     work = sum(32 * q.I_max for q in reqs)
     line = {
         "metric": "bQAP solves/s", "value": value, "unit": "solves/s", "n_gpus": 1,
@@ -385,11 +392,105 @@ def run_serve(args):
                        "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3)},
         "replica_steps_per_s": work / span,
-        "vs_one_at_a_time": {"requests": k, "solves_per_s": seq, "speedup": value / seq},
+        "vs_one_at_a_time": {"requests": k, "served_s": span_k, "one_at_a_time_s": seq_span,
+                             "speedup": seq_span / span_k,
+                             "kernel_ms_served_over_alone":
+                                 sum(served_ms) / max(sum(alone_ms), 1e-9)},
         "e2e": {"value": value, "unit": "solves/s",
                 "h2d_bytes_per_step": sum(3 * q.instance.n ** 2 * 4 for q in reqs),
                 "d2h_bytes_per_step": None, "note": "serving is end to end by construction"},
         "gpu_launches": len(reqs), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def hv_norm(points, lo, hi):
+    """Normalised 2-D hypervolume (minimisation) of ``points`` in the box
+    [lo, hi] scaled to [0, 1]^2, reference point (1.1, 1.1)."""
+    pts = sorted(((p[0] - lo[0]) / max(hi[0] - lo[0], 1), (p[1] - lo[1]) / max(hi[1] - lo[1], 1))
+                 for p in points)
+    hv, prev2 = 0.0, 1.1
+    for a, b in pts:
+        if b < prev2:
+            hv += (1.1 - a) * (prev2 - b)
+            prev2 = b
+    return hv
+
+
+def run_sbda(args):
+    """SB-DA (Alg. 2: eleven scalarised DA runs, one batch launch) against
+    MDA (Alg. 3) on the P25 instance, same replicas and I_max per run: the
+    paper's comparison of the two (Table 3), with both fronts' normalised
+    hypervolume over the union's cost range."""
+    import torch
+    from paper_2205_13399_gb300 import inputs, moda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    qi = inputs.workload_instance("P25")
+    run = dict(inputs.WORKLOAD_RUN["P25"])
+    if args.I_max is not None:
+        run["I_max"] = args.I_max
+    R, I_max = run["replicas"], run["I_max"]
+    inst = moda.Instance(qi.F1, qi.F2, qi.D)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), out
+
+    def sbda():
+        return moda.sbda(inst, replicas=R, I_max=I_max, seed=run["seed"], stream=stream)
+
+    def mda():
+        r = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"], stream=stream)
+        r.wait()
+        return r
+
+    for _ in range(args.warmup):
+        sbda()
+        mda().close()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    s_ms, m_ms = [], []
+    for _ in range(args.steps):
+        ms, (runs, front_s) = timed(sbda)
+        s_ms.append(ms)
+        ms, r = timed(mda)
+        m_ms.append(ms)
+        front_m = [(p["c1"], p["c2"]) for p in r.read_archive(-1) if p["feasible"]]
+        r.close()
+        for x in runs:
+            x.close()
+    clk = clocks.stop()
+    fs = [(p["c1"], p["c2"]) for p in front_s]
+    allp = fs + front_m
+    lo = (min(p[0] for p in allp), min(p[1] for p in allp))
+    hi = (max(p[0] for p in allp), max(p[1] for p in allp))
+    sb = statistics.mean(s_ms)
+    value = 11 * R * I_max / (sb / 1e3)
+    line = {
+        "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sb,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"SBDA: SB-DA (11 weights, Alg. 2) vs MDA (Alg. 3) on P25, "
+                               f"{R} replicas, I_max={I_max} per run",
+                   "weights": 11, "replicas": R, "I_max": I_max,
+                   "l2": "flushed before each timed solve (512 MiB write)"},
+        "vs_mda": {"sbda_ms": sb, "mda_ms": statistics.mean(m_ms),
+                   "sbda_over_mda_time": sb / statistics.mean(m_ms),
+                   "sbda_front_points": len(fs), "mda_front_points": len(front_m),
+                   "hv_sbda": hv_norm(fs, lo, hi), "hv_mda": hv_norm(front_m, lo, hi)},
+        "e2e": {"value": value, "unit": "replica-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": None, "note": "front read-back inside the timed call"},
+        "gpu_launches": 12 * args.steps, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -402,11 +503,11 @@ def main(argv=None):
     world, rank, local = dist_env()
     import numpy as np
     import torch
-    if args.workload in ("BATCH", "SERVE"):
+    if args.workload in ("BATCH", "SERVE", "SBDA"):
         if world > 1:
-            raise SystemExit("BATCH and SERVE run on one GPU")
+            raise SystemExit("BATCH, SERVE and SBDA run on one GPU")
         torch.cuda.set_device(local)
-        return run_batch(args) if args.workload == "BATCH" else run_serve(args)
+        return {"BATCH": run_batch, "SERVE": run_serve, "SBDA": run_sbda}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")

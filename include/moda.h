@@ -200,6 +200,35 @@ moda_status moda_run_elapsed_ms(moda_run run, float *ms);
 
 void moda_destroy_run(moda_run run);
 
+/* ---- SB-DA (Sec. 3.2, Alg. 2), the paper's scalarisation baseline -----
+ *
+ * moda_scalarize builds the single-objective instance of weight gamma =
+ * gamma_num / gamma_den, scaled by gamma_den so that it stays integral:
+ * flows gamma_num Fs^1 + (gamma_den - gamma_num) Fs^2 (Alg. 2, cost line)
+ * with the penalty weight of Eq. vermap taken on that cost (Alg. 2, alpha
+ * line; the instance's w1, w2 are w and 0) and a second objective of zero.
+ * MODA_EOVERFLOW when a scaled field could exceed int32.
+ *
+ * Alg. 1 (DA) on it is moda_anneal with escape = MODA_ESC_OFFSET,
+ * archive_size = 1 and delta0, deltaf and beta multiplied by gamma_den:
+ * with the second objective zero the acceptance penalty is
+ * max(0, Delta E - E_offset), and the explorative archive of one slot
+ * keeps the lowest-energy state reached by a flip (the earliest on ties),
+ * which is DA's "best solution found" (the initial state if no flip is
+ * ever accepted).
+ *
+ * moda_sbda_front merges finished runs of one source instance, one run per
+ * weight: each replica's best state, if it is a permutation, with its QAP
+ * costs (c1, c2) on the source instance, then the non-dominated points
+ * (Alg. 2, last line), among equal cost vectors the lowest (run, replica).
+ * Points come sorted by c1, with E = c, replica = replica and slot = run
+ * index; perms as in moda_read_archive.  MODA_EBUSY if a run has not
+ * finished. */
+moda_status moda_scalarize(moda_instance src, int32_t gamma_num, int32_t gamma_den,
+                           moda_instance *out);
+moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t count,
+                            moda_point *pts, int32_t cap, int32_t *total, uint8_t *perms);
+
 /* ---- Serving ---------------------------------------------------------
  *
  * A queue of anneal requests served as they arrive (not in the paper:

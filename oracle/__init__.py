@@ -72,6 +72,17 @@ class _Params(ctypes.Structure):
     ]
 
 
+class _DAParams(ctypes.Structure):
+    _fields_ = [
+        ("I_max", ctypes.c_int64),
+        ("delta0", ctypes.c_double),
+        ("deltaf", ctypes.c_double),
+        ("xi", ctypes.c_double),
+        ("beta", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -110,6 +121,16 @@ def _load():
         lib.oracle_mda_run_many.restype = ctypes.c_int
         lib.oracle_mda_run_many.argtypes = [P, ctypes.POINTER(_Params), i64, P, ctypes.c_int,
                                             P, P, P, P, P, P, P]
+        lib.oracle_sbda_qubo.restype = P
+        lib.oracle_sbda_qubo.argtypes = [P, i64, i64]
+        lib.oracle_squbo_free.argtypes = [P]
+        lib.oracle_squbo_w.restype = i64
+        lib.oracle_squbo_w.argtypes = [P]
+        lib.oracle_squbo_energy.restype = i64
+        lib.oracle_squbo_energy.argtypes = [P, P]
+        lib.oracle_da_run_many.restype = ctypes.c_int
+        lib.oracle_da_run_many.argtypes = [P, ctypes.POINTER(_DAParams), i64, P, ctypes.c_int,
+                                           P, P, P, P, P]
         _lib = lib
         return lib
 
@@ -292,3 +313,63 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
     if tr is not None:
         out["trace"] = tr
     return out
+
+
+def da_run(inst: Instance, gnum: int, gden: int, *, I_max: int, replicas, seed: int = 0,
+           delta0: float = 1e9, deltaf: float = 1e4, xi: float = 1e-3,
+           beta: int | None = None, threads: int | None = None) -> dict:
+    """Alg. 1 (DA) on the scalarised QUBO of Alg. 2 for gamma = gnum / gden,
+    in integers scaled by gden: Q = gnum R + (gden - gnum) S + alpha G with
+    alpha from Eq. vermap on that cost, temperatures delta0 * gden and
+    deltaf * gden, offset rate beta * gden (beta defaults to delta0 / I_max).
+    Returns ``w`` and per replica ``best_x`` [R, m], ``best_E`` [R],
+    ``x`` [R, m], ``E_final`` [R] and ``stats`` [R, 2] (flips, offset
+    raises)."""
+    lib = _load()
+    if isinstance(replicas, (int, np.integer)):
+        replicas = range(int(replicas))
+    reps = np.ascontiguousarray(np.asarray(replicas, dtype=np.uint32).reshape(-1))
+    R, m = reps.size, inst.m
+    if beta is None:
+        beta = int(round(delta0 / I_max)) if I_max > 0 else 0
+    q = lib.oracle_sbda_qubo(inst._h, int(gnum), int(gden))
+    if not q:
+        raise ValueError("bad scalarisation weight")
+    try:
+        prm = _DAParams(int(I_max), float(delta0) * gden, float(deltaf) * gden, float(xi),
+                        int(beta) * gden, int(seed) & 0xFFFFFFFFFFFFFFFF)
+        out = {"w": int(lib.oracle_squbo_w(q)),
+               "best_x": np.zeros((R, m), dtype=np.uint8),
+               "best_E": np.zeros(R, dtype=np.int64),
+               "x": np.zeros((R, m), dtype=np.uint8),
+               "E_final": np.zeros(R, dtype=np.int64),
+               "stats": np.zeros((R, 2), dtype=np.int64)}
+        nth = threads if threads else (os.cpu_count() or 1)
+        rc = lib.oracle_da_run_many(q, ctypes.byref(prm), R, _ptr(reps), int(nth),
+                                    _ptr(out["best_x"]), _ptr(out["best_E"]), _ptr(out["x"]),
+                                    _ptr(out["E_final"]), _ptr(out["stats"]))
+        if rc != 0:
+            raise RuntimeError(f"oracle DA failed with code {rc}")
+        out["energy_check"] = [int(lib.oracle_squbo_energy(q, _ptr(np.ascontiguousarray(x))))
+                               for x in out["best_x"][:2]]
+    finally:
+        lib.oracle_squbo_free(q)
+    return out
+
+
+def sbda(inst: Instance, *, gden: int = 10, gammas=None, **kw) -> dict:
+    """Alg. 2: one DA run (``da_run``) per weight gamma = g / gden, g in
+    ``gammas`` (default 0..gden), then the non-dominated feasible solutions
+    of all runs by their QAP costs (c1, c2).  Returns ``runs`` (per weight)
+    and ``front``: a list of (c1, c2, weight index, replica) sorted by c1,
+    among equal cost vectors the lowest (weight index, replica)."""
+    gammas = list(range(gden + 1)) if gammas is None else list(gammas)
+    runs = [da_run(inst, g, gden, **kw) for g in gammas]
+    cand = []
+    for gi, r in enumerate(runs):
+        for rep, x in enumerate(r["best_x"]):
+            if inst.constraint(x) == 0:
+                cand.append((inst.cost(0, x), inst.cost(1, x), gi, rep))
+    keep = nondominated([(c[0], c[1]) for c in cand])
+    front = sorted((cand[i] for i in keep), key=lambda c: (c[0], c[1]))
+    return {"runs": runs, "front": front}

@@ -651,3 +651,208 @@ int oracle_mda_run_many(const oracle_instance *inst, const oracle_params *prm,
   pthread_mutex_destroy(&job.lock);
   return job.rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* SB-DA (Sec. 3.2, Alg. 2) and the DA it calls (Sec. 3.1, Alg. 1)          */
+/* ------------------------------------------------------------------------ */
+
+/* The scalarised QUBO of Alg. 2 for the weight gamma = gnum / gden, kept
+ * integral by scaling everything by gden (temperatures and the offset rate
+ * are scaled by the same factor, which leaves exp(-a / delta) unchanged):
+ *   C = gnum R + (gden - gnum) S                      (Alg. 2, cost line)
+ *   alpha = w / 2, w by Eq. vermap on C               (Alg. 2, alpha line)
+ *   Q = C + alpha G                                   (G entries are even) */
+typedef struct oracle_squbo {
+  int n;
+  int64_t m;
+  int64_t w;
+  int64_t offset;  /* alpha p_g */
+  int64_t *Q;      /* upper triangular */
+  int64_t *P;      /* symmetric, diagonal = Q_pp (Eq. cale) */
+} oracle_squbo;
+
+void oracle_squbo_free(oracle_squbo *q) {
+  if (!q) return;
+  free(q->Q);
+  free(q->P);
+  free(q);
+}
+
+oracle_squbo *oracle_sbda_qubo(const oracle_instance *inst, int64_t gnum,
+                               int64_t gden) {
+  if (gden < 1 || gnum < 0 || gnum > gden) return NULL;
+  const int64_t m = inst->m;
+  oracle_squbo *q = (oracle_squbo *)calloc(1, sizeof(*q));
+  if (!q) return NULL;
+  q->n = inst->n;
+  q->m = m;
+  q->Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m * m));
+  q->P = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m * m));
+  int64_t *C = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m * m));
+  if (!q->Q || !q->P || !C) {
+    free(C);
+    oracle_squbo_free(q);
+    return NULL;
+  }
+  for (int64_t e = 0; e < m * m; ++e)
+    C[e] = gnum * inst->C[0][e] + (gden - gnum) * inst->C[1][e];
+  q->w = oracle_penalty_w(m, C);
+  for (int64_t e = 0; e < m * m; ++e) q->Q[e] = C[e] + q->w * (inst->G[e] / 2);
+  q->offset = q->w * (inst->pg / 2);
+  for (int64_t p = 0; p < m; ++p)
+    for (int64_t r = 0; r < m; ++r)
+      q->P[p * m + r] = p == r ? q->Q[p * m + p] : q->Q[p * m + r] + q->Q[r * m + p];
+  free(C);
+  return q;
+}
+
+int64_t oracle_squbo_w(const oracle_squbo *q) { return q->w; }
+
+/* E(x) = x^T Q x + alpha p_g */
+int64_t oracle_squbo_energy(const oracle_squbo *q, const uint8_t *x) {
+  return oracle_quadratic(q->m, q->Q, x) + q->offset;
+}
+
+typedef struct oracle_da_params {
+  int64_t I_max;
+  double delta0, deltaf, xi;  /* already scaled by gden */
+  int64_t beta;               /* already scaled by gden */
+  uint64_t seed;
+} oracle_da_params;
+
+/* Alg. 1 for one replica with the draws of Alg. 3 (same Philox counters).
+ * "Best solution found": the lowest energy among the states reached by
+ * accepted flips, the earliest on ties; the initial state when no flip is
+ * ever accepted.  stats: [flips, offset raises]. */
+int oracle_da_run(const oracle_squbo *q, const oracle_da_params *prm,
+                  uint32_t replica, uint8_t *best_x, int64_t *best_E,
+                  uint8_t *x_final, int64_t *E_final, int64_t *stats) {
+  const int64_t m = q->m;
+  if (prm->I_max < 0 || prm->I_max > 0xFFFFFFFFll) return -1;
+  int rc = 0;
+  uint8_t *x = (uint8_t *)calloc((size_t)m, 1);
+  int64_t *phi = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+  int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+  int64_t *accepted = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+  double *T = (double *)malloc(sizeof(double) * 65536);
+  if (!x || !phi || !dE || !accepted || !T) {
+    rc = -2;
+    goto done;
+  }
+  oracle_neglog_table(T);
+  stats[0] = stats[1] = 0;
+  /* "x <- a random binary solution" (the init draws of Alg. 3) */
+  for (int64_t k = 0; k < m; ++k) {
+    uint32_t w = draw_word(prm->seed, (uint32_t)(k >> 7), 0, replica, TAG_INIT,
+                           (int)((k >> 5) & 3));
+    x[k] = (uint8_t)((w >> (k & 31)) & 1u);
+  }
+  int64_t E = oracle_squbo_energy(q, x);
+  for (int64_t p = 0; p < m; ++p) phi[p] = 0;
+  for (int64_t r = 0; r < m; ++r) {
+    if (!x[r]) continue;
+    for (int64_t p = 0; p < m; ++p)
+      if (p != r) phi[p] += q->P[r * m + p];
+  }
+  memcpy(best_x, x, (size_t)m);
+  *best_E = E;
+  int have_best = 0;
+  double delta = prm->delta0;
+  const double factor = 1.0 - prm->xi;
+  int64_t Eoff = 0;
+  for (int64_t it = 1; it <= prm->I_max; ++it) {
+    const uint32_t step = (uint32_t)it;
+    if (delta > prm->deltaf) delta = delta * factor;
+    /* calculate Delta E (Eq. cale) */
+    for (int64_t p = 0; p < m; ++p)
+      dE[p] = (1 - 2 * (int64_t)x[p]) * (q->P[p * m + p] + phi[p]);
+    /* propose every flip with Delta E_i - E_offset (Eq. paccepts) */
+    int64_t count = 0;
+    for (int64_t p = 0; p < m; ++p) {
+      int64_t e = dE[p] - Eoff;
+      int64_t a = e > 0 ? e : 0;
+      uint32_t w = draw_word(prm->seed, (uint32_t)(p >> 2), step, replica, TAG_ACCEPT,
+                             (int)(p & 3));
+      if ((double)a <= delta * T[w >> 16]) accepted[count++] = p;
+    }
+    if (count > 0) {
+      uint32_t u = draw_word(prm->seed, 0, step, replica, TAG_SELECT, 0);
+      int64_t r = accepted[pick(u, count)];
+      int64_t sgn = x[r] ? -1 : 1;
+      E += dE[r];
+      x[r] ^= 1;
+      for (int64_t p = 0; p < m; ++p)
+        if (p != r) phi[p] += sgn * q->P[r * m + p];
+      Eoff = 0;
+      stats[0] += 1;
+      if (!have_best || E < *best_E) {
+        memcpy(best_x, x, (size_t)m);
+        *best_E = E;
+        have_best = 1;
+      }
+    } else {
+      Eoff += prm->beta;
+      stats[1] += 1;
+    }
+  }
+  memcpy(x_final, x, (size_t)m);
+  *E_final = E;
+done:
+  free(x); free(phi); free(dE); free(accepted); free(T);
+  return rc;
+}
+
+typedef struct {
+  const oracle_squbo *q;
+  const oracle_da_params *prm;
+  const uint32_t *replicas;
+  int64_t n_rep;
+  uint8_t *best_x, *x_final;
+  int64_t *best_E, *E_final, *stats;
+  int64_t next;
+  int rc;
+  pthread_mutex_t lock;
+} da_job;
+
+static void *da_worker(void *arg) {
+  da_job *job = (da_job *)arg;
+  const int64_t m = job->q->m;
+  for (;;) {
+    pthread_mutex_lock(&job->lock);
+    int64_t r = job->next++;
+    pthread_mutex_unlock(&job->lock);
+    if (r >= job->n_rep) break;
+    int rc = oracle_da_run(job->q, job->prm, job->replicas[r], job->best_x + r * m,
+                           job->best_E + r, job->x_final + r * m, job->E_final + r,
+                           job->stats + 2 * r);
+    if (rc != 0) {
+      pthread_mutex_lock(&job->lock);
+      job->rc = rc;
+      pthread_mutex_unlock(&job->lock);
+    }
+  }
+  return NULL;
+}
+
+int oracle_da_run_many(const oracle_squbo *q, const oracle_da_params *prm, int64_t n_rep,
+                       const uint32_t *replicas, int nthreads, uint8_t *best_x,
+                       int64_t *best_E, uint8_t *x_final, int64_t *E_final,
+                       int64_t *stats) {
+  da_job job;
+  memset(&job, 0, sizeof(job));
+  job.q = q; job.prm = prm; job.replicas = replicas; job.n_rep = n_rep;
+  job.best_x = best_x; job.best_E = best_E; job.x_final = x_final;
+  job.E_final = E_final; job.stats = stats;
+  pthread_mutex_init(&job.lock, NULL);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > n_rep) nthreads = (int)(n_rep > 0 ? n_rep : 1);
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  int started = 0;
+  for (int i = 0; i < nthreads; ++i)
+    if (pthread_create(&th[i], NULL, da_worker, &job) == 0) started++;
+  if (started == 0) da_worker(&job);
+  for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+  free(th);
+  pthread_mutex_destroy(&job.lock);
+  return job.rc;
+}

@@ -138,6 +138,11 @@ namespace moda {
 void set_last_error(const char *msg) { g_error = msg; }
 }  // namespace moda
 
+struct moda_instance_s;
+namespace {
+moda_status finish_instance(moda_instance inst, const moda_penalty *pen, moda_instance *out);
+}  // namespace
+
 struct moda_instance_s {
   int32_t n = 0, m = 0, W = 0;
   int device = 0;
@@ -236,6 +241,17 @@ moda_status moda_create_instance(int32_t n, const int16_t *F1,
       inst->Fs2[i * n + j] = (int32_t)F2[i * n + j] + (int32_t)F2[j * n + i];
       inst->D[i * n + j] = D[i * n + j];
     }
+  return finish_instance(inst, pen, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Bounds, penalty weights and device upload of an instance whose host
+// Fs1, Fs2 and D are filled; takes ownership of `inst`.
+moda_status finish_instance(moda_instance inst, const moda_penalty *pen, moda_instance *out) {
+  const int n = inst->n, nn = inst->m;
   // Bound of every local field and of w_k: (max row sum of Fs) x (max row
   // sum of D).
   int64_t dmax = 0, f1max = 0, f2max = 0;
@@ -250,7 +266,7 @@ moda_status moda_create_instance(int32_t n, const int16_t *F1,
     f1max = std::max(f1max, s1);
     f2max = std::max(f2max, s2);
   }
-  const int64_t b1 = f1max * dmax, b2 = f2max * dmax;
+  const int64_t b1 = f1max * dmax, b2 = f2max * dmax;  // every entry is >= 0
   if (b1 >= (int64_t(1) << 31) || b2 >= (int64_t(1) << 31)) {
     delete inst;
     return fail(MODA_EOVERFLOW, "local fields may exceed int32");
@@ -281,6 +297,39 @@ moda_status moda_create_instance(int32_t n, const int16_t *F1,
   }
   *out = inst;
   return MODA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+moda_status moda_scalarize(moda_instance src, int32_t gamma_num, int32_t gamma_den,
+                           moda_instance *out) {
+  if (!out) return fail(MODA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!src) return fail(MODA_EINVAL, "NULL instance");
+  if (gamma_den < 1 || gamma_num < 0 || gamma_num > gamma_den)
+    return fail(MODA_EINVAL, "need 0 <= gamma_num <= gamma_den, gamma_den >= 1");
+  moda_instance inst = new (std::nothrow) moda_instance_s;
+  if (!inst) return fail(MODA_ENOMEM, "host allocation");
+  const int nn = src->m;
+  inst->n = src->n;
+  inst->m = nn;
+  inst->W = src->W;
+  inst->Fs1.resize(nn);
+  inst->Fs2.assign(nn, 0);
+  inst->D = src->D;
+  for (int e = 0; e < nn; ++e) {
+    const int64_t v = (int64_t)gamma_num * src->Fs1[e] +
+                      (int64_t)(gamma_den - gamma_num) * src->Fs2[e];
+    if (v >= (int64_t(1) << 31)) {
+      delete inst;
+      return fail(MODA_EOVERFLOW, "scalarised flows exceed int32");
+    }
+    inst->Fs1[e] = (int32_t)v;
+  }
+  cudaSetDevice(src->device);
+  return finish_instance(inst, nullptr, out);
 }
 
 void moda_destroy_instance(moda_instance inst) {
@@ -1074,6 +1123,95 @@ void moda_server_destroy(moda_server S) {
     if (kv.second->state == Request::kDone && kv.second->run) moda_destroy_run(kv.second->run);
   for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
   delete S;
+}
+
+
+// ---- SB-DA front (Alg. 2) ------------------------------------------------
+
+moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t count,
+                            moda_point *pts, int32_t cap, int32_t *total, uint8_t *perms) {
+  if (!src || !runs || count < 1 || !total || (cap > 0 && !pts))
+    return fail(MODA_EINVAL, "need the instance, runs, count >= 1 and outputs");
+  const int n = src->n, m = src->m, W = src->W;
+  struct Cand {
+    int64_t c1, c2;
+    int32_t run, rep;
+    std::vector<uint8_t> perm;
+  };
+  std::vector<Cand> cand;
+  for (int32_t i = 0; i < count; ++i) {
+    moda_run r = runs[i];
+    if (!r || r->inst->n != n) return fail(MODA_EINVAL, "run of another size");
+    if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+    const int R = r->R, s = r->s;
+    std::vector<int32_t> cnt(R);
+    std::vector<uint32_t> bits((size_t)R * s * W), x((size_t)R * W);
+    moda_status st = moda_read_replica(r, -1, cnt.data(), nullptr, bits.data(), x.data(),
+                                       nullptr, nullptr);
+    if (st != MODA_OK) return st;
+    for (int q = 0; q < R; ++q) {
+      // the run's best state: its one archive member, else the initial state
+      const uint32_t *w = cnt[q] > 0 ? bits.data() + (size_t)q * s * W : x.data() + (size_t)q * W;
+      std::vector<uint8_t> perm(n, 0xFF);
+      std::vector<int> colc(n, 0);
+      bool ok = true;
+      for (int f = 0; f < n && ok; ++f) {
+        int ones = 0;
+        for (int u = 0; u < n; ++u) {
+          const int p = f * n + u;
+          if ((w[p >> 5] >> (p & 31)) & 1u) {
+            ++ones;
+            perm[f] = (uint8_t)u;
+            ++colc[u];
+          }
+        }
+        ok = ones == 1;
+      }
+      for (int u = 0; u < n && ok; ++u) ok = colc[u] == 1;
+      if (!ok) continue;  // infeasible: not a solution of the QAP
+      // c_k = sum_ij F^k_ij d_{pi(i) pi(j)} = (1/2) sum_ij Fs^k_ij d_{pi(i) pi(j)}
+      int64_t c1 = 0, c2 = 0;
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+          const int64_t d = src->D[perm[a] * n + perm[b]];
+          c1 += (int64_t)src->Fs1[a * n + b] * d;
+          c2 += (int64_t)src->Fs2[a * n + b] * d;
+        }
+      cand.push_back(Cand{c1 / 2, c2 / 2, i, q, std::move(perm)});
+    }
+  }
+  // non-dominated by (c1, c2); among equal vectors the lowest (run, replica)
+  std::vector<size_t> order(cand.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return std::tie(cand[a].c1, cand[a].c2, cand[a].run, cand[a].rep) <
+           std::tie(cand[b].c1, cand[b].c2, cand[b].run, cand[b].rep);
+  });
+  std::vector<size_t> keep;
+  int64_t best2 = INT64_MAX;
+  for (size_t k : order) {  // ascending c1: kept iff c2 beats every earlier one
+    if (cand[k].c2 < best2) {
+      keep.push_back(k);
+      best2 = cand[k].c2;
+    }
+  }
+  *total = (int32_t)keep.size();
+  const int32_t nw = std::min<int32_t>(cap, (int32_t)keep.size());
+  for (int32_t k = 0; k < nw; ++k) {
+    const Cand &c = cand[keep[k]];
+    moda_point p{};
+    p.E1 = c.c1;
+    p.E2 = c.c2;
+    p.c1 = c.c1;
+    p.c2 = c.c2;
+    p.g = 0;
+    p.feasible = 1;
+    p.replica = c.rep;
+    p.slot = c.run;
+    pts[k] = p;
+    if (perms) memcpy(perms + (size_t)k * n, c.perm.data(), (size_t)n);
+  }
+  return MODA_OK;
 }
 
 }  // extern "C"

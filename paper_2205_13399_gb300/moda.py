@@ -32,7 +32,8 @@ ABI_FUNCTIONS = [
     "moda_read_archive", "moda_run_elapsed_ms", "moda_destroy_run",
     "moda_last_error", "moda_anneal_noalloc", "moda_anneal_batch",
     "moda_server_create", "moda_server_submit", "moda_server_poll", "moda_server_info",
-    "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak",
+    "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak", "moda_scalarize",
+    "moda_sbda_front",
 ]
 
 
@@ -142,6 +143,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = st
         f.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+    lib.moda_scalarize.restype = st
+    lib.moda_scalarize.argtypes = [P, i32, i32, ctypes.POINTER(P)]
+    lib.moda_sbda_front.restype = st
+    lib.moda_sbda_front.argtypes = [P, ctypes.POINTER(P), i32, ctypes.POINTER(Point), i32,
+                                    ctypes.POINTER(i32), P]
     lib.moda_anneal_noalloc.restype = st
     lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
                                         ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
@@ -186,6 +192,23 @@ class Instance:
         _check(_lib.moda_create_instance(n, _ptr(self._F1), _ptr(self._F2), _ptr(self._D),
                                          pen, ctypes.byref(h)))
         self._h = h
+        self._info()
+
+    @classmethod
+    def _from_handle(cls, h):
+        self = cls.__new__(cls)
+        self._h = h
+        self._info()
+        return self
+
+    def scalarize(self, gamma_num: int, gamma_den: int) -> "Instance":
+        """``moda_scalarize``: the single-objective instance of Alg. 2 for
+        gamma = gamma_num / gamma_den, scaled by gamma_den."""
+        h = ctypes.c_void_p()
+        _check(_lib.moda_scalarize(self._h, int(gamma_num), int(gamma_den), ctypes.byref(h)))
+        return Instance._from_handle(h)
+
+    def _info(self):
         nn = ctypes.c_int32()
         w1, w2 = ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.moda_instance_info(self._h, ctypes.byref(nn), ctypes.byref(w1),
@@ -411,3 +434,39 @@ def probe_smem_peak(iters: int = 20000, stream=None) -> tuple[float, float]:
     _check(_lib.moda_probe_smem_peak(int(iters), _stream_handle(stream), ctypes.byref(v),
                                      ctypes.byref(ms)))
     return float(v.value), float(ms.value)
+
+
+def sbda(inst: Instance, *, replicas: int, I_max: int, seed: int = 0, gamma_den: int = 10,
+         gammas=None, delta0: float = 1e9, deltaf: float = 1e4, xi: float = 1e-3,
+         beta: int | None = None, block_threads: int = 0, stream=None):
+    """SB-DA (Alg. 2): one DA run (Alg. 1) per weight gamma = g / gamma_den,
+    g in ``gammas`` (default 0..gamma_den), all enqueued as one
+    ``moda_anneal_batch`` launch, then the merged non-dominated feasible
+    front (``moda_sbda_front``).  Returns (runs, front); front points are
+    dicts with c1, c2, weight (index into gammas), replica and perm."""
+    gammas = list(range(gamma_den + 1)) if gammas is None else list(gammas)
+    if beta is None:
+        beta = int(round(delta0 / I_max)) if I_max > 0 else 0
+    insts = [inst.scalarize(g, gamma_den) for g in gammas]
+    params = [make_params(replicas=replicas, I_max=I_max, seed=seed, escape="offset",
+                          archive_size=1, delta0=delta0 * gamma_den,
+                          deltaf=deltaf * gamma_den, xi=xi, beta=beta * gamma_den,
+                          block_threads=block_threads) for _ in gammas]
+    runs = anneal_batch(insts, params, stream=stream)
+    for r in runs:
+        r.wait()
+    return runs, sbda_front(inst, runs)
+
+
+def sbda_front(inst: Instance, runs) -> list[dict]:
+    """``moda_sbda_front`` over finished runs, one per weight."""
+    k = len(runs)
+    hs = (ctypes.c_void_p * k)(*[r._h for r in runs])
+    tot = ctypes.c_int32()
+    _check(_lib.moda_sbda_front(inst._h, hs, k, None, 0, ctypes.byref(tot), None))
+    cnt = max(tot.value, 1)
+    pts = (Point * cnt)()
+    perm = np.zeros((cnt, inst.n), dtype=np.uint8)
+    _check(_lib.moda_sbda_front(inst._h, hs, k, pts, tot.value, ctypes.byref(tot), _ptr(perm)))
+    return [dict(c1=pts[i].c1, c2=pts[i].c2, weight=pts[i].slot, replica=pts[i].replica,
+                 perm=[int(v) for v in perm[i]]) for i in range(tot.value)]

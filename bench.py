@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--prefetch", type=int, default=0,
                     help="field-cache prefetch distance + 1 (0: automatic)")
     ap.add_argument("--field-cache", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--normalize", action="store_true",
+                    help="QUBO normalisation (Sec. 4.2) in the acceptance test")
     ap.add_argument("--I-max", dest="I_max", type=int, default=None,
                     help="override the workload's iteration budget (profiling only)")
     return ap.parse_args(argv)
@@ -527,7 +529,7 @@ def main(argv=None):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(replicas=R, replica_base=base, I_max=I_max, seed=run["seed"],
               block_threads=args.block_threads, prefetch=args.prefetch,
-              field_cache=args.field_cache)
+              field_cache=args.field_cache, normalize=args.normalize)
 
     def step():
         r = moda.anneal(g, stream=stream, **kw).wait()

@@ -108,6 +108,14 @@ typedef struct {
   int32_t prefetch;      /* field-cache prefetch distance: 0 auto, k in 1..4
                             copies a jump's target k - 1 iterations ahead
                             (MODA_EUNSUPPORTED if it does not fit). */
+  int32_t normalize;     /* 1: QUBO normalisation of Sec. 4.2 -- each
+                            objective's largest cost-QUBO coefficient set to
+                            2^23 -- applied where it acts: the acceptance
+                            test sees s_k Delta E_k, s_k = 2^23 / (max Fs^k_ij
+                            * max d_uv), in IEEE double (the offset in the
+                            same units); archives and energies stay the
+                            unscaled integers, dominance being unchanged by
+                            a positive scale per objective.  0: off. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */

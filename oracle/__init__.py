@@ -69,6 +69,7 @@ class _Params(ctypes.Structure):
         ("escape", ctypes.c_int),
         ("check", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("normalize", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,8 @@ def _load():
         lib.oracle_mda_run_many.restype = ctypes.c_int
         lib.oracle_mda_run_many.argtypes = [P, ctypes.POINTER(_Params), i64, P, ctypes.c_int,
                                             P, P, P, P, P, P, P]
+        lib.oracle_norm_scale.restype = ctypes.c_double
+        lib.oracle_norm_scale.argtypes = [P, ctypes.c_int]
         lib.oracle_sbda_qubo.restype = P
         lib.oracle_sbda_qubo.argtypes = [P, i64, i64]
         lib.oracle_squbo_free.argtypes = [P]
@@ -185,6 +188,10 @@ class Instance:
         if x.size != self.m:
             raise ValueError("state has the wrong length")
         return x
+
+    def norm_scale(self, k: int) -> float:
+        """s_k = 2^23 / (largest coefficient of cost QUBO k), Sec. 4.2."""
+        return float(_load().oracle_norm_scale(self._h, int(k)))
 
     def energy(self, k: int, x) -> int:
         return int(_lib.oracle_energy(self._h, k, _ptr(self._bits(x))))
@@ -274,7 +281,7 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
         deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
         archive_size: int = 0, check: bool = False, trace: bool = False,
-        threads: int | None = None) -> dict:
+        threads: int | None = None, normalize: bool = False) -> dict:
     """Alg. 3 for each replica index in ``replicas`` (an int r means the
     replica indices 0..r-1).
 
@@ -293,7 +300,7 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     prm = _Params(int(I_max), float(delta0), float(deltaf), float(xi), int(beta), int(s),
                   ACCEPT[accept], ARCHIVE[archive], ESCAPE[escape], int(bool(check)),
-                  int(seed) & 0xFFFFFFFFFFFFFFFF)
+                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(normalize)))
     out = {
         "count": np.zeros(R, dtype=np.int64),
         "E": np.zeros((R, s, 2), dtype=np.int64),

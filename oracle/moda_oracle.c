@@ -319,7 +319,26 @@ typedef struct oracle_params {
   int check;          /* 1: recompute energies and fields from scratch
                          every iteration and fail on any mismatch */
   uint64_t seed;
+  int normalize;      /* 1: Sec. 4.2 normalisation, see oracle_norm_scale */
 } oracle_params;
+
+/* Sec. 4.2: "the largest QUBO coefficient representing any objective QUBO
+ * R and S" is set to 2^23.  Objective k is scaled by
+ *   s_k = 2^23 / max_{p <= q} C_k[p][q]      (1 if that maximum is 0)
+ * over its upper-triangular cost QUBO as the worked example prints it.
+ * Y_k = s_k R_k + alpha'_k G with alpha'_k from s_k R_k is s_k times the
+ * unscaled Y_k, so E'_k = s_k E_k; dominance between states is unchanged
+ * and only the acceptance test (Eqs. pacceptms / pacceptml / paccepts)
+ * sees the scale.  The scaled quantities are doubles, evaluated in IEEE
+ * double as written, operation by operation. */
+double oracle_norm_scale(const oracle_instance *inst, int k) {
+  const int64_t m = inst->m;
+  int64_t mx = 0;
+  for (int64_t p = 0; p < m; ++p)
+    for (int64_t q = p; q < m; ++q)
+      if (inst->C[k][p * m + q] > mx) mx = inst->C[k][p * m + q];
+  return mx > 0 ? 8388608.0 / (double)mx : 1.0;
+}
 
 /* Per-replica outputs. */
 typedef struct oracle_result {
@@ -484,6 +503,8 @@ int oracle_mda_run(const oracle_instance *inst, const oracle_params *prm,
   double delta = prm->delta0;
   const double factor = 1.0 - prm->xi;
   int64_t Eoff = 0;
+  const double sc0 = prm->normalize ? oracle_norm_scale(inst, 0) : 1.0;
+  const double sc1 = prm->normalize ? oracle_norm_scale(inst, 1) : 1.0;
 
   for (int64_t it = 1; it <= prm->I_max; ++it) {
     const uint32_t step = (uint32_t)it;
@@ -499,17 +520,29 @@ int oracle_mda_run(const oracle_instance *inst, const oracle_params *prm,
     /* Parallel trial: every bit is tested. */
     int64_t count = 0;
     for (int64_t p = 0; p < m; ++p) {
-      int64_t e0 = dE0[p], e1 = dE1[p];
-      if (prm->escape == 1) {
-        e0 -= Eoff;
-        e1 -= Eoff;
-      }
-      int64_t a0 = e0 > 0 ? e0 : 0, a1 = e1 > 0 ? e1 : 0;
-      int64_t a = prm->accept == 0 ? a0 + a1 : (a0 < a1 ? a0 : a1);
       uint32_t w = draw_word(prm->seed, (uint32_t)(p >> 2), step, replica,
                              TAG_ACCEPT, (int)(p & 3));
       double t = T[w >> 16];
-      if ((double)a <= delta * t) accepted[count++] = p;
+      if (!prm->normalize) {
+        int64_t e0 = dE0[p], e1 = dE1[p];
+        if (prm->escape == 1) {
+          e0 -= Eoff;
+          e1 -= Eoff;
+        }
+        int64_t a0 = e0 > 0 ? e0 : 0, a1 = e1 > 0 ? e1 : 0;
+        int64_t a = prm->accept == 0 ? a0 + a1 : (a0 < a1 ? a0 : a1);
+        if ((double)a <= delta * t) accepted[count++] = p;
+      } else {
+        /* normalised: s_k Delta E_k - E_offset per objective, in doubles */
+        double e0 = sc0 * (double)dE0[p], e1 = sc1 * (double)dE1[p];
+        if (prm->escape == 1) {
+          e0 = e0 - (double)Eoff;
+          e1 = e1 - (double)Eoff;
+        }
+        double a0 = e0 > 0 ? e0 : 0.0, a1 = e1 > 0 ? e1 : 0.0;
+        double a = prm->accept == 0 ? a0 + a1 : (a0 < a1 ? a0 : a1);
+        if (a <= delta * t) accepted[count++] = p;
+      }
     }
 
     int64_t event;

@@ -148,6 +148,7 @@ struct moda_instance_s {
   int device = 0;
   int64_t w1 = 0, w2 = 0;
   int64_t b1 = 0, b2 = 0;  // bounds of the local fields
+  int64_t c1max = 0, c2max = 0;  // largest cost-QUBO coefficients
   std::vector<int32_t> Fs1, Fs2, D;  // host copies
   int32_t *dFs1 = nullptr, *dFs2 = nullptr, *dD = nullptr;
 };
@@ -267,6 +268,16 @@ moda_status finish_instance(moda_instance inst, const moda_penalty *pen, moda_in
     f2max = std::max(f2max, s2);
   }
   const int64_t b1 = f1max * dmax, b2 = f2max * dmax;  // every entry is >= 0
+  {
+    int64_t e1 = 0, e2 = 0, ed = 0;
+    for (int e = 0; e < nn; ++e) {
+      e1 = std::max<int64_t>(e1, inst->Fs1[e]);
+      e2 = std::max<int64_t>(e2, inst->Fs2[e]);
+      ed = std::max<int64_t>(ed, inst->D[e]);
+    }
+    inst->c1max = e1 * ed;
+    inst->c2max = e2 * ed;
+  }
   if (b1 >= (int64_t(1) << 31) || b2 >= (int64_t(1) << 31)) {
     delete inst;
     return fail(MODA_EOVERFLOW, "local fields may exceed int32");
@@ -417,6 +428,8 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kMaxLookahead + 1)
     return fail(MODA_EINVAL, "prefetch must be in [0, 4]");
+  if (p->normalize != 0 && p->normalize != 1)
+    return fail(MODA_EINVAL, "normalize must be 0 or 1");
   const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Field cache: one record of the fields per archive slot, so a jump to
   // the archive reloads the member's fields instead of rebuilding them.
@@ -530,6 +543,11 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   a.bits_in_smem = place.bits_in_smem;
   a.lookahead = place.lookahead;
   a.de_in_smem = place.de_in_smem;
+  a.normalize = p->normalize;
+  a.s1 = p->normalize ? moda::norm_scale(inst->c1max) : 1.0;
+  a.s2 = p->normalize ? moda::norm_scale(inst->c2max) : 1.0;
+  a.tmin = dd->tmin;
+  a.tmax = dd->tmax;
   a.nsched = sch.count;
   a.sch_delta = sch.delta;
   a.sch_lo = sch.lo;
@@ -843,7 +861,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     const Prepared &pl = pls[i];
     cudaGraphNode_t n0, n1, n2, n3;
     const void *func = nullptr;
-    e = moda::anneal_function(pl.rounds, pl.narrow, pl.smem, &func);
+    e = moda::anneal_function(pl.rounds, pl.narrow, pl.args.normalize != 0, pl.smem, &func);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, r->start);
     if (e == cudaSuccess) {
       cudaMemsetParams mp{};

@@ -58,6 +58,9 @@ struct AnnealArgs {
   int32_t bits_in_smem;     // archive states kept in shared memory
   int32_t lookahead;        // field-cache prefetch distance (iterations)
   int32_t de_in_smem;       // accepted bits publish Delta E in shared memory
+  int32_t normalize;        // Sec. 4.2 normalisation in the acceptance test
+  double s1, s2;            // its per-objective scales (1 when off)
+  double tmin, tmax;        // -ln(u) at the largest and smallest u
   const double *sch_delta;  // [nsched] delta_t, t = 1..nsched
   const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
   const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
@@ -110,7 +113,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.mask = o;  o = align_up(o + 4 * 4 * items, 16);  // accept, state x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
   L.rnd = o;   o = align_up(o + 32 * 4 * 4, 16);             // 32 iterations
-  L.sch = o;   o = align_up(o + 32 * 32, 16);                // 32 entries
+  L.sch = o;   o = align_up(o + 32 * 48, 16);                // 32 entries
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
@@ -146,6 +149,13 @@ inline bool narrow_ok(int n, int64_t b1, int64_t b2, int64_t w1, int64_t w2) {
   return e1 + e2 < 2147483647.0L;
 }
 
+// Sec. 4.2 normalisation: objective k's scale 2^23 / (largest coefficient
+// of its cost QUBO), that coefficient being max Fs^k_ij * max d_uv for
+// non-negative flows and distances; 1 for an objective without cost.
+inline double norm_scale(int64_t max_coef) {
+  return max_coef > 0 ? 8388608.0 / (double)max_coef : 1.0;
+}
+
 // Bits per thread the kernel is instantiated for.
 bool supported_rounds(int b);
 
@@ -158,7 +168,8 @@ cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
 // threads per replica, `smem` bytes of dynamic shared memory, which this
 // call allows), for launching from a CUDA graph node with one AnnealArgs
 // argument.
-cudaError_t anneal_function(int rounds, bool narrow, size_t smem, const void **func);
+cudaError_t anneal_function(int rounds, bool narrow, bool norm, size_t smem,
+                            const void **func);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);

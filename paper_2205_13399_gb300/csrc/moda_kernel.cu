@@ -258,6 +258,9 @@ struct SchEntry {
   double delta;
   int64_t lo, hi;
   int32_t lo32, hi32;
+  // normalised acceptance: fl(delta T_min) and fl(delta T_max); lo and hi
+  // then bound the integer penalty (see fill_rings)
+  double lod, hid;
 };
 
 // What iteration t does when no bit is accepted (Alg. 3), settled by the
@@ -274,7 +277,9 @@ struct JumpRec {
 
 // NARROW: Delta E and the acceptance penalty in int32 (the host checked
 // |Delta E_1| + |Delta E_2| < 2^31 for every state); otherwise int64.
-template <int B, bool NARROW>
+// NORM: QUBO normalisation (Sec. 4.2), objective k's Delta E scaled by s_k
+// inside the acceptance test, in IEEE double.
+template <int B, bool NARROW, bool NORM>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
@@ -351,11 +356,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // iterations first .. first + 7 into the rings, all lanes on one path:
   // lane l < 24 draws tag kTagSelect + l % 3 of iteration first + l / 3,
   // lane l < 8 copies the schedule entry of iteration first + l.
+  // Normalised: the exact thresholds are fl(delta T_min) and fl(delta
+  // T_max) on the scaled penalty a'; lo and hi become integer bounds on the
+  // unscaled penalty A (a1 + a2, or their minimum), with s_min A <= a' <=
+  // s_max A up to a few roundings: A <= lo implies a' <= fl(delta T_min)
+  // and A > hi implies a' > fl(delta T_max), by margins of 1e-12.
+  const double s_min = A.s1 < A.s2 ? A.s1 : A.s2, s_max = A.s1 < A.s2 ? A.s2 : A.s1;
   auto fill_rings = [&](uint32_t first) {
     const uint32_t it = first + (uint32_t)(lane & 7);
     const uint32_t sn = (it <= nsched ? it : nsched) - 1;
     const double sd = A.sch_delta[sn];
-    const int64_t slo = A.sch_lo[sn], shi = A.sch_hi[sn];
+    int64_t slo = A.sch_lo[sn], shi = A.sch_hi[sn];
+    double lod = 0, hid = 0;
+    if (NORM) {
+      lod = __dmul_rn(sd, A.tmin);
+      hid = __dmul_rn(sd, A.tmax);
+      const double ql = floor(lod / (s_max * (1.0 + 1e-12)));
+      const double qh = floor(hid / (s_min * (1.0 - 1e-12)));
+      slo = ql < 4.0e18 ? (int64_t)ql : (int64_t)4000000000000000000ll;
+      shi = qh < 4.0e18 ? (int64_t)qh : (int64_t)4000000000000000000ll;
+    }
     const uint32_t q = first + (uint32_t)(lane < 24 ? lane / 3 : 7);
     const uint32_t tag = (uint32_t)(lane % 3);
     uint32_t c[4] = {0u, q, rep, kTagSelect + tag};
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (lane < 24) sRnd[(q % kRing) * 4 + tag] = c[0];
     if (lane < 8)
       sSch[it % kRing] = SchEntry{sd, slo, shi, (int32_t)(slo < 2147483647ll ? slo : 2147483647ll),
-                                  (int32_t)(shi < 2147483647ll ? shi : 2147483647ll)};
+                                  (int32_t)(shi < 2147483647ll ? shi : 2147483647ll), lod, hid};
   };
   if (control) {
     if (lane == 0 && pf) {
@@ -506,13 +526,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   uint32_t pend = 0, ph = 0;
   JumpRec jr{kNone, 0, -1, 0};
   // schedule entry of the current iteration, in registers
-  double cur_delta;
+  double cur_delta, cur_lod = 0, cur_hid = 0;
   dE_t cur_lo, cur_hi;
   {
     const SchEntry e = sSch[1];
     cur_delta = e.delta;
     cur_lo = NARROW ? (dE_t)e.lo32 : (dE_t)e.lo;
     cur_hi = NARROW ? (dE_t)e.hi32 : (dE_t)e.hi;
+    if (NORM) {
+      cur_lod = e.lod;
+      cur_hid = e.hid;
+    }
   }
 
   for (uint32_t t = 1; t <= I_max; ++t) {
@@ -527,6 +551,48 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const dE_t e1 = D1[k], e2 = D2[k];
+        if (NORM) {
+          const bool in = k * Tw + tid < m;
+          const dE_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
+          const dE_t ai = A.accept == 0 ? u1 + u2 : (u1 < u2 ? u1 : u2);
+          bool acc = false, need = in;  // offset escape: every bit exactly
+          if (A.escape == 0) {
+            acc = in && ai <= lo;
+            need = in && ai > lo && ai <= hi;
+          }
+          if (__any_sync(kFull, need)) {
+            // a' = s_1 Delta E_1 (- E_off), ... in IEEE double, as written
+            double x1 = __dmul_rn(A.s1, (double)e1), x2 = __dmul_rn(A.s2, (double)e2);
+            if (A.escape == 1) {
+              x1 = __dsub_rn(x1, (double)Eoff);
+              x2 = __dsub_rn(x2, (double)Eoff);
+            }
+            const double b1 = x1 > 0 ? x1 : 0.0, b2 = x2 > 0 ? x2 : 0.0;
+            const double ad = A.accept == 0 ? __dadd_rn(b1, b2) : (b1 < b2 ? b1 : b2);
+            if (need && ad <= cur_lod) acc = true;
+            const bool draw = need && ad > cur_lod && ad <= cur_hid;
+            if (__any_sync(kFull, draw)) {
+              const int p = k * Tw + tid;
+              uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
+              philox10(c, k0, k1);
+              const uint32_t w = word_of(c, p & 3);
+              if (draw) acc = ad <= __dmul_rn(delta, A.table[w >> 16]);
+            }
+          }
+          if (acc && de_smem) {
+            dE2_t v;
+            v.x = e1;
+            v.y = e2;
+            sDE[k * Tw + tid] = v;
+          }
+          const uint32_t bal = __ballot_sync(kFull, acc);
+          if (lane == 0) mask[k * NWB + warp] = bal;
+          if (de_smem) {
+            const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
+            if (lane == 0) xm[k * NWB + warp] = xb;
+          }
+          continue;
+        }
         dE_t a1, a2;
         if (A.escape == 1) {  // the offset lowers Delta E (Alg. 1)
           const dE_t off = NARROW ? (dE_t)(Eoff < 2147483647ll ? Eoff : 2147483647ll) : (dE_t)Eoff;
@@ -841,6 +907,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     cur_delta = nse.delta;
     cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
     cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;
+    if (NORM) {
+      cur_lod = nse.lod;
+      cur_hid = nse.hid;
+    }
     if (A.trace != nullptr && tid == 0) {
       int64_t *tr = A.trace + ((size_t)rb * (size_t)I_max + (size_t)(t - 1)) * 3;
       tr[0] = E1;
@@ -891,27 +961,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 }
 
-template <int B, bool NARROW>
+template <int B, bool NARROW, bool NORM>
 cudaError_t launch_bn(const AnnealArgs &args, int replicas, int workers,
                       size_t smem, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(
-      anneal_kernel<B, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      anneal_kernel<B, NARROW, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  anneal_kernel<B, NARROW><<<replicas, workers + 32, smem, stream>>>(args);
+  anneal_kernel<B, NARROW, NORM><<<replicas, workers + 32, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
 template <int B>
 cudaError_t launch_b(const AnnealArgs &args, int replicas, int workers, bool narrow,
                      size_t smem, cudaStream_t stream) {
-  return narrow ? launch_bn<B, true>(args, replicas, workers, smem, stream)
-                : launch_bn<B, false>(args, replicas, workers, smem, stream);
+  if (args.normalize)
+    return narrow ? launch_bn<B, true, true>(args, replicas, workers, smem, stream)
+                  : launch_bn<B, false, true>(args, replicas, workers, smem, stream);
+  return narrow ? launch_bn<B, true, false>(args, replicas, workers, smem, stream)
+                : launch_bn<B, false, false>(args, replicas, workers, smem, stream);
 }
 
 template <int B>
-cudaError_t function_b(bool narrow, size_t smem, const void **func) {
-  const void *f = narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true>)
-                         : reinterpret_cast<const void *>(anneal_kernel<B, false>);
+cudaError_t function_b(bool narrow, bool norm, size_t smem, const void **func) {
+  const void *f =
+      norm ? (narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true, true>)
+                     : reinterpret_cast<const void *>(anneal_kernel<B, false, true>))
+           : (narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true, false>)
+                     : reinterpret_cast<const void *>(anneal_kernel<B, false, false>));
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) *func = f;
   return e;
@@ -923,14 +999,15 @@ bool supported_rounds(int b) {
   return b == 1 || b == 2 || b == 3 || b == 4 || b == 6 || b == 8;
 }
 
-cudaError_t anneal_function(int rounds, bool narrow, size_t smem, const void **func) {
+cudaError_t anneal_function(int rounds, bool narrow, bool norm, size_t smem,
+                            const void **func) {
   switch (rounds) {
-    case 1: return function_b<1>(narrow, smem, func);
-    case 2: return function_b<2>(narrow, smem, func);
-    case 3: return function_b<3>(narrow, smem, func);
-    case 4: return function_b<4>(narrow, smem, func);
-    case 6: return function_b<6>(narrow, smem, func);
-    case 8: return function_b<8>(narrow, smem, func);
+    case 1: return function_b<1>(narrow, norm, smem, func);
+    case 2: return function_b<2>(narrow, norm, smem, func);
+    case 3: return function_b<3>(narrow, norm, smem, func);
+    case 4: return function_b<4>(narrow, norm, smem, func);
+    case 6: return function_b<6>(narrow, norm, smem, func);
+    case 8: return function_b<8>(narrow, norm, smem, func);
     default: return cudaErrorInvalidValue;
   }
 }

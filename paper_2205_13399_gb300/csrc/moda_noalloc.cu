@@ -161,6 +161,14 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   }
   if (f1max * dmax >= (int64_t(1) << 31) || f2max * dmax >= (int64_t(1) << 31))
     return nofail(MODA_EOVERFLOW, "local fields may exceed int32");
+  if (p->normalize != 0 && p->normalize != 1)
+    return nofail(MODA_EINVAL, "normalize must be 0 or 1");
+  int64_t e1max = 0, e2max = 0, edmax = 0;  // largest entries (normalisation)
+  for (int e = 0; e < n * n; ++e) {
+    e1max = std::max<int64_t>(e1max, fs1[e]);
+    e2max = std::max<int64_t>(e2max, fs2[e]);
+    edmax = std::max<int64_t>(edmax, dd[e]);
+  }
   const int64_t w1 = pen && pen->kind == 1 ? pen->w1 : f1max * dmax;
   const int64_t w2 = pen && pen->kind == 1 ? pen->w2 : f2max * dmax;
 
@@ -270,6 +278,11 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   a.bits_in_smem = place.bits_in_smem;
   a.lookahead = place.lookahead;
   a.de_in_smem = place.de_in_smem;
+  a.normalize = p->normalize;
+  a.s1 = p->normalize ? moda::norm_scale(e1max * edmax) : 1.0;
+  a.s2 = p->normalize ? moda::norm_scale(e2max * edmax) : 1.0;
+  a.tmin = S->tmin;
+  a.tmax = S->tmax;
   a.sch_delta = S->delta;
   a.sch_lo = S->lo;
   a.sch_hi = S->hi;

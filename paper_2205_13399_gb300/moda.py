@@ -66,6 +66,7 @@ class Params(ctypes.Structure):
         ("trace", ctypes.c_int32),
         ("field_cache", ctypes.c_int32),
         ("prefetch", ctypes.c_int32),
+        ("normalize", ctypes.c_int32),
     ]
 
 
@@ -317,13 +318,14 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
                 deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
-                trace: bool = False, field_cache: str = "auto", prefetch: int = 0) -> Params:
+                trace: bool = False, field_cache: str = "auto", prefetch: int = 0,
+                normalize: bool = False) -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
-                  int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch))
+                  int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)))
 
 
 def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,

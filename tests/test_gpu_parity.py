@@ -163,3 +163,30 @@ def test_large_configs_prefix(name, cache):
     rows = [1, run["replicas"] - 1]
     _, orc = oracle_run(inst, replicas=rows, I_max=I_max, seed=run["seed"])
     compare(res, rows, orc, inst.n * inst.n)
+
+
+@pytest.mark.parametrize("cache", ["on", "off"])
+@pytest.mark.parametrize("acc,arc,esc", VARIANTS)
+def test_normalised_variants_traced(acc, arc, esc, cache):
+    """QUBO normalisation (Sec. 4.2) in the acceptance test: trajectories,
+    archives and counters equal the oracle's, per iteration, for every mode,
+    narrow and wide Delta E, one and several bits per thread."""
+    if esc == "offset" and cache == "on":
+        pytest.skip("the field cache serves only jumps to the archive")
+    for n, bt in ((5, 0), (9, 0), (12, 32), (20, 0)):
+        inst = inputs.uniform_instance(n, index=100 + n, workload="P8")
+        kw = dict(replicas=3, I_max=1500, seed=21 + n, accept=acc, archive=arc, escape=esc,
+                  beta=700, **FAST)
+        _, _, res, tr = gpu_run(inst, block_threads=bt, trace=True, field_cache=cache,
+                                normalize=True, **kw)
+        _, orc = oracle_run(inst, trace=True, normalize=True, **kw)
+        compare(res, range(3), orc, n * n, gpu_trace=tr)
+
+
+def test_normalised_wide_and_schedule_tail():
+    """A wide (int64 Delta E) instance past the end of the cooling schedule."""
+    inst = inputs.workload_instance("P50")
+    kw = dict(replicas=2, I_max=14000, seed=5, **FAST)
+    _, _, res, tr = gpu_run(inst, trace=True, normalize=True, **kw)
+    _, orc = oracle_run(inst, trace=True, normalize=True, **kw)
+    compare(res, range(2), orc, inst.n * inst.n, gpu_trace=tr)

@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["moda", "reference"], default="moda")
     ap.add_argument("--workload", default="P25",
-                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE", "SBDA"])
+                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE", "SBDA", "HVTRACE"])
     ap.add_argument("--instances", type=int, default=512, help="BATCH: instances")
     ap.add_argument("--seq-instances", type=int, default=24,
                     help="BATCH / SERVE: requests also run one at a time for comparison")
@@ -498,6 +498,66 @@ def run_sbda(args):
     return 0
 
 
+def run_hvtrace(args):
+    """Fig. mdasl: the hypervolume of the merged archive after every K
+    iterations, strict against lenient acceptance (explorative archive), on
+    the P25 instance; feasible points' costs normalised to [1, 2] over both
+    runs, reference point (2.1, 2.1), so 1.21 is the largest possible."""
+    import torch
+    from paper_2205_13399_gb300 import inputs, moda
+    qi = inputs.workload_instance("P25")
+    run = dict(inputs.WORKLOAD_RUN["P25"])
+    if args.I_max is not None:
+        run["I_max"] = args.I_max
+    R, I_max = run["replicas"], run["I_max"]
+    K = max(1, I_max // 100)
+    inst = moda.Instance(qi.F1, qi.F2, qi.D)
+    out, ms = {}, {}
+    for _ in range(args.warmup):
+        moda.anneal(inst, replicas=R, I_max=min(I_max, 2000), seed=run["seed"]).wait().close()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for acc in ("strict", "lenient"):
+        r = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"], accept=acc,
+                        snapshot_every=K).wait()
+        ms[acc] = r.elapsed_ms()
+        out[acc] = [[(p["c1"], p["c2"]) for p in r.read_archive(snapshot=j, perms=False)
+                     if p["feasible"]] for j in range(I_max // K)]
+        r.close()
+    plain = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"]).wait()
+    plain_ms = plain.elapsed_ms()
+    plain.close()
+    clk = clocks.stop()
+    allp = [p for acc in out for f in out[acc] for p in f]
+    lo = (min(p[0] for p in allp), min(p[1] for p in allp)) if allp else (0, 0)
+    hi = (max(p[0] for p in allp), max(p[1] for p in allp)) if allp else (1, 1)
+    hv = {acc: [hv_norm(f, lo, hi) if f else 0.0 for f in out[acc]] for acc in out}
+
+    def reach(curve, frac=0.95):
+        top = curve[-1]
+        for j, v in enumerate(curve):
+            if v >= frac * top:
+                return (j + 1) * K
+        return None
+
+    line = {
+        "metric": "replica-steps/s", "value": R * I_max / (ms["strict"] / 1e3),
+        "unit": "replica-steps/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": ms["strict"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"HVTRACE: P25, {R} replicas, I_max={I_max}, archive snapshot "
+                               f"every {K} iterations, strict vs lenient (explore)",
+                   "snapshot_every": K},
+        "hv_final": {acc: hv[acc][-1] for acc in hv},
+        "iterations_to_95pct_hv": {acc: reach(hv[acc]) for acc in hv},
+        "hv_every_10_snapshots": {acc: [round(v, 4) for v in hv[acc][9::10]] for acc in hv},
+        "snapshot_overhead": {"ms_with": ms["strict"], "ms_plain": plain_ms},
+        "gpu_launches": 2, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -505,11 +565,12 @@ def main(argv=None):
     world, rank, local = dist_env()
     import numpy as np
     import torch
-    if args.workload in ("BATCH", "SERVE", "SBDA"):
+    if args.workload in ("BATCH", "SERVE", "SBDA", "HVTRACE"):
         if world > 1:
-            raise SystemExit("BATCH, SERVE and SBDA run on one GPU")
+            raise SystemExit("BATCH, SERVE, SBDA and HVTRACE run on one GPU")
         torch.cuda.set_device(local)
-        return {"BATCH": run_batch, "SERVE": run_serve, "SBDA": run_sbda}[args.workload](args)
+        return {"BATCH": run_batch, "SERVE": run_serve, "SBDA": run_sbda,
+                "HVTRACE": run_hvtrace}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")

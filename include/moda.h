@@ -116,6 +116,11 @@ typedef struct {
                             same units); archives and energies stay the
                             unscaled integers, dominance being unchanged by
                             a positive scale per objective.  0: off. */
+  int32_t snapshot_every; /* K > 0: after every iteration t with t % K == 0
+                            the kernel copies each replica's archive to the
+                            run (I_max / K snapshots, for the hypervolume
+                            trace of Fig. mdasl; moda_read_snapshot);
+                            0: none.  Not with moda_anneal_noalloc. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */
@@ -201,6 +206,11 @@ moda_status moda_read_trace(moda_run run, int32_t r, int64_t *trace);
  * facility, or 0xFF for an infeasible point. */
 moda_status moda_read_archive(moda_run run, int32_t r, moda_point *pts,
                               int32_t cap, int32_t *count, uint8_t *perms);
+
+/* As moda_read_archive, for the archive as it stood after iteration
+ * (snap + 1) * params.snapshot_every (0 <= snap < I_max / snapshot_every). */
+moda_status moda_read_snapshot(moda_run run, int32_t snap, int32_t r, moda_point *pts,
+                               int32_t cap, int32_t *count, uint8_t *perms);
 
 /* Device time of the anneal kernel of a finished run, in milliseconds
  * (CUDA events on the run's stream). */

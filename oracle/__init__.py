@@ -70,6 +70,7 @@ class _Params(ctypes.Structure):
         ("check", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("normalize", ctypes.c_int),
+        ("snap_every", ctypes.c_int64),
     ]
 
 
@@ -121,7 +122,7 @@ def _load():
                                             ctypes.c_uint32, i64]
         lib.oracle_mda_run_many.restype = ctypes.c_int
         lib.oracle_mda_run_many.argtypes = [P, ctypes.POINTER(_Params), i64, P, ctypes.c_int,
-                                            P, P, P, P, P, P, P]
+                                            P, P, P, P, P, P, P, P, P, P]
         lib.oracle_norm_scale.restype = ctypes.c_double
         lib.oracle_norm_scale.argtypes = [P, ctypes.c_int]
         lib.oracle_sbda_qubo.restype = P
@@ -281,7 +282,7 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
         deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
         archive_size: int = 0, check: bool = False, trace: bool = False,
-        threads: int | None = None, normalize: bool = False) -> dict:
+        threads: int | None = None, normalize: bool = False, snapshot_every: int = 0) -> dict:
     """Alg. 3 for each replica index in ``replicas`` (an int r means the
     replica indices 0..r-1).
 
@@ -300,7 +301,7 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     prm = _Params(int(I_max), float(delta0), float(deltaf), float(xi), int(beta), int(s),
                   ACCEPT[accept], ARCHIVE[archive], ESCAPE[escape], int(bool(check)),
-                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(normalize)))
+                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(normalize)), int(snapshot_every))
     out = {
         "count": np.zeros(R, dtype=np.int64),
         "E": np.zeros((R, s, 2), dtype=np.int64),
@@ -310,15 +311,26 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
         "stats": np.zeros((R, 4), dtype=np.int64),
     }
     tr = np.zeros((R, I_max, 3), dtype=np.int64) if trace else None
+    ns = I_max // snapshot_every if snapshot_every > 0 else 0
+    snap = None
+    if ns > 0:
+        snap = {"count": np.zeros((R, ns), dtype=np.int64),
+                "E": np.zeros((R, ns, s, 2), dtype=np.int64),
+                "bits": np.zeros((R, ns, s, m), dtype=np.uint8)}
     nth = threads if threads else (os.cpu_count() or 1)
     rc = lib.oracle_mda_run_many(inst._h, ctypes.byref(prm), R, _ptr(reps), int(nth),
                                  _ptr(out["count"]), _ptr(out["E"]), _ptr(out["bits"]),
                                  _ptr(out["x"]), _ptr(out["E_final"]), _ptr(out["stats"]),
-                                 _ptr(tr) if tr is not None else None)
+                                 _ptr(tr) if tr is not None else None,
+                                 _ptr(snap["count"]) if snap else None,
+                                 _ptr(snap["E"]) if snap else None,
+                                 _ptr(snap["bits"]) if snap else None)
     if rc != 0:
         raise RuntimeError(f"oracle run failed with code {rc}")
     if tr is not None:
         out["trace"] = tr
+    if snap is not None:
+        out["snapshots"] = snap
     return out
 
 

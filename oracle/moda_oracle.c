@@ -320,6 +320,9 @@ typedef struct oracle_params {
                          every iteration and fail on any mismatch */
   uint64_t seed;
   int normalize;      /* 1: Sec. 4.2 normalisation, see oracle_norm_scale */
+  int64_t snap_every; /* > 0: copy the archive after every iteration t with
+                         t % snap_every == 0 (the per-iteration archive
+                         behind Fig. mdasl's hypervolume trace) */
 } oracle_params;
 
 /* Sec. 4.2: "the largest QUBO coefficient representing any objective QUBO
@@ -350,6 +353,9 @@ typedef struct oracle_result {
   int64_t stats[4];      /* flips, jumps to the archive, escapes with an empty
                             archive, offset raises */
   int64_t *trace;        /* [I_max][3] E1, E2, event, or NULL */
+  int64_t *snap_count;   /* [I_max / snap_every] archive sizes, or NULL */
+  int64_t *snap_E;       /* [I_max / snap_every][s][2] */
+  uint8_t *snap_bits;    /* [I_max / snap_every][s][m] */
 } oracle_result;
 
 /* x dominates y (Sec. 3.3): no worse in both energies and not equivalent. */
@@ -589,6 +595,12 @@ int oracle_mda_run(const oracle_instance *inst, const oracle_params *prm,
       res->stats[3] += 1;
       event = INT64_MIN;
     }
+    if (res->snap_count && prm->snap_every > 0 && it % prm->snap_every == 0) {
+      const int64_t j = it / prm->snap_every - 1;
+      res->snap_count[j] = res->archive_count;
+      memcpy(res->snap_E + j * s * 2, res->archive_E, sizeof(int64_t) * (size_t)(2 * s));
+      memcpy(res->snap_bits + j * s * m, res->archive_bits, (size_t)(s * m));
+    }
     if (res->trace) {
       res->trace[(it - 1) * 3 + 0] = E[0];
       res->trace[(it - 1) * 3 + 1] = E[1];
@@ -628,6 +640,8 @@ typedef struct {
   int64_t n_rep;
   int64_t *count, *E, *E_final, *stats, *trace;
   uint8_t *bits, *x_final;
+  int64_t *snap_count, *snap_E;
+  uint8_t *snap_bits;
   int64_t next;
   int rc;
   pthread_mutex_t lock;
@@ -647,6 +661,10 @@ static void *batch_worker(void *arg) {
     res.archive_bits = job->bits + r * s * m;
     res.x_final = job->x_final + r * m;
     res.trace = job->trace ? job->trace + r * job->prm->I_max * 3 : NULL;
+    const int64_t ns = job->prm->snap_every > 0 ? job->prm->I_max / job->prm->snap_every : 0;
+    res.snap_count = job->snap_count && ns > 0 ? job->snap_count + r * ns : NULL;
+    res.snap_E = job->snap_E ? job->snap_E + r * ns * s * 2 : NULL;
+    res.snap_bits = job->snap_bits ? job->snap_bits + r * ns * s * m : NULL;
     int rc = oracle_mda_run(job->inst, job->prm, job->replicas[r], &res);
     job->count[r] = res.archive_count;
     job->E_final[r * 2 + 0] = res.E_final[0];
@@ -665,9 +683,13 @@ int oracle_mda_run_many(const oracle_instance *inst, const oracle_params *prm,
                         int64_t n_rep, const uint32_t *replicas, int nthreads,
                         int64_t *count, int64_t *E, uint8_t *bits,
                         uint8_t *x_final, int64_t *E_final, int64_t *stats,
-                        int64_t *trace) {
+                        int64_t *trace, int64_t *snap_count, int64_t *snap_E,
+                        uint8_t *snap_bits) {
   batch_job job;
   memset(&job, 0, sizeof(job));
+  job.snap_count = snap_count;
+  job.snap_E = snap_E;
+  job.snap_bits = snap_bits;
   job.inst = inst; job.prm = prm; job.replicas = replicas; job.n_rep = n_rep;
   job.count = count; job.E = E; job.bits = bits; job.x_final = x_final;
   job.E_final = E_final; job.stats = stats; job.trace = trace;

@@ -176,13 +176,18 @@ struct moda_run_s {
   bool checked = false;
   size_t bytes = 0;  // device memory held by the run's buffers
   std::shared_ptr<ServerAccount> acct;  // serving: released on destroy
+  int32_t nsnap = 0;  // archive snapshots: I_max / snapshot_every
+  int32_t *snap_count = nullptr;
+  int64_t *snap_E = nullptr;
+  uint32_t *snap_bits = nullptr;
 };
 
 namespace {
 
 void free_run_buffers(moda_run r) {
   void *ptrs[] = {r->arch_E, r->arch_bits, r->arch_count, r->x_final,
-                  r->E_final, r->stats, r->trace, r->error, r->fcache};
+                  r->E_final, r->stats, r->trace, r->error, r->fcache,
+                  r->snap_count, r->snap_E, r->snap_bits};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (r->start) cudaEventDestroy(r->start);
@@ -401,7 +406,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   int T = 0, B = 0;
   if (p->block_threads > 0) {
     if (p->block_threads % 32 || p->block_threads > moda::kMaxWorkers)
-      return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 992");
+      return fail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 960");
     T = p->block_threads;
     for (int b : kRounds)
       if ((int64_t)b * T >= m) {
@@ -430,6 +435,9 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
     return fail(MODA_EINVAL, "prefetch must be in [0, 4]");
   if (p->normalize != 0 && p->normalize != 1)
     return fail(MODA_EINVAL, "normalize must be 0 or 1");
+  if (p->snapshot_every < 0) return fail(MODA_EINVAL, "snapshot_every must be >= 0");
+  if (p->snapshot_every > 0 && p->I_max / p->snapshot_every > 1000000)
+    return fail(MODA_EINVAL, "more than 10^6 snapshots");
   const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Field cache: one record of the fields per archive slot, so a jump to
   // the archive reloads the member's fields instead of rebuilding them.
@@ -444,9 +452,10 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
     want_cache = cache_bytes <= free_b / 10 * 6;
   }
   // Shared-memory placement, best first: the field cache (if wanted), the
-  // archive energies and states on chip (then energies only, then
-  // neither), Delta E published in shared memory, and the prefetch
-  // distance (1, then 0 iterations, unless prescribed).
+  // prefetch distance (1, then 0 iterations, then reading the cache in
+  // place, unless prescribed), the archive energies and states on chip
+  // (then energies only, then neither), Delta E published in shared
+  // memory.
   moda::Placement place{};
   bool placed = false;
   moda::SmemLayout lay{};
@@ -454,9 +463,9 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   // (prefetch distance -1: the cache is read in place, no buffers)
   const int la_lo = p->prefetch > 0 ? p->prefetch - 1 : -1;
   for (int c = want_cache ? 1 : 0; c >= 0 && !placed; --c)
-    for (int opt = 0; opt < 3 && !placed; ++opt)
-      for (int de = 1; de >= 0 && !placed; --de)
-        for (int la = c ? la_hi : 0; la >= (c ? la_lo : 0) && !placed; --la) {
+    for (int la = c ? la_hi : 0; la >= (c ? la_lo : 0) && !placed; --la)
+      for (int opt = 0; opt < 3 && !placed; ++opt)
+        for (int de = 1; de >= 0 && !placed; --de) {
           const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1, narrow};
           const moda::SmemLayout l =
               moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, pl);
@@ -503,6 +512,13 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   alloc((void **)&r->error, sizeof(int32_t));
   if (p->trace && p->I_max > 0)
     alloc((void **)&r->trace, R * (size_t)p->I_max * 3 * sizeof(int64_t));
+  if (p->snapshot_every > 0 && p->I_max / p->snapshot_every > 0) {
+    r->nsnap = (int32_t)(p->I_max / p->snapshot_every);
+    const size_t ns = (size_t)r->nsnap;
+    alloc((void **)&r->snap_count, R * ns * sizeof(int32_t));
+    alloc((void **)&r->snap_E, R * ns * s * 2 * sizeof(int64_t));
+    alloc((void **)&r->snap_bits, R * ns * s * W * sizeof(uint32_t));
+  }
   if (st != MODA_OK) {
     free_run_buffers(r);
     delete r;
@@ -548,6 +564,11 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   a.s2 = p->normalize ? moda::norm_scale(inst->c2max) : 1.0;
   a.tmin = dd->tmin;
   a.tmax = dd->tmax;
+  a.snap_every = r->nsnap > 0 ? p->snapshot_every : 0;
+  a.nsnap = r->nsnap;
+  a.snap_count = r->snap_count;
+  a.snap_E = r->snap_E;
+  a.snap_bits = r->snap_bits;
   a.nsched = sch.count;
   a.sch_delta = sch.delta;
   a.sch_lo = sch.lo;
@@ -595,6 +616,10 @@ size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
   if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2)
     b += R * s * moda::slot_layout((int)m, narrow).bytes;
   if (p.trace && p.I_max > 0) b += R * (size_t)p.I_max * 3 * sizeof(int64_t);
+  if (p.snapshot_every > 0) {
+    const size_t ns = (size_t)(p.I_max / p.snapshot_every);
+    b += R * ns * (sizeof(int32_t) + s * 2 * sizeof(int64_t) + s * W * sizeof(uint32_t));
+  }
   return b;
 }
 
@@ -698,30 +723,35 @@ moda_status moda_read_trace(moda_run r, int32_t rep, int64_t *trace) {
   return MODA_OK;
 }
 
-moda_status moda_read_archive(moda_run r, int32_t rep, moda_point *pts,
-                              int32_t cap, int32_t *count, uint8_t *perms) {
-  if (!r || !count) return fail(MODA_EINVAL, "NULL argument");
-  if (rep < -1 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
-  if (cap < 0 || (cap > 0 && !pts)) return fail(MODA_EINVAL, "bad output buffer");
-  cudaSetDevice(r->inst->device);
-  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+}  // extern "C"
+
+namespace {
+
+// The non-dominated members of replica `rep` (or all, rep == -1) of an
+// archive held on the device as counts[q * ns + j], energies at
+// E + (q * ns + j) * s * 2 and states at bits + (q * ns + j) * s * W: the
+// final archives (ns = 1, j = 0) or snapshot j of ns.
+moda_status archive_front(moda_run r, int32_t rep, moda_point *pts, int32_t cap,
+                          int32_t *count, uint8_t *perms, const int32_t *dcnt,
+                          const int64_t *dE, const uint32_t *dbits, size_t ns, size_t j) {
   const int n = r->inst->n, W = r->inst->W;
   const size_t s = r->s;
   const int first = rep < 0 ? 0 : rep, last = rep < 0 ? r->R : rep + 1;
-  const size_t nrep = (size_t)(last - first);
-  std::vector<int32_t> counts(nrep);
-  std::vector<int64_t> E(nrep * s * 2);
-  moda_status st = moda_read_replica(r, rep, counts.data(), E.data(), nullptr,
-                                     nullptr, nullptr, nullptr);
-  if (st != MODA_OK) return st;
   struct Cand {
     int64_t e1, e2;
     int32_t rep, slot;
   };
   std::vector<Cand> c;
-  for (size_t q = 0; q < nrep; ++q)
-    for (int32_t k = 0; k < counts[q]; ++k)
-      c.push_back({E[(q * s + k) * 2], E[(q * s + k) * 2 + 1], (int32_t)(first + q), k});
+  std::vector<int64_t> E(s * 2);
+  for (int q = first; q < last; ++q) {
+    int32_t cnt = 0;
+    const size_t row = (size_t)q * ns + j;
+    MODA_CUDA(cudaMemcpy(&cnt, dcnt + row, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (cnt <= 0) continue;
+    MODA_CUDA(cudaMemcpy(E.data(), dE + row * s * 2, sizeof(int64_t) * 2 * (size_t)cnt,
+                         cudaMemcpyDeviceToHost));
+    for (int32_t k = 0; k < cnt; ++k) c.push_back({E[2 * k], E[2 * k + 1], q, k});
+  }
   std::sort(c.begin(), c.end(), [](const Cand &a, const Cand &b) {
     if (a.e1 != b.e1) return a.e1 < b.e1;
     if (a.e2 != b.e2) return a.e2 < b.e2;
@@ -746,7 +776,7 @@ moda_status moda_read_archive(moda_run r, int32_t rep, moda_point *pts,
   std::vector<uint32_t> word(W);
   for (int k = 0; k < wr; ++k) {
     const Cand &q = keep[k];
-    MODA_CUDA(cudaMemcpy(word.data(), r->arch_bits + ((size_t)q.rep * s + q.slot) * W,
+    MODA_CUDA(cudaMemcpy(word.data(), dbits + (((size_t)q.rep * ns + j) * s + q.slot) * W,
                          W * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     std::vector<int> rows(n, 0), cols(n, 0), loc(n, -1);
     for (int p = 0; p < n * n; ++p)
@@ -773,6 +803,34 @@ moda_status moda_read_archive(moda_run r, int32_t rep, moda_point *pts,
         perms[(size_t)k * n + i] = g == 0 ? (uint8_t)loc[i] : (uint8_t)0xFF;
   }
   return MODA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+moda_status moda_read_archive(moda_run r, int32_t rep, moda_point *pts,
+                              int32_t cap, int32_t *count, uint8_t *perms) {
+  if (!r || !count) return fail(MODA_EINVAL, "NULL argument");
+  if (rep < -1 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
+  if (cap < 0 || (cap > 0 && !pts)) return fail(MODA_EINVAL, "bad output buffer");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  return archive_front(r, rep, pts, cap, count, perms, r->arch_count, r->arch_E,
+                       r->arch_bits, 1, 0);
+}
+
+moda_status moda_read_snapshot(moda_run r, int32_t snap, int32_t rep, moda_point *pts,
+                               int32_t cap, int32_t *count, uint8_t *perms) {
+  if (!r || !count) return fail(MODA_EINVAL, "NULL argument");
+  if (r->nsnap == 0) return fail(MODA_EINVAL, "the run took no snapshots");
+  if (snap < 0 || snap >= r->nsnap) return fail(MODA_EINVAL, "snapshot out of range");
+  if (rep < -1 || rep >= r->R) return fail(MODA_EINVAL, "replica out of range");
+  if (cap < 0 || (cap > 0 && !pts)) return fail(MODA_EINVAL, "bad output buffer");
+  cudaSetDevice(r->inst->device);
+  if (!run_done(r)) return fail(MODA_EBUSY, "run still executing");
+  return archive_front(r, rep, pts, cap, count, perms, r->snap_count, r->snap_E,
+                       r->snap_bits, (size_t)r->nsnap, (size_t)snap);
 }
 
 moda_status moda_run_elapsed_ms(moda_run r, float *ms) {
@@ -861,7 +919,8 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     const Prepared &pl = pls[i];
     cudaGraphNode_t n0, n1, n2, n3;
     const void *func = nullptr;
-    e = moda::anneal_function(pl.rounds, pl.narrow, pl.args.normalize != 0, pl.smem, &func);
+    e = moda::anneal_function(pl.rounds, pl.narrow, moda::uses_extensions(pl.args), pl.smem,
+                              &func);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, r->start);
     if (e == cudaSuccess) {
       cudaMemsetParams mp{};
@@ -877,7 +936,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       cudaKernelNodeParams kp{};
       kp.func = const_cast<void *>(func);
       kp.gridDim = dim3((unsigned)r->R);
-      kp.blockDim = dim3((unsigned)(pl.workers + 32));
+      kp.blockDim = dim3((unsigned)(pl.workers + 64));
       kp.sharedMemBytes = (unsigned)pl.smem;
       kp.kernelParams = kargs;
       kp.extra = nullptr;

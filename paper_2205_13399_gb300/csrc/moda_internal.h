@@ -12,8 +12,8 @@
 namespace moda {
 
 constexpr int kMaxN = 128;          // n <= 128: a bit index fits (i << 8) | u
-constexpr int kMaxThreads = 1024;   // threads of a block, control warp included
-constexpr int kMaxWorkers = kMaxThreads - 32;
+constexpr int kMaxThreads = 1024;   // threads of a block, control warps included
+constexpr int kMaxWorkers = kMaxThreads - 64;
 constexpr int kTableSize = 65536;   // -ln(u) table, u quantised to 2^-16
 constexpr int kMaxLookahead = 3;    // field-cache prefetch distance
 constexpr int kStats = 8;           // counters per replica (see moda.h)
@@ -61,6 +61,11 @@ struct AnnealArgs {
   int32_t normalize;        // Sec. 4.2 normalisation in the acceptance test
   double s1, s2;            // its per-objective scales (1 when off)
   double tmin, tmax;        // -ln(u) at the largest and smallest u
+  int32_t snap_every;       // > 0: archive snapshot after every such iteration
+  int32_t nsnap;            // I_max / snap_every
+  int32_t *snap_count;      // [R][nsnap]
+  int64_t *snap_E;          // [R][nsnap][s][2]
+  uint32_t *snap_bits;      // [R][nsnap][s][W]
   const double *sch_delta;  // [nsched] delta_t, t = 1..nsched
   const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
   const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
@@ -96,7 +101,7 @@ struct Placement {
 // Byte offsets of the shared-memory carve-up of one annealing block with
 // `workers` bit-owning threads (plus one control warp).
 struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, init, mbar, dE, pf,
+  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, stat, init, mbar, dE, pf,
       pf_slot, pfE, pfW, archE, archB, total;
 };
 
@@ -118,6 +123,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);
   L.jr = o;    o = align_up(o + 8 * 32, 16);                 // 8 entries
+  L.stat = o;  o = align_up(o + 8 * 4, 16);                  // counters
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
   L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits, 16);
@@ -156,10 +162,15 @@ inline double norm_scale(int64_t max_coef) {
   return max_coef > 0 ? 8388608.0 / (double)max_coef : 1.0;
 }
 
+// Normalisation or snapshots: the kernel variant that carries them.
+inline bool uses_extensions(const AnnealArgs &a) {
+  return a.normalize != 0 || a.snap_every > 0;
+}
+
 // Bits per thread the kernel is instantiated for.
 bool supported_rounds(int b);
 
-// Launch one block of `workers` + 32 threads per replica on `stream`.
+// Launch one block of `workers` + 64 threads per replica on `stream`.
 cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
                           int rounds, bool narrow, size_t smem_bytes,
                           cudaStream_t stream);

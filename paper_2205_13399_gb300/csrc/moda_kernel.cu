@@ -148,6 +148,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
+// The two control warps alone (named barrier 1, 64 threads).
+__device__ __forceinline__ void bar_sync_pair() {
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+}
+
 // ---- warp-level mask scans ----------------------------------------------
 
 // Over `items` ballot masks in (round, warp) order: each lane sums a
@@ -277,9 +282,10 @@ struct JumpRec {
 
 // NARROW: Delta E and the acceptance penalty in int32 (the host checked
 // |Delta E_1| + |Delta E_2| < 2^31 for every state); otherwise int64.
-// NORM: QUBO normalisation (Sec. 4.2), objective k's Delta E scaled by s_k
-// inside the acceptance test, in IEEE double.
-template <int B, bool NARROW, bool NORM>
+// EXT: the optional extensions -- QUBO normalisation (Sec. 4.2: objective
+// k's Delta E scaled by s_k inside the acceptance test, in IEEE double) and
+// archive snapshots -- compiled in; without them the loop carries neither.
+template <int B, bool NARROW, bool EXT>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
@@ -287,10 +293,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = A.n, m = A.m, W = A.W, s = A.s;
   const int T = blockDim.x, tid = threadIdx.x;
-  const int Tw = T - 32;                 // worker threads
+  const int Tw = T - 64;                 // worker threads
   const int lane = tid & 31, warp = tid >> 5, NWB = Tw >> 5;
   const bool worker = tid < Tw;
-  const bool control = !worker;          // the last warp
+  const bool control = !worker;          // the last two warps:
+  const bool ctlA = warp == NWB;         // draws, schedule, jump records
+  const bool ctlB = warp == NWB + 1;     // field-cache prefetch
   const int items = B * NWB;
   const int per = (items + 31) >> 5;     // ballot words per lane in scans
   const bool fc = A.fcache != nullptr;
@@ -305,6 +313,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
                     de_smem, NARROW};
   const SmemLayout lay = smem_layout(n, m, W, s, Tw, B, P);
+  const bool NORM_ON = EXT && A.normalize != 0;
   const SlotLayout sl = slot_layout(m, NARROW);
   const dE_t w1 = (dE_t)A.w1, w2 = (dE_t)A.w2;
   int2 *sFs = reinterpret_cast<int2 *>(smem + lay.Fs);
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const double sd = A.sch_delta[sn];
     int64_t slo = A.sch_lo[sn], shi = A.sch_hi[sn];
     double lod = 0, hid = 0;
-    if (NORM) {
+    if (NORM_ON) {
       lod = __dmul_rn(sd, A.tmin);
       hid = __dmul_rn(sd, A.tmax);
       const double ql = floor(lod / (s_max * (1.0 + 1e-12)));
@@ -385,13 +394,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       sSch[it % kRing] = SchEntry{sd, slo, shi, (int32_t)(slo < 2147483647ll ? slo : 2147483647ll),
                                   (int32_t)(shi < 2147483647ll ? shi : 2147483647ll), lod, hid};
   };
-  if (control) {
-    if (lane == 0 && pf) {
-      for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
-      fence_mbar_init();
-    }
-    fill_rings(1);  // iterations 1..8; iteration t = 8i + 1 fills t+8..t+15
+  if (ctlB && lane == 0 && pf) {
+    for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
+    fence_mbar_init();
   }
+  if (ctlA) fill_rings(1);  // iterations 1..8; iteration t = 8i + 1 fills t+8..t+15
 
   // Own bit k is valid when worker && k*Tw + tid < m: own[k] packs its
   // facility i (bits 8..15) and location u (bits 0..7); D1[k], D2[k] hold
@@ -518,13 +525,47 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int64_t Eoff = 0;
   int acount = 0;
   int fail = 0;  // a bounded wait gave up (OR-reduced at every iteration)
-  uint32_t st_flip = 0, st_jump = 0, st_empty = 0, st_off = 0;
-  uint32_t st_pf = 0, st_direct = 0;
+  // Outcome counters, kept by control warp A's lane 0 in shared memory:
+  // flips, jumps, empty escapes, offset raises, prefetched jumps, direct
+  // reads.
+  uint32_t *sStat = reinterpret_cast<uint32_t *>(smem + lay.stat);
+  if (tid < 8) sStat[tid] = 0;
   int flip_streak = 0;  // consecutive flip iterations: no prefetch while hot
   // Control lane 0's copy bookkeeping: buffer b has a copy in flight when
   // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
   uint32_t pend = 0, ph = 0;
-  JumpRec jr{kNone, 0, -1, 0};
+  // buffer of iteration t (warp A) and of t + LA (warp B): t % NB kept
+  // by counting; the slot the previous flip wrote (warp B)
+  int jb = NB > 1 ? 1 : 0;
+  int pb_next = (int)((1u + (uint32_t)(LA > 0 ? LA : 0)) % (uint32_t)NB);
+  uint32_t last_t = 0;
+  int last_target = -1;
+  const uint32_t bits_lo = (uint32_t)(uintptr_t)gBits;  // low bits of the state array
+  // Archive snapshots (Fig. mdasl), taken by the control warp alone: the
+  // archive as it stood after iteration t is copied right after the
+  // barrier of iteration t + 1 (or after the loop), in that iteration's
+  // decision; it cannot change before then, and the next change (a flip's
+  // writes) comes after a barrier this warp reaches only when the copy is
+  // done.
+  const bool snap = EXT && A.snap_every > 0;
+  int32_t snap_left = A.snap_every;
+  int32_t snap_j = 0;
+  bool snap_mark = false;  // this iteration is followed by a snapshot
+  bool snap_due = false;   // the previous one was
+  auto take_snapshot = [&]() {
+    const size_t row = (size_t)rb * (size_t)A.nsnap + (size_t)snap_j;
+    int64_t *dE = A.snap_E + row * (size_t)s * 2;
+    uint32_t *dB = A.snap_bits + row * (size_t)s * W;
+    for (int e = lane; e < acount; e += 32) {
+      const longlong2 v = aE[e];
+      dE[2 * e] = v.x;
+      dE[2 * e + 1] = v.y;
+    }
+    for (int e = lane; e < acount * W; e += 32) dB[e] = aBits[e];
+    if (lane == 0) A.snap_count[row] = acount;
+    ++snap_j;
+    snap_due = false;
+  };
   // schedule entry of the current iteration, in registers
   double cur_delta, cur_lod = 0, cur_hid = 0;
   dE_t cur_lo, cur_hi;
@@ -533,7 +574,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     cur_delta = e.delta;
     cur_lo = NARROW ? (dE_t)e.lo32 : (dE_t)e.lo;
     cur_hi = NARROW ? (dE_t)e.hi32 : (dE_t)e.hi;
-    if (NORM) {
+    if (NORM_ON) {
       cur_lod = e.lod;
       cur_hid = e.hid;
     }
@@ -541,6 +582,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
   for (uint32_t t = 1; t <= I_max; ++t) {
     const int buf = (int)(t & 1u);
+    // this iteration's jump record: settled by warp A before the barrier,
+    // read by the other warps after it
+    JumpRec jr{kNone, 0, -1, 0, 0, 0, 0, 0};
     uint32_t *mask = sMask + buf * items;        // accept ballots
     uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
 
@@ -551,7 +595,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const dE_t e1 = D1[k], e2 = D2[k];
-        if (NORM) {
+        if (NORM_ON) {
           const bool in = k * Tw + tid < m;
           const dE_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
           const dE_t ai = A.accept == 0 ? u1 + u2 : (u1 < u2 ? u1 : u2);
@@ -628,51 +672,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           if (lane == 0) xm[k * NWB + warp] = xb;
         }
       }
-    } else {
-      // ---- control warp: draws, schedule and prefetch -------------------
+    } else if (ctlA) {
+      // ---- control warp A: draws, schedule, the jump record -------------
       if (t % 8u == 1u) fill_rings(t + 8);
-      if (pf && lane == 0) {
-        // Copy for the jump iteration t + LA would make.  A slot written in
-        // the previous iteration is left alone: its writes are ordered for
-        // the copy engine only by a later barrier.
-        const uint32_t tt = t + (uint32_t)LA;
-        const int b = (int)(tt % (uint32_t)NB);
-        bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= I_max;
-        int slot_p = 0;
-        if (issue) {
-          slot_p = pick(sRnd[(tt % kRing) * 4 + 1], acount);
-          if (sWr[(t - 1) & 7] == slot_p) issue = false;
-        }
-        uint32_t par = 0;
-        if (issue) {
-          if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
-            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
-            ph ^= 1u << b;
-            pend &= ~(1u << b);
-          }
-          unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
-          uint32_t eb = 0, bb = 0, boff = 0;
-          if (!A.energies_in_smem) eb = 16;
-          if (!A.bits_in_smem) {
-            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)slot_p * W);
-            boff = (uint32_t)(b0 & 15);
-            bb = (uint32_t)align_up(boff + 4 * (size_t)W, 16);
-          }
-          fence_proxy_async_shared();
-          mbar_expect_tx(&sBar[b], (uint32_t)sl.bytes + eb + bb);
-          bulk_g2s(pb, gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes, &sBar[b]);
-          if (eb) bulk_g2s(pb + lay.pfE, gE + 2 * (size_t)slot_p, 16, &sBar[b]);
-          if (bb)
-            bulk_g2s(pb + lay.pfW,
-                     reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
-                     bb, &sBar[b]);
-          par = (ph >> b) & 1u;
-          pend |= 1u << b;
-        }
-        sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
-        sWr[t & 7] = -1;  // set to the written slot by a flip below
+      if (snap && --snap_left == 0) {  // iteration t ends with a snapshot
+        snap_left = A.snap_every;
+        snap_mark = true;
       }
-      __syncwarp();
+      if (lane == 0) sWr[t & 7] = -1;  // set to the written slot by a flip below
+      if (pf && LA == 0) bar_sync_pair();  // warp B recorded its copy for t
       // The jump iteration t makes if it accepts no bit (its draw and |A|
       // are known now).  Its copy is usable if it was started LA iterations
       // ago for this slot and no iteration since rewrote that slot.
@@ -686,21 +694,67 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           for (uint32_t x = (uint32_t)rec.iter; ok && x < t; ++x)
             if (sWr[x & 7] == jr.slot) ok = false;
           if (ok) {
-            const int b = (int)(t % (uint32_t)NB);
-            const uint32_t pb = (uint32_t)(lay.pf + (size_t)b * lay.pf_slot);
-            jr.pbuf = b;
+            const uint32_t pb = (uint32_t)lay.pf + (uint32_t)jb * (uint32_t)lay.pf_slot;
+            jr.pbuf = jb;
             jr.parity = (uint32_t)rec.parity;
             jr.rf = pb;
-            jr.se = A.energies_in_smem ? (uint32_t)(lay.archE + 16 * (size_t)jr.slot)
+            jr.se = A.energies_in_smem ? (uint32_t)lay.archE + 16u * (uint32_t)jr.slot
                                        : pb + (uint32_t)lay.pfE;
-            const uintptr_t b0 = (uintptr_t)(gBits + (size_t)jr.slot * W);
-            jr.ws = A.bits_in_smem ? (uint32_t)(lay.archB + 4 * (size_t)jr.slot * W)
-                                   : pb + (uint32_t)lay.pfW + (uint32_t)(b0 & 15);
-            jr.bar = (uint32_t)(lay.mbar + 8 * (size_t)b);
+            jr.ws = A.bits_in_smem
+                        ? (uint32_t)lay.archB + 4u * (uint32_t)(jr.slot * W)
+                        : pb + (uint32_t)lay.pfW + ((bits_lo + 4u * (uint32_t)(jr.slot * W)) & 15u);
+            jr.bar = (uint32_t)lay.mbar + 8u * (uint32_t)jb;
           }
         }
       }
       if (lane == 0) sJr[t & 7] = jr;
+      if (++jb == NB) jb = 0;
+    } else {
+      // ---- control warp B: the field-cache prefetch ---------------------
+      if (pf && lane == 0) {
+        // Copy for the jump iteration t + LA would make.  A slot written in
+        // the previous iteration is left alone: its writes are ordered for
+        // the copy engine only by a later barrier.
+        const uint32_t tt = t + (uint32_t)LA;
+        const int b = pb_next;
+        bool issue = A.escape == 0 && acount > 0 && flip_streak < 3 && tt <= I_max;
+        int slot_p = 0;
+        if (issue) {
+          slot_p = pick(sRnd[(tt % kRing) * 4 + 1], acount);
+          if (last_t + 1 == t && last_target == slot_p) issue = false;
+        }
+        uint32_t par = 0;
+        if (issue) {
+          if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
+            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
+            ph ^= 1u << b;
+            pend &= ~(1u << b);
+          }
+          unsigned char *pb = smem + lay.pf + (size_t)b * lay.pf_slot;
+          uint32_t eb = 0, bb = 0, boff = 0;
+          if (!A.energies_in_smem) eb = 16;
+          if (!A.bits_in_smem) {
+            boff = (bits_lo + 4u * (uint32_t)(slot_p * W)) & 15u;
+            bb = (boff + 4u * (uint32_t)W + 15u) & ~15u;
+          }
+          fence_proxy_async_shared();
+          mbar_expect_tx(&sBar[b], (uint32_t)sl.bytes + eb + bb);
+          bulk_g2s(pb, gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes, &sBar[b]);
+          if (eb) bulk_g2s(pb + lay.pfE, gE + 2 * (size_t)slot_p, 16, &sBar[b]);
+          if (bb)
+            bulk_g2s(pb + lay.pfW,
+                     reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
+                     bb, &sBar[b]);
+          par = (ph >> b) & 1u;
+          pend |= 1u << b;
+        }
+        sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
+      }
+      if (++pb_next == NB) pb_next = 0;
+      if (pf && LA == 0) {
+        __syncwarp();
+        bar_sync_pair();  // the copy for t is recorded for warp A
+      }
     }
     if (__syncthreads_or(fail)) break;  // a bounded wait gave up (uniform)
     // schedule entry of the next iteration, loaded early
@@ -717,16 +771,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (q < per && it < items) cnt += __popc(mask[it]);
       }
       const int total = (int)__reduce_add_sync(kFull, (unsigned)cnt);
-      if (total > 0) {
-        kind = kFlip;
-        if (worker) {
+      if (worker) {
+        if (total > 0) {
+          kind = kFlip;
           const int incl = warp_incl_scan(cnt, lane);
           ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, cnt, pick(rnd[0], total));
+        } else {
+          jr = sJr[t & 7];
+          kind = jr.kind;
         }
+      } else if (ctlA) {
+        kind = total > 0 ? kFlip : jr.kind;
+        // the archive as it stood after the previous iteration
+        if (snap_due) take_snapshot();
+        snap_due = snap_mark;
+        snap_mark = false;
       } else {
-        if (worker) jr = sJr[t & 7];
-        kind = jr.kind;
-        if (control && lane == 0 && jr.pbuf >= 0) {  // the copy is consumed
+        if (total == 0) jr = sJr[t & 7];  // settled by warp A
+        kind = total > 0 ? kFlip : jr.kind;
+        if (total == 0 && lane == 0 && jr.pbuf >= 0) {  // the copy is consumed
           ph ^= 1u << jr.pbuf;
           pend &= ~(1u << jr.pbuf);
         }
@@ -839,14 +902,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
             fence_proxy_async_global();  // later bulk copies read these
           }
-        } else if (pf && lane == 0) {
-          sWr[t & 7] = target;
+        } else {
+          if (ctlA && pf && lane == 0) sWr[t & 7] = target;
+          last_target = target;
+          last_t = t;
         }
       }
       E1 = nE1;
       E2 = nE2;
       Eoff = 0;
-      if (control) ++st_flip;
+      if (ctlA && lane == 0) ++sStat[0];
     } else if (kind == kJump) {
       // Alg. 3: jump to a random archive member.
       const int slot = jr.slot, pbuf = jr.pbuf;
@@ -885,9 +950,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
           }
         } else if (pbuf >= 0) {
-          ++st_pf;
+          if (ctlA && lane == 0) ++sStat[4];
         } else {
-          ++st_direct;
+          if (ctlA && lane == 0) ++sStat[5];
         }
       } else {
         const longlong2 se = aE[slot];
@@ -896,18 +961,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         int64_t s1, s2;
         rebuild(aBits + (size_t)slot * W, s1, s2);
       }
-      if (control) ++st_jump;
+      if (ctlA && lane == 0) ++sStat[1];
     } else if (A.escape == 0) {
-      if (control) ++st_empty;
+      if (ctlA && lane == 0) ++sStat[2];
     } else {
       Eoff += A.beta;
-      if (control) ++st_off;
+      if (ctlA && lane == 0) ++sStat[3];
     }
     if (control) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
     cur_delta = nse.delta;
     cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
     cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;
-    if (NORM) {
+    if (NORM_ON) {
       cur_lod = nse.lod;
       cur_hid = nse.hid;
     }
@@ -918,8 +983,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       tr[2] = kind == kFlip ? (int64_t)ps : kind == kJump ? -1 - (int64_t)jr.slot : INT64_MIN;
     }
   }
+  __syncthreads();  // the last iteration's archive writes
+  if (ctlA && (snap_due || snap_mark)) take_snapshot();
   // No bulk copy may be in flight when the block exits.
-  if (pf && control && lane == 0) {
+  if (pf && ctlB && lane == 0) {
     for (int b = 0; b < NB; ++b)
       if ((pend >> b) & 1u)
         if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
@@ -943,14 +1010,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   if (A.bits_in_smem) {
     for (int e = tid; e < acount * W; e += T) gBits[e] = aBits[e];
   }
-  if (tid == Tw) {  // the control warp counted the outcomes
+  if (tid == Tw) {  // control warp A counted the outcomes
     int64_t *st = A.stats + (size_t)kStats * rb;
-    st[0] = st_flip;
-    st[1] = st_jump;
-    st[2] = st_empty;
-    st[3] = st_off;
-    st[4] = st_pf;
-    st[5] = st_direct;
+    for (int q = 0; q < 6; ++q) st[q] = sStat[q];
     st[6] = 0;
     st[7] = 0;
     A.arch_count[rb] = acount;
@@ -961,20 +1023,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 }
 
-template <int B, bool NARROW, bool NORM>
+template <int B, bool NARROW, bool EXT>
 cudaError_t launch_bn(const AnnealArgs &args, int replicas, int workers,
                       size_t smem, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(
-      anneal_kernel<B, NARROW, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      anneal_kernel<B, NARROW, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  anneal_kernel<B, NARROW, NORM><<<replicas, workers + 32, smem, stream>>>(args);
+  anneal_kernel<B, NARROW, EXT><<<replicas, workers + 64, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
 template <int B>
 cudaError_t launch_b(const AnnealArgs &args, int replicas, int workers, bool narrow,
                      size_t smem, cudaStream_t stream) {
-  if (args.normalize)
+  if (uses_extensions(args))
     return narrow ? launch_bn<B, true, true>(args, replicas, workers, smem, stream)
                   : launch_bn<B, false, true>(args, replicas, workers, smem, stream);
   return narrow ? launch_bn<B, true, false>(args, replicas, workers, smem, stream)

@@ -163,6 +163,8 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
     return nofail(MODA_EOVERFLOW, "local fields may exceed int32");
   if (p->normalize != 0 && p->normalize != 1)
     return nofail(MODA_EINVAL, "normalize must be 0 or 1");
+  if (p->snapshot_every != 0)
+    return nofail(MODA_EUNSUPPORTED, "archive snapshots need allocated buffers");
   int64_t e1max = 0, e2max = 0, edmax = 0;  // largest entries (normalisation)
   for (int e = 0; e < n * n; ++e) {
     e1max = std::max<int64_t>(e1max, fs1[e]);
@@ -183,7 +185,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   if (!B) return nofail(MODA_EUNSUPPORTED, "n too large for the block size");
   if (p->block_threads > 0) {
     if (p->block_threads % 32 || p->block_threads > moda::kMaxWorkers)
-      return nofail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 992");
+      return nofail(MODA_EINVAL, "block_threads must be a multiple of 32, <= 960");
     T = p->block_threads;
   } else {
     T = ((m + B - 1) / B + 31) / 32 * 32;
@@ -210,9 +212,9 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   moda::Placement place{};
   moda::SmemLayout lay{};
   bool placed = false;
-  for (int opt = 0; opt < 3 && !placed; ++opt)
-    for (int de = 1; de >= 0 && !placed; --de)
-      for (int la = cache ? 1 : 0; la >= (cache ? -1 : 0) && !placed; --la) {
+  for (int la = cache ? 1 : 0; la >= (cache ? -1 : 0) && !placed; --la)
+    for (int opt = 0; opt < 3 && !placed; ++opt)
+      for (int de = 1; de >= 0 && !placed; --de) {
         const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1, narrow};
         const moda::SmemLayout l = moda::smem_layout(n, m, W, s, T, B, pl);
         if ((int64_t)l.total <= dev_smem) {

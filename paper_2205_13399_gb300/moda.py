@@ -33,7 +33,7 @@ ABI_FUNCTIONS = [
     "moda_last_error", "moda_anneal_noalloc", "moda_anneal_batch",
     "moda_server_create", "moda_server_submit", "moda_server_poll", "moda_server_info",
     "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak", "moda_scalarize",
-    "moda_sbda_front",
+    "moda_sbda_front", "moda_read_snapshot",
 ]
 
 
@@ -67,6 +67,7 @@ class Params(ctypes.Structure):
         ("field_cache", ctypes.c_int32),
         ("prefetch", ctypes.c_int32),
         ("normalize", ctypes.c_int32),
+        ("snapshot_every", ctypes.c_int32),
     ]
 
 
@@ -119,6 +120,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.moda_read_archive.restype = st
     lib.moda_read_archive.argtypes = [P, i32, ctypes.POINTER(Point), i32,
                                       ctypes.POINTER(i32), P]
+    lib.moda_read_snapshot.restype = st
+    lib.moda_read_snapshot.argtypes = [P, i32, i32, ctypes.POINTER(Point), i32,
+                                       ctypes.POINTER(i32), P]
     lib.moda_run_elapsed_ms.restype = st
     lib.moda_run_elapsed_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.moda_destroy_run.restype = None
@@ -285,16 +289,23 @@ class Run:
         _check(_lib.moda_read_trace(self._h, int(replica), _ptr(tr)))
         return tr
 
-    def read_archive(self, replica: int = -1, cap: int | None = None, perms: bool = True):
-        """Non-dominated archive members (``moda_read_archive``) as a list of
-        dicts with E1, E2, c1, c2, g, feasible, replica, slot and perm."""
+    def read_archive(self, replica: int = -1, cap: int | None = None, perms: bool = True,
+                     snapshot: int | None = None):
+        """Non-dominated archive members (``moda_read_archive``, or
+        ``moda_read_snapshot`` of snapshot ``snapshot``) as a list of dicts
+        with E1, E2, c1, c2, g, feasible, replica, slot and perm."""
         cnt = ctypes.c_int32()
-        _check(_lib.moda_read_archive(self._h, int(replica), None, 0, ctypes.byref(cnt), None))
+        if snapshot is None:
+            def call(*a):
+                return _lib.moda_read_archive(self._h, int(replica), *a)
+        else:
+            def call(*a):
+                return _lib.moda_read_snapshot(self._h, int(snapshot), int(replica), *a)
+        _check(call(None, 0, ctypes.byref(cnt), None))
         total = cnt.value if cap is None else min(cap, cnt.value)
         pts = (Point * max(total, 1))()
         pbuf = np.zeros((max(total, 1), self.inst.n), dtype=np.uint8)
-        _check(_lib.moda_read_archive(self._h, int(replica), pts, total, ctypes.byref(cnt),
-                                      _ptr(pbuf) if perms else None))
+        _check(call(pts, total, ctypes.byref(cnt), _ptr(pbuf) if perms else None))
         out = []
         for k in range(total):
             p = pts[k]
@@ -319,13 +330,14 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
                 trace: bool = False, field_cache: str = "auto", prefetch: int = 0,
-                normalize: bool = False) -> Params:
+                normalize: bool = False, snapshot_every: int = 0) -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
-                  int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)))
+                  int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)),
+                  int(snapshot_every))
 
 
 def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,

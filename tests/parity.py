@@ -30,12 +30,12 @@ def gpu_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explo
 
 def oracle_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explore",
                escape="archive", delta0=1e9, deltaf=1e4, xi=1e-3, beta=None, archive_size=0,
-               trace=False, w=None, threads=None, normalize=False):
+               trace=False, w=None, threads=None, normalize=False, snapshot_every=0):
     oi = oracle.Instance(inst_np.F1, inst_np.F2, inst_np.D, w=w)
     out = oracle.run(oi, I_max=I_max, replicas=replicas, seed=seed, accept=accept,
                      archive=archive, escape=escape, delta0=delta0, deltaf=deltaf, xi=xi,
                      beta=beta, archive_size=archive_size, trace=trace, threads=threads,
-                     normalize=normalize)
+                     normalize=normalize, snapshot_every=snapshot_every)
     return oi, out
 
 

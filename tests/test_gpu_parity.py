@@ -5,6 +5,7 @@ event) record of every iteration."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2205_13399_gb300 import inputs
 from parity import compare, gpu_run, oracle_run
 
@@ -190,3 +191,34 @@ def test_normalised_wide_and_schedule_tail():
     _, _, res, tr = gpu_run(inst, trace=True, normalize=True, **kw)
     _, orc = oracle_run(inst, trace=True, normalize=True, **kw)
     compare(res, range(2), orc, inst.n * inst.n, gpu_trace=tr)
+
+
+@pytest.mark.parametrize("n,bt,esc", [(6, 0, "archive"), (13, 64, "archive"), (20, 0, "offset")])
+def test_archive_snapshots_match_oracle(n, bt, esc):
+    """Archive snapshots every K iterations (Fig. mdasl's hypervolume
+    trace) equal the oracle's: sizes, energies and states."""
+    from paper_2205_13399_gb300 import moda
+    inst = inputs.uniform_instance(n, index=60 + n, workload="P8")
+    K = 250
+    kw = dict(replicas=3, I_max=2000, seed=9 + n, escape=esc, beta=600, **FAST)
+    g = moda.Instance(inst.F1, inst.F2, inst.D)
+    run = moda.anneal(g, block_threads=bt, snapshot_every=K, **kw).wait()
+    _, orc = oracle_run(inst, snapshot_every=K, **kw)
+    snap = orc["snapshots"]
+    m = n * n
+    for j in range(2000 // K):
+        for r in range(3):
+            pts = run.read_archive(replica=r, snapshot=j)
+            c = int(snap["count"][r, j])
+            E = snap["E"][r, j, :c]
+            # the GPU front of the snapshot equals the non-dominated subset
+            # of the oracle's snapshot archive (lowest slot among equals)
+            keep = oracle.nondominated([tuple(e) for e in E])
+            want = sorted(((int(E[k, 0]), int(E[k, 1]), k) for k in keep))
+            got = [(p["E1"], p["E2"], p["slot"]) for p in pts]
+            assert got == want, (j, r)
+            for p in pts:
+                x = snap["bits"][r, j, p["slot"]]
+                assert p["g"] == oracle.Instance(inst.F1, inst.F2, inst.D).constraint(x)
+    last = run.read_archive(snapshot=2000 // K - 1)
+    assert last == run.read_archive()

@@ -281,3 +281,26 @@ def test_selection_uniform():
     exp = R / m
     chi2 = float(((counts - exp) ** 2 / exp).sum())
     assert chi2 < (m - 1) + 6 * math.sqrt(2 * (m - 1))
+
+
+# --------------------------------------------------------------------------
+# archive snapshots (the per-iteration archive behind Fig. mdasl)
+# --------------------------------------------------------------------------
+
+def test_snapshots_are_prefix_archives():
+    """Snapshot j of a run is the final archive of the same run stopped after
+    (j + 1) K iterations (every iteration depends only on earlier ones)."""
+    qi = inputs.uniform_instance(6, index=3, workload="P8")
+    inst = oracle.Instance(qi.F1, qi.F2, qi.D)
+    kw = dict(replicas=3, seed=4, delta0=2e6, deltaf=3e3, xi=0.02)
+    K = 400
+    full = oracle.run(inst, I_max=2000, snapshot_every=K, **kw)
+    snap = full["snapshots"]
+    assert snap["count"].shape == (3, 5)
+    for j in (0, 2, 4):
+        part = oracle.run(inst, I_max=(j + 1) * K, **kw)
+        assert np.array_equal(snap["count"][:, j], part["count"])
+        for r in range(3):
+            c = int(part["count"][r])
+            assert np.array_equal(snap["E"][r, j, :c], part["E"][r, :c])
+            assert np.array_equal(snap["bits"][r, j, :c], part["bits"][r, :c])

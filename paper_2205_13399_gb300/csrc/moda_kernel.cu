@@ -524,12 +524,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
   int64_t Eoff = 0;
   int acount = 0;
-  int fail = 0;  // a bounded wait gave up (OR-reduced at every iteration)
   // Outcome counters, kept by control warp A's lane 0 in shared memory:
   // flips, jumps, empty escapes, offset raises, prefetched jumps, direct
   // reads.
   uint32_t *sStat = reinterpret_cast<uint32_t *>(smem + lay.stat);
   if (tid < 8) sStat[tid] = 0;
+  // A bounded wait gave up: the thread sets `fail` and the shared flag
+  // sStat[7]; the iteration barrier counts it like an accepted bit, and a
+  // nonzero count with the flag set ends the loop in every thread.
+  int fail = 0;
+  auto set_fail = [&]() {
+    fail = 1;
+    sStat[7] = 1;
+  };
   int flip_streak = 0;  // consecutive flip iterations: no prefetch while hot
   // Control lane 0's copy bookkeeping: buffer b has a copy in flight when
   // pend >> b & 1; its mbarrier's next phase parity is ph >> b & 1.
@@ -588,6 +595,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     uint32_t *mask = sMask + buf * items;        // accept ballots
     uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
 
+    bool acc_any = false;  // this thread accepted a bit
     if (worker) {
       // ---- workers: the parallel trial of their bits --------------------
       const double delta = cur_delta;
@@ -635,6 +643,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
             if (lane == 0) xm[k * NWB + warp] = xb;
           }
+          acc_any |= acc;
           continue;
         }
         dE_t a1, a2;
@@ -671,6 +680,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
           if (lane == 0) xm[k * NWB + warp] = xb;
         }
+        acc_any |= acc;
       }
     } else if (ctlA) {
       // ---- control warp A: draws, schedule, the jump record -------------
@@ -726,7 +736,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         uint32_t par = 0;
         if (issue) {
           if ((pend >> b) & 1u) {  // retire the unused copy in this buffer
-            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) fail = 1;
+            if (!mbar_wait(&sBar[b], (ph >> b) & 1u)) set_fail();
             ph ^= 1u << b;
             pend &= ~(1u << b);
           }
@@ -756,7 +766,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         bar_sync_pair();  // the copy for t is recorded for warp A
       }
     }
-    if (__syncthreads_or(fail)) break;  // a bounded wait gave up (uniform)
+    // The barrier counts the threads that accepted a bit (or gave up a
+    // wait): 0 means no bit was accepted, the common case once the
+    // schedule has cooled, settled without reading the ballots.
+    const int nacc = __syncthreads_count(acc_any || fail);
+    if (nacc > 0 && sStat[7]) break;  // a bounded wait gave up (uniform)
     // schedule entry of the next iteration, loaded early
     const SchEntry nse = sSch[(t + 1) % kRing];
 
@@ -764,16 +778,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const uint32_t *rnd = sRnd + (t % kRing) * 4;
     int kind, ps = 0;
     {
-      int cnt = 0;
-#pragma unroll
-      for (int q = 0; q < B; ++q) {  // items <= B * 31, so per <= B
-        const int it = lane * per + q;
-        if (q < per && it < items) cnt += __popc(mask[it]);
-      }
-      const int total = (int)__reduce_add_sync(kFull, (unsigned)cnt);
       if (worker) {
-        if (total > 0) {
+        if (nacc > 0) {
           kind = kFlip;
+          int cnt = 0;
+#pragma unroll
+          for (int q = 0; q < B; ++q) {  // items <= B * 31, so per <= B
+            const int it = lane * per + q;
+            if (q < per && it < items) cnt += __popc(mask[it]);
+          }
+          // one bit per thread: the count is the number of accepted bits
+          const int total = B == 1 ? nacc : (int)__reduce_add_sync(kFull, (unsigned)cnt);
           const int incl = warp_incl_scan(cnt, lane);
           ps = warp_mask_select(mask, items, NWB, Tw, lane, incl, cnt, pick(rnd[0], total));
         } else {
@@ -781,15 +796,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           kind = jr.kind;
         }
       } else if (ctlA) {
-        kind = total > 0 ? kFlip : jr.kind;
+        kind = nacc > 0 ? kFlip : jr.kind;
         // the archive as it stood after the previous iteration
         if (snap_due) take_snapshot();
         snap_due = snap_mark;
         snap_mark = false;
       } else {
-        if (total == 0) jr = sJr[t & 7];  // settled by warp A
-        kind = total > 0 ? kFlip : jr.kind;
-        if (total == 0 && lane == 0 && jr.pbuf >= 0) {  // the copy is consumed
+        if (nacc == 0) jr = sJr[t & 7];  // settled by warp A
+        kind = nacc > 0 ? kFlip : jr.kind;
+        if (nacc == 0 && lane == 0 && jr.pbuf >= 0) {  // the copy is consumed
           ph ^= 1u << jr.pbuf;
           pend &= ~(1u << jr.pbuf);
         }
@@ -918,7 +933,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       if (fc) {
         if (worker) {
           if (pbuf >= 0) {  // from the prefetch buffer (shared memory)
-            if (!mbar_wait(reinterpret_cast<uint64_t *>(smem + jr.bar), jr.parity)) fail = 1;
+            if (!mbar_wait(reinterpret_cast<uint64_t *>(smem + jr.bar), jr.parity)) set_fail();
             const dE2_t *rf = reinterpret_cast<const dE2_t *>(smem + jr.rf);
             const uint32_t *ws = reinterpret_cast<const uint32_t *>(smem + jr.ws);
             const longlong2 se = *reinterpret_cast<const longlong2 *>(smem + jr.se);

@@ -115,7 +115,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   const size_t bits = (size_t)rounds * workers;
   L.Fs = o;    o = align_up(o + 8 * nn, 16);                 // int2 pairs
   L.D = o;     o = align_up(o + 4 * nn, 16);
-  L.mask = o;  o = align_up(o + 4 * 4 * items, 16);  // accept, state x 2
+  L.mask = o;  o = align_up(o + 4 * 2 * items, 16);  // accept ballots x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
   L.rnd = o;   o = align_up(o + 32 * 4 * 4, 16);             // 32 iterations
   L.sch = o;   o = align_up(o + 32 * 48, 16);                // 32 entries
@@ -126,7 +126,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.stat = o;  o = align_up(o + 8 * 4, 16);                  // counters
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
-  L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits, 16);
+  L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits + bits, 16);  // + state bytes
   // Prefetch buffers (lookahead + 2: the one being filled, the one of the
   // current iteration and the one a lagging warp may still read): one
   // field-cache record, then the member's energies and the 16-byte-aligned

@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   uint32_t *sInit = reinterpret_cast<uint32_t *>(smem + lay.init);
   uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + lay.mbar);
   dE2_t *sDE = reinterpret_cast<dE2_t *>(smem + lay.dE);  // [bits]
+  // state bit of each accepted bit, published beside its Delta E
+  uint8_t *sXb = reinterpret_cast<uint8_t *>(smem + lay.dE) + sizeof(dE2_t) * (size_t)B * Tw;
   // Prefetch bookkeeping of the control warp (after initialisation; shares
   // the reduction space): sPf[target iteration % 8], and sWr[iteration % 8]
   // = the archive slot that iteration wrote (-1 = none).
@@ -593,7 +595,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // read by the other warps after it
     JumpRec jr{kNone, 0, -1, 0, 0, 0, 0, 0};
     uint32_t *mask = sMask + buf * items;        // accept ballots
-    uint32_t *xm = sMask + (2 + buf) * items;    // state ballots
 
     bool acc_any = false;  // this thread accepted a bit
     if (worker) {
@@ -636,13 +637,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             v.x = e1;
             v.y = e2;
             sDE[k * Tw + tid] = v;
+          sXb[k * Tw + tid] = (uint8_t)((xmask >> k) & 1u);
+            sXb[k * Tw + tid] = (uint8_t)((xmask >> k) & 1u);
           }
           const uint32_t bal = __ballot_sync(kFull, acc);
           if (lane == 0) mask[k * NWB + warp] = bal;
-          if (de_smem) {
-            const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
-            if (lane == 0) xm[k * NWB + warp] = xb;
-          }
           acc_any |= acc;
           continue;
         }
@@ -673,13 +672,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           v.x = e1;
           v.y = e2;
           sDE[k * Tw + tid] = v;
+          sXb[k * Tw + tid] = (uint8_t)((xmask >> k) & 1u);
         }
         const uint32_t bal = __ballot_sync(kFull, acc);
         if (lane == 0) mask[k * NWB + warp] = bal;
-        if (de_smem) {
-          const uint32_t xb = __ballot_sync(kFull, (xmask >> k) & 1u);
-          if (lane == 0) xm[k * NWB + warp] = xb;
-        }
         acc_any |= acc;
       }
     } else if (ctlA) {
@@ -820,7 +816,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         dE1 = (int64_t)v.x;
         dE2 = (int64_t)v.y;
         // ballot word of bit ps: (round, warp) = ps / 32 because Tw % 32 == 0
-        sg = 1 - 2 * (int)((xm[ps >> 5] >> (ps & 31)) & 1u);
+        sg = 1 - 2 * (int)sXb[ps];
       } else {
         const int kk = ps / Tw;
         if (ps - kk * Tw == tid) {  // the owner publishes Delta E and its sign
@@ -983,7 +979,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       Eoff += A.beta;
       if (ctlA && lane == 0) ++sStat[3];
     }
-    if (control) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
+    if (ctlB) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
     cur_delta = nse.delta;
     cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
     cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;

@@ -147,12 +147,14 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   return L;
 }
 
-// True when |Delta E_1| + |Delta E_2| stays below 2^31 for every state:
-// |Delta E_k| <= B_k + w_k (2n + 1), B_k the bound of the fields.
+// True when every |Delta E_k| stays below 2^31 for every state:
+// |Delta E_k| <= B_k + w_k (2n + 1), B_k the bound of the fields.  The
+// kernel then keeps Delta E in int32 and the acceptance penalty (a sum of
+// two values in [0, 2^31)) in uint32.
 inline bool narrow_ok(int n, int64_t b1, int64_t b2, int64_t w1, int64_t w2) {
   const long double e1 = (long double)b1 + (long double)w1 * (2 * n + 1);
   const long double e2 = (long double)b2 + (long double)w2 * (2 * n + 1);
-  return e1 + e2 < 2147483647.0L;
+  return e1 < 2147483647.0L && e2 < 2147483647.0L;
 }
 
 // Sec. 4.2 normalisation: objective k's scale 2^23 / (largest coefficient

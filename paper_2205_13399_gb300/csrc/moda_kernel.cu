@@ -262,7 +262,7 @@ struct PfRec {
 struct SchEntry {
   double delta;
   int64_t lo, hi;
-  int32_t lo32, hi32;
+  uint32_t lo32, hi32;  // clamped to 2^32 - 1
   // normalised acceptance: fl(delta T_min) and fl(delta T_max); lo and hi
   // then bound the integer penalty (see fill_rings)
   double lod, hid;
@@ -280,8 +280,9 @@ struct JumpRec {
   uint32_t rf, se, ws, bar;
 };
 
-// NARROW: Delta E and the acceptance penalty in int32 (the host checked
-// |Delta E_1| + |Delta E_2| < 2^31 for every state); otherwise int64.
+// NARROW: Delta E in int32 and the acceptance penalty in uint32 (the host
+// checked |Delta E_k| < 2^31 for every state and objective); otherwise
+// int64.
 // EXT: the optional extensions -- QUBO normalisation (Sec. 4.2: objective
 // k's Delta E scaled by s_k inside the acceptance test, in IEEE double) and
 // archive snapshots -- compiled in; without them the loop carries neither.
@@ -290,6 +291,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
   using dE2_t = typename std::conditional<NARROW, int2, longlong2>::type;
+  // acceptance penalty: a sum of two non-negative Delta E, so uint32 in
+  // the narrow variant (each |Delta E_k| < 2^31)
+  using pen_t = typename std::conditional<NARROW, uint32_t, int64_t>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = A.n, m = A.m, W = A.W, s = A.s;
   const int T = blockDim.x, tid = threadIdx.x;
@@ -393,8 +397,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     philox10(c, k0, k1);
     if (lane < 24) sRnd[(q % kRing) * 4 + tag] = c[0];
     if (lane < 8)
-      sSch[it % kRing] = SchEntry{sd, slo, shi, (int32_t)(slo < 2147483647ll ? slo : 2147483647ll),
-                                  (int32_t)(shi < 2147483647ll ? shi : 2147483647ll), lod, hid};
+      sSch[it % kRing] = SchEntry{sd, slo, shi,
+                                  (uint32_t)(slo < 4294967295ll ? slo : 4294967295ll),
+                                  (uint32_t)(shi < 4294967295ll ? shi : 4294967295ll), lod, hid};
   };
   if (ctlB && lane == 0 && pf) {
     for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
@@ -577,12 +582,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   };
   // schedule entry of the current iteration, in registers
   double cur_delta, cur_lod = 0, cur_hid = 0;
-  dE_t cur_lo, cur_hi;
+  pen_t cur_lo, cur_hi;
   {
     const SchEntry e = sSch[1];
     cur_delta = e.delta;
-    cur_lo = NARROW ? (dE_t)e.lo32 : (dE_t)e.lo;
-    cur_hi = NARROW ? (dE_t)e.hi32 : (dE_t)e.hi;
+    cur_lo = NARROW ? (pen_t)e.lo32 : (pen_t)e.lo;
+    cur_hi = NARROW ? (pen_t)e.hi32 : (pen_t)e.hi;
     if (NORM_ON) {
       cur_lod = e.lod;
       cur_hid = e.hid;
@@ -600,14 +605,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (worker) {
       // ---- workers: the parallel trial of their bits --------------------
       const double delta = cur_delta;
-      const dE_t lo = cur_lo, hi = cur_hi;
+      const pen_t lo = cur_lo, hi = cur_hi;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const dE_t e1 = D1[k], e2 = D2[k];
         if (NORM_ON) {
           const bool in = k * Tw + tid < m;
           const dE_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
-          const dE_t ai = A.accept == 0 ? u1 + u2 : (u1 < u2 ? u1 : u2);
+          const pen_t ai = A.accept == 0 ? (pen_t)u1 + (pen_t)u2 : (pen_t)(u1 < u2 ? u1 : u2);
           bool acc = false, need = in;  // offset escape: every bit exactly
           if (A.escape == 0) {
             acc = in && ai <= lo;
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           a1 = e1 > 0 ? e1 : 0;
           a2 = e2 > 0 ? e2 : 0;
         }
-        const dE_t a = A.accept == 0 ? a1 + a2 : (a1 < a2 ? a1 : a2);
+        const pen_t a = A.accept == 0 ? (pen_t)a1 + (pen_t)a2 : (pen_t)(a1 < a2 ? a1 : a2);
         const bool in = k * Tw + tid < m;
         bool acc = in && a <= lo;
         // a in (lo, hi]: the draw decides (warp-uniform branch; cold
@@ -981,8 +986,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     if (ctlB) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
     cur_delta = nse.delta;
-    cur_lo = NARROW ? (dE_t)nse.lo32 : (dE_t)nse.lo;
-    cur_hi = NARROW ? (dE_t)nse.hi32 : (dE_t)nse.hi;
+    cur_lo = NARROW ? (pen_t)nse.lo32 : (pen_t)nse.lo;
+    cur_hi = NARROW ? (pen_t)nse.hi32 : (pen_t)nse.hi;
     if (NORM_ON) {
       cur_lod = nse.lod;
       cur_hid = nse.hid;

@@ -222,3 +222,33 @@ def test_archive_snapshots_match_oracle(n, bt, esc):
                 assert p["g"] == oracle.Instance(inst.F1, inst.F2, inst.D).constraint(x)
     last = run.read_archive(snapshot=2000 // K - 1)
     assert last == run.read_archive()
+
+
+@pytest.mark.parametrize("n,fv,dv", [(3, 4000, 8000), (4, 2500, 4500)])
+@pytest.mark.parametrize("acc", ["strict", "lenient"])
+def test_narrow_penalty_sum_above_2_31(n, fv, dv, acc):
+    """Each |Delta E_k| bound is below 2^31 but their sum is not: the int32
+    Delta E variant runs, with the acceptance penalty in uint32; early
+    iterations (delta near 10^9) test penalties around 2^31 against the
+    draw, so a wrapped sum would change the trajectory."""
+    rng = np.random.default_rng(n)
+    F1 = rng.integers(fv // 2, fv, (n, n))
+    F2 = rng.integers(fv // 2, fv, (n, n))
+    for F in (F1, F2):
+        np.fill_diagonal(F, 0)
+    D = np.triu(rng.integers(dv // 2, dv, (n, n)), 1)
+    D = D + D.T
+    Fs1, Fs2 = (F1 + F1.T).astype(np.int64), (F2 + F2.T).astype(np.int64)
+    dm = int(D.sum(1).max())
+    e = [int(F.sum(1).max()) * dm * (2 * n + 2) for F in (Fs1, Fs2)]
+    assert max(e) < 2 ** 31 <= sum(e)
+
+    class Inst:
+        pass
+    inst = Inst()
+    inst.F1, inst.F2, inst.D, inst.n = F1.astype(np.int16), F2.astype(np.int16), \
+        D.astype(np.int16), n
+    kw = dict(replicas=16, I_max=3000, seed=13, accept=acc)
+    _, _, res, tr = gpu_run(inst, trace=True, **kw)
+    _, orc = oracle_run(inst, trace=True, **kw)
+    compare(res, range(16), orc, n * n, gpu_trace=tr)

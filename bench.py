@@ -41,6 +41,30 @@ OPS_PER_BIT_TRIAL = 20
 INT_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 
+# DRAM bytes (read + write) of one annealing launch, from one ncu capture
+# of the default workload (profiles/anneal_kernel_P25_dram.md), valid only
+# for the kernel sources it was taken on (their SHA-256 below).
+KERNEL_TRAFFIC = {"workload": "P25", "sha256": "a6516a9bcdb373b40e5e61090090e2badfd5692fd70880e0650dedefd27915be",
+                  "bytes": 11116455680 + 894336000}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("moda_kernel.cu", "moda_internal.h"):
+        with open(os.path.join(ROOT, "paper_2205_13399_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(workload: str, I_max: int, default_I_max: int):
+    """DRAM bytes per launch when the stored capture matches this kernel and
+    workload, else None."""
+    if (KERNEL_TRAFFIC["bytes"] is None or workload != KERNEL_TRAFFIC["workload"]
+            or I_max != default_I_max or kernel_sources_sha256() != KERNEL_TRAFFIC["sha256"]):
+        return None
+    return KERNEL_TRAFFIC["bytes"]
+
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
@@ -49,7 +73,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["moda", "reference"], default="moda")
     ap.add_argument("--workload", default="P25",
-                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE", "SBDA", "HVTRACE"])
+                    choices=["P8", "P25", "P50", "P75", "BATCH", "SERVE", "SBDA", "HVTRACE",
+                             "QUBO"])
     ap.add_argument("--instances", type=int, default=512, help="BATCH: instances")
     ap.add_argument("--seq-instances", type=int, default=24,
                     help="BATCH / SERVE: requests also run one at a time for comparison")
@@ -558,6 +583,56 @@ def run_hvtrace(args):
     return 0
 
 
+def run_qubo(args):
+    """Explicit QUBOs with K = 3 objectives: dense random m = 1024 matrices,
+    128 replicas, I_max = 10^5 (the stored-P generalisation of the path)."""
+    import torch
+    from paper_2205_13399_gb300 import inputs, moda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K, m, R = 3, 1024, 128
+    I_max = args.I_max if args.I_max is not None else 100_000
+    Q = inputs.random_qubo(K, m)
+    q = moda.Qubo(Q)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kw = dict(replicas=R, I_max=I_max, seed=0)
+    for _ in range(args.warmup):
+        q.anneal(stream=stream, **dict(kw, I_max=min(I_max, 2000))).wait().close()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        r = q.anneal(stream=stream, **kw).wait()
+        ms.append(r.elapsed_ms())
+        r.close()
+    clk = clocks.stop()
+    value = R * I_max * args.steps / (sum(ms) / 1e3)
+    t0 = time.perf_counter()
+    q2 = moda.Qubo(Q)
+    r = q2.anneal(stream=stream, **kw).wait()
+    res = r.read()
+    e2e_s = time.perf_counter() - t0
+    r.close()
+    line = {
+        "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"QUBO: K={K} dense random QUBOs, m={m} bits, {R} replicas, "
+                               f"I_max={I_max}", "K": K, "bits": m, "replicas": R,
+                   "I_max": I_max, "l2": "flushed between timed steps (512 MiB write)"},
+        "bit_trials_per_s": value * m,
+        "e2e": {"value": R * I_max / e2e_s, "unit": "replica-steps/s",
+                "h2d_bytes_per_step": int(Q.nbytes),
+                "d2h_bytes_per_step": int(sum(v.nbytes for v in res.values())), "steps": 1},
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -565,12 +640,12 @@ def main(argv=None):
     world, rank, local = dist_env()
     import numpy as np
     import torch
-    if args.workload in ("BATCH", "SERVE", "SBDA", "HVTRACE"):
+    if args.workload in ("BATCH", "SERVE", "SBDA", "HVTRACE", "QUBO"):
         if world > 1:
-            raise SystemExit("BATCH, SERVE, SBDA and HVTRACE run on one GPU")
+            raise SystemExit("BATCH, SERVE, SBDA, HVTRACE and QUBO run on one GPU")
         torch.cuda.set_device(local)
         return {"BATCH": run_batch, "SERVE": run_serve, "SBDA": run_sbda,
-                "HVTRACE": run_hvtrace}[args.workload](args)
+                "HVTRACE": run_hvtrace, "QUBO": run_qubo}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -646,6 +721,10 @@ def main(argv=None):
     roofline = roofline_line(ops_per_launch, statistics.mean(kernel_ms) / 1e3,
                              props.multi_processor_count, sm_max_mhz,
                              f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial")
+    roofline["traffic"] = kernel_traffic(
+        args.workload, I_max, inputs.WORKLOAD_RUN[args.workload]["I_max"])
+    if roofline["traffic"] is not None:
+        roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read + write)"
 
     line = {
         "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s",

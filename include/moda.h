@@ -63,6 +63,8 @@ typedef enum {
 typedef struct moda_instance_s *moda_instance;
 typedef struct moda_run_s *moda_run;
 typedef struct moda_server_s *moda_server;
+typedef struct moda_qubo_s *moda_qubo;
+typedef struct moda_qrun_s *moda_qrun;
 
 /* Sec. 3.3: strict = product of the per-objective probabilities
  * (Eq. pacceptms); lenient = their maximum (Eq. pacceptml). */
@@ -246,6 +248,38 @@ moda_status moda_scalarize(moda_instance src, int32_t gamma_num, int32_t gamma_d
                            moda_instance *out);
 moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t count,
                             moda_point *pts, int32_t cap, int32_t *total, uint8_t *perms);
+
+/* ---- Explicit QUBOs with K objectives ---------------------------------
+ *
+ * Alg. 3 on objectives given as explicit QUBO matrices instead of the
+ * bi-objective QAP: E_k(x) = x^T Q_k x with Q_k upper triangular (Sec. 2.2's
+ * convention; entries below the diagonal are ignored), Delta E from the
+ * stored P_k = Q_k + Q_k^T with P_pp = Q_pp (Eq. cale), and K-dimensional
+ * dominance in the archive updates (Alg. 4 / Alg. 5).  Any constraint
+ * penalty is part of the caller's Q_k.  Draws, acceptance (strict: the sum
+ * of max(0, Delta E_k - E_offset) over the objectives; lenient: their
+ * minimum), selection, archive and escape follow moda_anneal.
+ *
+ * moda_qubo_create copies K (1..3) matrices of m x m int32 (m <= 4096,
+ * row-major, [K][m][m]) to the current device; MODA_EOVERFLOW when an
+ * entry of Q + Q^T leaves int32.  moda_qubo_anneal enqueues params->replicas
+ * runs on cuda_stream (params.normalize and params.snapshot_every must be
+ * 0; params.field_cache == 2 turns the archive Delta E records off, jumps
+ * then rebuild Delta E).  moda_qrun_read copies, for all replicas, any
+ * non-NULL of: archive sizes [R], energies [R][s][K], states [R][s][W]
+ * (W = ceil(m / 32), bit p in word p / 32), final states [R][W] and
+ * energies [R][K], counters [R][4] (flips, jumps, empty escapes, offset
+ * raises) and the trace [R][I_max][K + 1] (energies, event as in
+ * moda_read_trace) of a run made with params.trace. */
+moda_status moda_qubo_create(int32_t K, int32_t m, const int32_t *Q, moda_qubo *out);
+void moda_qubo_destroy(moda_qubo q);
+moda_status moda_qubo_anneal(moda_qubo q, const moda_params *params, void *cuda_stream,
+                             moda_qrun *out);
+moda_status moda_qrun_wait(moda_qrun run);
+moda_status moda_qrun_read(moda_qrun run, int32_t *count, int64_t *E, uint32_t *bits,
+                           uint32_t *x, int64_t *E_final, int64_t *stats, int64_t *trace);
+moda_status moda_qrun_elapsed_ms(moda_qrun run, float *ms);
+void moda_qrun_destroy(moda_qrun run);
 
 /* ---- Serving ---------------------------------------------------------
  *

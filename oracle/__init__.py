@@ -135,6 +135,14 @@ def _load():
         lib.oracle_da_run_many.restype = ctypes.c_int
         lib.oracle_da_run_many.argtypes = [P, ctypes.POINTER(_DAParams), i64, P, ctypes.c_int,
                                            P, P, P, P, P]
+        lib.oracle_kqubo_new.restype = P
+        lib.oracle_kqubo_new.argtypes = [ctypes.c_int, i64, P]
+        lib.oracle_kqubo_free.argtypes = [P]
+        lib.oracle_kqubo_energy.restype = i64
+        lib.oracle_kqubo_energy.argtypes = [P, ctypes.c_int, P]
+        lib.oracle_kqubo_run.restype = ctypes.c_int
+        lib.oracle_kqubo_run.argtypes = [P, ctypes.POINTER(_Params), ctypes.c_uint32,
+                                         P, P, P, P, P, P, P]
         _lib = lib
         return lib
 
@@ -392,3 +400,71 @@ def sbda(inst: Instance, *, gden: int = 10, gammas=None, **kw) -> dict:
     keep = nondominated([(c[0], c[1]) for c in cand])
     front = sorted((cand[i] for i in keep), key=lambda c: (c[0], c[1]))
     return {"runs": runs, "front": front}
+
+
+class KQubo:
+    """K objectives given as explicit m x m QUBOs (upper triangle used),
+    E_k(x) = x^T Q_k x."""
+
+    def __init__(self, Q):
+        Q = np.ascontiguousarray(np.asarray(Q, dtype=np.int64))
+        if Q.ndim != 3 or Q.shape[1] != Q.shape[2]:
+            raise ValueError("Q must be K x m x m")
+        self.K, self.m = int(Q.shape[0]), int(Q.shape[1])
+        self._Q = Q
+        self._h = _load().oracle_kqubo_new(self.K, self.m, _ptr(Q))
+        if not self._h:
+            raise MemoryError("oracle_kqubo_new failed")
+
+    def energy(self, k: int, x) -> int:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.uint8).reshape(-1))
+        return int(_load().oracle_kqubo_energy(self._h, int(k), _ptr(x)))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().oracle_kqubo_free(self._h)
+            self._h = None
+
+
+def kqubo_run(q: KQubo, *, I_max: int, replicas, seed: int = 0, accept: str = "strict",
+              archive: str = "explore", escape: str = "archive", delta0: float = 1e9,
+              deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
+              archive_size: int = 0, check: bool = False, trace: bool = False) -> dict:
+    """Alg. 3 on K explicit QUBOs for each replica index in ``replicas`` (an
+    int r means 0..r-1).  Returns ``count`` [R], ``E`` [R, s, K], ``bits``
+    [R, s, m], ``x`` [R, m], ``E_final`` [R, K], ``stats`` [R, 4] and, when
+    asked, ``trace`` [R, I_max, K + 1] (energies, event)."""
+    lib = _load()
+    if isinstance(replicas, (int, np.integer)):
+        replicas = range(int(replicas))
+    reps = [int(r) for r in replicas]
+    R, m, K = len(reps), q.m, q.K
+    s = archive_size if archive_size > 0 else m
+    if beta is None:
+        beta = int(round(delta0 / I_max)) if I_max > 0 else 0
+    prm = _Params(int(I_max), float(delta0), float(deltaf), float(xi), int(beta), int(s),
+                  ACCEPT[accept], ARCHIVE[archive], ESCAPE[escape], int(bool(check)),
+                  int(seed) & 0xFFFFFFFFFFFFFFFF, 0, 0)
+    out = {"count": np.zeros(R, dtype=np.int64), "E": np.zeros((R, s, K), dtype=np.int64),
+           "bits": np.zeros((R, s, m), dtype=np.uint8), "x": np.zeros((R, m), dtype=np.uint8),
+           "E_final": np.zeros((R, K), dtype=np.int64), "stats": np.zeros((R, 4), dtype=np.int64)}
+    if trace:
+        out["trace"] = np.zeros((R, I_max, K + 1), dtype=np.int64)
+    for i, r in enumerate(reps):
+        cnt = np.zeros(1, dtype=np.int64)
+        E = np.ascontiguousarray(out["E"][i])
+        bits = np.ascontiguousarray(out["bits"][i])
+        x = np.zeros(m, dtype=np.uint8)
+        Ef = np.zeros(K, dtype=np.int64)
+        st = np.zeros(4, dtype=np.int64)
+        tr = np.zeros((I_max, K + 1), dtype=np.int64) if trace else None
+        rc = lib.oracle_kqubo_run(q._h, ctypes.byref(prm), r, _ptr(cnt), _ptr(E), _ptr(bits),
+                                  _ptr(x), _ptr(Ef), _ptr(st), _ptr(tr) if trace else None)
+        if rc != 0:
+            raise RuntimeError(f"oracle K-objective run failed with code {rc}")
+        out["count"][i] = cnt[0]
+        out["E"][i], out["bits"][i], out["x"][i] = E, bits, x
+        out["E_final"][i], out["stats"][i] = Ef, st
+        if trace:
+            out["trace"][i] = tr
+    return out

@@ -911,3 +911,208 @@ int oracle_da_run_many(const oracle_squbo *q, const oracle_da_params *prm, int64
   pthread_mutex_destroy(&job.lock);
   return job.rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Explicit QUBOs with K objectives (Alg. 3 on stored matrices)             */
+/* ------------------------------------------------------------------------ */
+
+/* K objectives, each an explicit upper-triangular QUBO Q_k of m bits
+ * (E_k(x) = x^T Q_k x), with P_k = Q_k + Q_k^T off the diagonal and
+ * P_pp = Q_pp (Eq. cale).  Nothing about the QAP is assumed: any penalty
+ * is part of Q_k. */
+typedef struct oracle_kqubo {
+  int K;
+  int64_t m;
+  int64_t *Q;  /* [K][m][m] */
+  int64_t *P;  /* [K][m][m] */
+} oracle_kqubo;
+
+void oracle_kqubo_free(oracle_kqubo *q) {
+  if (!q) return;
+  free(q->Q);
+  free(q->P);
+  free(q);
+}
+
+oracle_kqubo *oracle_kqubo_new(int K, int64_t m, const int64_t *Q) {
+  if (K < 1 || K > 8 || m < 1) return NULL;
+  oracle_kqubo *q = (oracle_kqubo *)calloc(1, sizeof(*q));
+  if (!q) return NULL;
+  const size_t mm = (size_t)(m * m);
+  q->K = K;
+  q->m = m;
+  q->Q = (int64_t *)malloc(sizeof(int64_t) * mm * (size_t)K);
+  q->P = (int64_t *)malloc(sizeof(int64_t) * mm * (size_t)K);
+  if (!q->Q || !q->P) {
+    oracle_kqubo_free(q);
+    return NULL;
+  }
+  for (int k = 0; k < K; ++k) {
+    const int64_t *Qk = Q + (size_t)k * mm;
+    int64_t *Uk = q->Q + (size_t)k * mm, *Pk = q->P + (size_t)k * mm;
+    for (int64_t p = 0; p < m; ++p)
+      for (int64_t r = 0; r < m; ++r) Uk[p * m + r] = r >= p ? Qk[p * m + r] : 0;
+    for (int64_t p = 0; p < m; ++p)
+      for (int64_t r = 0; r < m; ++r)
+        Pk[p * m + r] = p == r ? Uk[p * m + p] : Uk[p * m + r] + Uk[r * m + p];
+  }
+  return q;
+}
+
+int64_t oracle_kqubo_energy(const oracle_kqubo *q, int k, const uint8_t *x) {
+  return oracle_quadratic(q->m, q->Q + (size_t)k * (size_t)(q->m * q->m), x);
+}
+
+static int dominates_k(int K, const int64_t *a, const int64_t *b) {
+  int strict = 0;
+  for (int k = 0; k < K; ++k) {
+    if (a[k] > b[k]) return 0;
+    if (a[k] < b[k]) strict = 1;
+  }
+  return strict;
+}
+
+/* Alg. 3 for one replica on K objectives, with Alg. 3's Philox counters;
+ * archive energies [s][K], trace [I_max][K + 1] (energies, event).  The
+ * strict rule sums max(0, Delta E_k) over the objectives, the lenient one
+ * takes their minimum (Eqs. pacceptms / pacceptml with K factors).  Returns
+ * 0, -1 bad arguments, -2 out of memory, -3 a check failed. */
+int oracle_kqubo_run(const oracle_kqubo *q, const oracle_params *prm, uint32_t replica,
+                     int64_t *count, int64_t *arch_E, uint8_t *arch_bits, uint8_t *x_final,
+                     int64_t *E_final, int64_t *stats, int64_t *trace) {
+  const int K = q->K;
+  const int64_t m = q->m;
+  const size_t mm = (size_t)(m * m);
+  const int64_t s = prm->archive_size > 0 ? prm->archive_size : m;
+  if (prm->I_max < 0 || prm->I_max > 0xFFFFFFFFll) return -1;
+  int rc = 0;
+  uint8_t *x = (uint8_t *)calloc((size_t)m, 1);
+  int64_t *phi = (int64_t *)calloc((size_t)(K * m), sizeof(int64_t));
+  int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K * m));
+  int64_t *accepted = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+  int64_t *Bbuf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(s + 1));
+  double *T = (double *)malloc(sizeof(double) * 65536);
+  int64_t E[8];
+  if (!x || !phi || !dE || !accepted || !Bbuf || !T) {
+    rc = -2;
+    goto done;
+  }
+  oracle_neglog_table(T);
+  for (int j = 0; j < 4; ++j) stats[j] = 0;
+  *count = 0;
+  for (int64_t p = 0; p < m; ++p) {
+    uint32_t w = draw_word(prm->seed, (uint32_t)(p >> 7), 0, replica, TAG_INIT,
+                           (int)((p >> 5) & 3));
+    x[p] = (uint8_t)((w >> (p & 31)) & 1u);
+  }
+#define KQ_FIELDS()                                                        \
+  do {                                                                     \
+    for (int64_t e = 0; e < K * m; ++e) phi[e] = 0;                        \
+    for (int64_t r = 0; r < m; ++r) {                                      \
+      if (!x[r]) continue;                                                 \
+      for (int k = 0; k < K; ++k) {                                        \
+        const int64_t *row = q->P + (size_t)k * mm + (size_t)r * (size_t)m; \
+        for (int64_t p = 0; p < m; ++p)                                    \
+          if (p != r) phi[k * m + p] += row[p];                            \
+      }                                                                    \
+    }                                                                      \
+  } while (0)
+  KQ_FIELDS();
+  for (int k = 0; k < K; ++k) E[k] = oracle_kqubo_energy(q, k, x);
+  double delta = prm->delta0;
+  const double factor = 1.0 - prm->xi;
+  int64_t Eoff = 0;
+  for (int64_t it = 1; it <= prm->I_max; ++it) {
+    const uint32_t step = (uint32_t)it;
+    if (delta > prm->deltaf) delta = delta * factor;
+    for (int k = 0; k < K; ++k)
+      for (int64_t p = 0; p < m; ++p)
+        dE[k * m + p] = (1 - 2 * (int64_t)x[p]) *
+                        (q->P[(size_t)k * mm + (size_t)(p * m + p)] + phi[k * m + p]);
+    int64_t cnt = 0;
+    for (int64_t p = 0; p < m; ++p) {
+      int64_t a = 0;
+      for (int k = 0; k < K; ++k) {
+        int64_t e = dE[k * m + p];
+        if (prm->escape == 1) e -= Eoff;
+        const int64_t ak = e > 0 ? e : 0;
+        if (prm->accept == 0) a += ak;
+        else a = (k == 0 || ak < a) ? ak : a;
+      }
+      uint32_t w = draw_word(prm->seed, (uint32_t)(p >> 2), step, replica, TAG_ACCEPT,
+                             (int)(p & 3));
+      if ((double)a <= delta * T[w >> 16]) accepted[cnt++] = p;
+    }
+    int64_t event = INT64_MIN;
+    if (cnt > 0) {
+      uint32_t u = draw_word(prm->seed, 0, step, replica, TAG_SELECT, 0);
+      const int64_t r = accepted[pick(u, cnt)];
+      const int64_t sgn = x[r] ? -1 : 1;
+      for (int k = 0; k < K; ++k) E[k] += dE[k * m + r];
+      x[r] ^= 1;
+      for (int k = 0; k < K; ++k) {
+        const int64_t *row = q->P + (size_t)k * mm + (size_t)r * (size_t)m;
+        for (int64_t p = 0; p < m; ++p)
+          if (p != r) phi[k * m + p] += sgn * row[p];
+      }
+      Eoff = 0;
+      /* Alg. 4 / Alg. 5 with K-dimensional dominance */
+      int64_t target = -1;
+      if (prm->archive == 0) {
+        for (int64_t y = 0; y < *count && target < 0; ++y)
+          if (dominates_k(K, E, arch_E + y * K)) target = y;
+        if (target < 0 && *count < s) target = (*count)++;
+      } else {
+        int64_t nb = 0;
+        int dominated = 0;
+        for (int64_t y = 0; y < *count; ++y) {
+          if (dominates_k(K, E, arch_E + y * K)) Bbuf[nb++] = y;
+          if (dominates_k(K, arch_E + y * K, E)) dominated = 1;
+        }
+        if (!dominated) {
+          if (nb > 0)
+            target = Bbuf[pick(draw_word(prm->seed, 0, step, replica, TAG_EXPLOIT, 0), nb)];
+          else if (*count < s)
+            target = (*count)++;
+        }
+      }
+      if (target >= 0) {
+        memcpy(arch_E + target * K, E, sizeof(int64_t) * (size_t)K);
+        memcpy(arch_bits + target * m, x, (size_t)m);
+      }
+      stats[0] += 1;
+      event = r;
+    } else if (prm->escape == 0) {
+      if (*count > 0) {
+        uint32_t u = draw_word(prm->seed, 0, step, replica, TAG_RESTART, 0);
+        const int64_t slot = pick(u, *count);
+        memcpy(x, arch_bits + slot * m, (size_t)m);
+        memcpy(E, arch_E + slot * K, sizeof(int64_t) * (size_t)K);
+        KQ_FIELDS();
+        stats[1] += 1;
+        event = -1 - slot;
+      } else {
+        stats[2] += 1;
+      }
+    } else {
+      Eoff += prm->beta;
+      stats[3] += 1;
+    }
+    if (trace) {
+      for (int k = 0; k < K; ++k) trace[(it - 1) * (K + 1) + k] = E[k];
+      trace[(it - 1) * (K + 1) + K] = event;
+    }
+    if (prm->check)
+      for (int k = 0; k < K; ++k)
+        if (E[k] != oracle_kqubo_energy(q, k, x)) {
+          rc = -3;
+          goto done;
+        }
+  }
+#undef KQ_FIELDS
+  memcpy(x_final, x, (size_t)m);
+  memcpy(E_final, E, sizeof(int64_t) * (size_t)K);
+done:
+  free(x); free(phi); free(dE); free(accepted); free(Bbuf); free(T);
+  return rc;
+}

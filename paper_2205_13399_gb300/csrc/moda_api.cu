@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "moda.h"
+#include "moda_host.h"
 #include "moda_internal.h"
 
 namespace {
@@ -136,6 +137,19 @@ moda_status device_schedule(DeviceData &dd, double d0, double df, double xi,
 
 namespace moda {
 void set_last_error(const char *msg) { g_error = msg; }
+
+moda_status schedule_view(int device, double delta0, double deltaf, double xi,
+                          int64_t I_max, ScheduleView *out) {
+  std::lock_guard<std::mutex> lock(g_dev_mutex);
+  DeviceData *dd = nullptr;
+  moda_status st = device_table(device, &dd);
+  if (st != MODA_OK) return st;
+  DeviceData::Sched sch;
+  st = device_schedule(*dd, delta0, deltaf, xi, I_max, &sch);
+  if (st != MODA_OK) return st;
+  *out = ScheduleView{sch.delta, sch.lo, sch.hi, sch.count, dd->table, dd->tmin, dd->tmax};
+  return MODA_OK;
+}
 }  // namespace moda
 
 struct moda_instance_s;

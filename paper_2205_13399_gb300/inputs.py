@@ -171,3 +171,11 @@ def serving_requests(count: int, rate_per_s: float = 200.0, sizes=(20, 30, 50, 7
         out.append(Request(t, QAPInstance(f"SERVE.{index0 + k}", n, F1, F2, D, rho),
                            I_max, index0 + k))
     return out
+
+
+def random_qubo(K: int, m: int, index: int = 0, lo: int = -100, hi: int = 100) -> np.ndarray:
+    """K dense QUBO matrices of m bits, upper triangle uniform integers in
+    [lo, hi] (the lower triangle is zero), for the explicit-QUBO path."""
+    rng = _rng("QUBO", index)
+    Q = rng.integers(lo, hi + 1, (K, m, m)).astype(np.int32)
+    return np.triu(Q)

@@ -33,7 +33,9 @@ ABI_FUNCTIONS = [
     "moda_last_error", "moda_anneal_noalloc", "moda_anneal_batch",
     "moda_server_create", "moda_server_submit", "moda_server_poll", "moda_server_info",
     "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak", "moda_scalarize",
-    "moda_sbda_front", "moda_read_snapshot",
+    "moda_sbda_front", "moda_read_snapshot", "moda_qubo_create", "moda_qubo_destroy",
+    "moda_qubo_anneal", "moda_qrun_wait", "moda_qrun_read", "moda_qrun_elapsed_ms",
+    "moda_qrun_destroy",
 ]
 
 
@@ -153,6 +155,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.moda_sbda_front.restype = st
     lib.moda_sbda_front.argtypes = [P, ctypes.POINTER(P), i32, ctypes.POINTER(Point), i32,
                                     ctypes.POINTER(i32), P]
+    lib.moda_qubo_create.restype = st
+    lib.moda_qubo_create.argtypes = [i32, i32, P, ctypes.POINTER(P)]
+    lib.moda_qubo_destroy.restype = None
+    lib.moda_qubo_destroy.argtypes = [P]
+    lib.moda_qubo_anneal.restype = st
+    lib.moda_qubo_anneal.argtypes = [P, ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+    lib.moda_qrun_wait.restype = st
+    lib.moda_qrun_wait.argtypes = [P]
+    lib.moda_qrun_read.restype = st
+    lib.moda_qrun_read.argtypes = [P, P, P, P, P, P, P, P]
+    lib.moda_qrun_elapsed_ms.restype = st
+    lib.moda_qrun_elapsed_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.moda_qrun_destroy.restype = None
+    lib.moda_qrun_destroy.argtypes = [P]
     lib.moda_anneal_noalloc.restype = st
     lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
                                         ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
@@ -484,3 +500,74 @@ def sbda_front(inst: Instance, runs) -> list[dict]:
     _check(_lib.moda_sbda_front(inst._h, hs, k, pts, tot.value, ctypes.byref(tot), _ptr(perm)))
     return [dict(c1=pts[i].c1, c2=pts[i].c2, weight=pts[i].slot, replica=pts[i].replica,
                  perm=[int(v) for v in perm[i]]) for i in range(tot.value)]
+
+
+class Qubo:
+    """K (1..3) objectives as explicit m x m QUBO matrices (upper triangle
+    used), resident on the current device (``moda_qubo_create``)."""
+
+    def __init__(self, Q):
+        Q = np.ascontiguousarray(np.asarray(Q, dtype=np.int32))
+        if Q.ndim != 3 or Q.shape[1] != Q.shape[2]:
+            raise ValueError("Q must be K x m x m")
+        self.K, self.m = int(Q.shape[0]), int(Q.shape[1])
+        self.W = (self.m + 31) // 32
+        h = ctypes.c_void_p()
+        _check(_lib.moda_qubo_create(self.K, self.m, _ptr(Q), ctypes.byref(h)))
+        self._h = h
+
+    def anneal(self, params: Params | None = None, stream=None, **kw) -> "QRun":
+        """``moda_qubo_anneal``: enqueue ``params.replicas`` runs."""
+        if params is None:
+            params = make_params(**kw)
+        h = ctypes.c_void_p()
+        _check(_lib.moda_qubo_anneal(self._h, ctypes.byref(params), _stream_handle(stream),
+                                     ctypes.byref(h)))
+        return QRun(self, h, params)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.moda_qubo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class QRun:
+    """Handle of an explicit-QUBO anneal (``moda_qrun_*``)."""
+
+    def __init__(self, q: Qubo, handle, params: Params):
+        self.q, self._h, self.params = q, handle, params
+        self.R = params.replicas
+        self.s = params.archive_size if params.archive_size > 0 else q.m
+
+    def wait(self):
+        _check(_lib.moda_qrun_wait(self._h))
+        return self
+
+    def elapsed_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(_lib.moda_qrun_elapsed_ms(self._h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def read(self, trace: bool = False) -> dict:
+        R, s, K, W = self.R, self.s, self.q.K, self.q.W
+        out = {"count": np.zeros(R, dtype=np.int32), "E": np.zeros((R, s, K), dtype=np.int64),
+               "bits": np.zeros((R, s, W), dtype=np.uint32), "x": np.zeros((R, W), dtype=np.uint32),
+               "E_final": np.zeros((R, K), dtype=np.int64), "stats": np.zeros((R, 4), dtype=np.int64)}
+        tr = np.zeros((R, self.params.I_max, K + 1), dtype=np.int64) if trace else None
+        _check(_lib.moda_qrun_read(self._h, _ptr(out["count"]), _ptr(out["E"]), _ptr(out["bits"]),
+                                   _ptr(out["x"]), _ptr(out["E_final"]), _ptr(out["stats"]),
+                                   _ptr(tr) if trace else None))
+        if trace:
+            out["trace"] = tr
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.moda_qrun_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

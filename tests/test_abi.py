@@ -128,3 +128,20 @@ def test_batch_and_server_null_arguments(lib):
     assert lib.moda_server_info(None, None, None, None, None) == 1
     lib.moda_server_destroy.restype = None
     lib.moda_server_destroy(None)
+
+
+def test_qubo_null_arguments(lib):
+    P = ctypes.c_void_p
+    out = ctypes.c_void_p()
+    lib.moda_qubo_create.restype = ctypes.c_int
+    assert lib.moda_qubo_create(2, 10, None, ctypes.byref(out)) == 1
+    lib.moda_qubo_anneal.restype = ctypes.c_int
+    assert lib.moda_qubo_anneal(None, None, None, ctypes.byref(out)) == 1
+    lib.moda_qrun_wait.restype = ctypes.c_int
+    assert lib.moda_qrun_wait(None) == 1
+    lib.moda_qrun_read.restype = ctypes.c_int
+    assert lib.moda_qrun_read(None, None, None, None, None, None, None, None) == 1
+    lib.moda_qubo_destroy.restype = None
+    lib.moda_qubo_destroy(None)
+    lib.moda_qrun_destroy.restype = None
+    lib.moda_qrun_destroy(None)

@@ -122,6 +122,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 // Bulk copy global -> shared; both addresses 16-byte aligned, bytes a
 // multiple of 16.
+// Bulk prefetch of global memory into L2 (no destination, no completion
+// signal); address 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
                                          uint32_t bytes, uint64_t *bar) {
   asm volatile(
@@ -760,6 +765,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           pend |= 1u << b;
         }
         sPf[tt & 7] = PfRec{issue ? (int)t : 0, slot_p, (int)par, 0};
+      } else if (!NARROW && fc && lane == 0 && A.escape == 0 && acount > 0 &&
+                 t + 2 <= I_max) {
+        // Records read in place (no prefetch buffers; the large 16-byte
+        // records of the int64 variant): bring the record and state of the
+        // member a jump two iterations ahead would land on into L2.  Only a
+        // hint -- the jump reads the current data anyway.
+        const uint32_t tt = t + 2;
+        const int slot_p = pick(sRnd[(tt % kRing) * 4 + 1], acount);
+        bulk_prefetch_l2(gF + (size_t)slot_p * sl.bytes, (uint32_t)sl.bytes);
+        if (!A.bits_in_smem) {
+          const uint32_t boff = (bits_lo + 4u * (uint32_t)(slot_p * W)) & 15u;
+          bulk_prefetch_l2(reinterpret_cast<const unsigned char *>(gBits + (size_t)slot_p * W) - boff,
+                           (boff + 4u * (uint32_t)W + 15u) & ~15u);
+        }
       }
       if (++pb_next == NB) pb_next = 0;
       if (pf && LA == 0) {

@@ -86,6 +86,8 @@ def parse_args(argv=None):
     ap.add_argument("--prefetch", type=int, default=0,
                     help="field-cache prefetch distance + 1 (0: automatic)")
     ap.add_argument("--field-cache", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick block shape and prefetch distance by timed trials first")
     ap.add_argument("--normalize", action="store_true",
                     help="QUBO normalisation (Sec. 4.2) in the acceptance test")
     ap.add_argument("--I-max", dest="I_max", type=int, default=None,
@@ -666,6 +668,12 @@ def main(argv=None):
     kw = dict(replicas=R, replica_base=base, I_max=I_max, seed=run["seed"],
               block_threads=args.block_threads, prefetch=args.prefetch,
               field_cache=args.field_cache, normalize=args.normalize)
+    tuned = None
+    if args.autotune:  # untimed: trials on the cold end of the schedule
+        best, trial_ms = moda.autotune(g, **kw)
+        kw.update(block_threads=best.block_threads, prefetch=best.prefetch)
+        tuned = {"block_threads": best.block_threads, "prefetch": best.prefetch,
+                 "trial_ms": trial_ms}
 
     def step():
         r = moda.anneal(g, stream=stream, **kw).wait()
@@ -732,7 +740,8 @@ def main(argv=None):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": workload_config(args.workload, inst_np, run,
-                                  {"parallelism": f"replicas x{world} GPU(s)"}),
+                                  {"parallelism": f"replicas x{world} GPU(s)",
+                                   **({"autotuned": tuned} if tuned else {})}),
         "bit_trials_per_s": value * m,
         "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},

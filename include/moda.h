@@ -281,6 +281,19 @@ moda_status moda_qrun_read(moda_qrun run, int32_t *count, int64_t *E, uint32_t *
 moda_status moda_qrun_elapsed_ms(moda_qrun run, float *ms);
 void moda_qrun_destroy(moda_qrun run);
 
+/* Autotuner of the launch layout: times short trials of every block shape
+ * the kernel has (bits per thread and threads per block) and, when the
+ * escape jumps to the archive, of field-cache prefetch distances 1 and 2
+ * besides the automatic choice, on `inst` with `params` (trial_iters
+ * iterations at the cold end of the schedule, delta = deltaf, on at most
+ * one replica per SM), and writes into *best a copy of *params with the
+ * fastest block_threads and prefetch; *best_ms (if not NULL) receives the
+ * winning trial's time.  Results of a run do not depend on these two
+ * fields, so tuning never changes what an anneal computes.  Blocks the
+ * calling thread while the trials run on cuda_stream. */
+moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t trial_iters,
+                          void *cuda_stream, moda_params *best, float *best_ms);
+
 /* ---- Serving ---------------------------------------------------------
  *
  * A queue of anneal requests served as they arrive (not in the paper:

@@ -1305,4 +1305,63 @@ moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t cou
   return MODA_OK;
 }
 
+
+// ---- autotuning ------------------------------------------------------------
+
+moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t trial_iters,
+                          void *cuda_stream, moda_params *best, float *best_ms) {
+  if (!inst || !params || !best) return fail(MODA_EINVAL, "NULL argument");
+  if (trial_iters < 1) return fail(MODA_EINVAL, "trial_iters must be >= 1");
+  const int m = inst->m;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // Candidates: every block shape the kernel has (B bits per thread, the
+  // fewest threads that hold m bits) and, when the escape jumps to the
+  // archive, prefetch distances 1 and 2 besides the automatic choice.
+  std::vector<int32_t> shapes;
+  for (int b : {1, 2, 3, 4, 6, 8}) {
+    const int64_t T = ((m + b - 1) / b + 31) / 32 * 32;
+    if (T >= 32 && T <= moda::kMaxWorkers &&
+        std::find(shapes.begin(), shapes.end(), (int32_t)T) == shapes.end())
+      shapes.push_back((int32_t)T);
+  }
+  std::vector<int32_t> prefetches = {0};
+  if (params->escape == MODA_ESC_ARCHIVE && params->field_cache != 2) {
+    prefetches.push_back(2);
+    prefetches.push_back(3);
+  }
+  // Trials run the cold end of the schedule (delta0 = deltaf, where a run
+  // spends most of its iterations) on at most one replica per SM.
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inst->device);
+  moda_params trial = *params;
+  trial.replicas = std::min(params->replicas, sms);
+  trial.I_max = trial_iters;
+  trial.delta0 = params->deltaf;
+  trial.trace = 0;
+  trial.snapshot_every = 0;
+  bool found = false;
+  float fastest = 0.f;
+  moda_params winner = *params;
+  for (int32_t T : shapes)
+    for (int32_t pf : prefetches) {
+      trial.block_threads = T;
+      trial.prefetch = pf;
+      moda_run r = nullptr;
+      if (moda_anneal(inst, &trial, stream, &r) != MODA_OK) continue;  // does not fit
+      float ms = 0.f;
+      const bool ok = moda_wait(r, -1) == MODA_OK && moda_run_elapsed_ms(r, &ms) == MODA_OK;
+      moda_destroy_run(r);
+      if (ok && (!found || ms < fastest)) {
+        found = true;
+        fastest = ms;
+        winner.block_threads = T;
+        winner.prefetch = pf;
+      }
+    }
+  if (!found) return fail(MODA_EUNSUPPORTED, "no candidate shape runs this instance");
+  *best = winner;
+  if (best_ms) *best_ms = fastest;
+  return MODA_OK;
+}
+
 }  // extern "C"

@@ -2,46 +2,42 @@
 // Alg. 3 of arXiv 2205.13399, for the bi-objective QAP: one thread block
 // runs one replica for all I_max iterations, its state held on chip.
 //
-// A block is Tw worker threads plus one control warp.  Worker `tid` owns
+// A block is Tw worker threads plus two control warps.  Worker `tid` owns
 // the bits p = k*Tw + tid, k < B ("rounds"), of the n*n-bit two-way
 // one-hot state (bit p = i*n + u: facility i at location u, Sec. 2.2) and
-// keeps in registers, per owned bit:
-//   x_p                 (a bit of `xmask`),
-//   rc_p = R_i + C_u    (row count of facility i plus column count of u),
-//   L1_p, L2_p          cost-only local fields
-//                       L_k[(i,u)] = sum_{(j,v)} Fs^k_ij d_uv x_jv,
-//                       Fs^k = F^k + F^k^T.
-// With zero-diagonal symmetric distances, P^k_(i,u),(j,v) = Fs^k_ij d_uv is
-// the off-diagonal of Eq. cale's P for the cost QUBO and its diagonal is 0,
-// so the cost part of Delta E_k at bit p is (1 - 2 x_p) L_k[p].  Flipping
-// bit (i,u) changes g (Eq. gqap) by 2 (1 - 2x)(rc - 1 - 2x), hence
-//   Delta E_k = (1 - 2x) L_k + w_k (1 - 2x)(rc - 1 - 2x),  alpha_k = w_k/2
-// (Eq. wqubom).  Q is never stored: a flip of (j,v) changes every field by
-// s * Fs^k_ij * d_uv -- the outer product of a flow column and a distance
-// column, s = +1 when the bit turns on.
+// keeps in registers, per owned bit, x_p (a bit of `xmask`) and
+//   Delta E_k(p) = (1 - 2 x_p)(L_k[p] + w_k (R_i + C_u - 1 - 2 x_p)),
+// L_k[(i,u)] = sum_{(j,v)} Fs^k_ij d_uv x_jv the cost local field (Fs^k =
+// F^k + F^k^T), R_i and C_u the row and column counts, alpha_k = w_k / 2
+// (Eq. cale with the penalty of Eq. wqubom).  With zero-diagonal symmetric
+// distances P^k_(i,u),(j,v) = Fs^k_ij d_uv, so Q is never stored: a flip of
+// (j,v) with s = +1 when the bit turns on changes every other Delta E_k(q)
+// by (1 - 2 x_q) s (Fs^k_ij d_uv + w_k [i == j or u == v]) -- the outer
+// product of a flow column and a distance column -- and the flipped bit's
+// Delta E changes sign.
 //
 // One iteration t (Alg. 3):
-//   workers   Delta E and the parallel trial of their bits; warp ballots
-//             give accept masks in (round, warp, lane) order = ascending
-//             bit order; accepted bits publish Delta E.
-//   control   meanwhile: the draws of a later iteration, the schedule
-//             entry of the next one, and (field cache on, replica not in a
-//             run of flips) a bulk copy (TMA, mbarrier) of the cached
-//             fields of the member that a jump at t + lookahead would land
-//             on -- its draw and |A| are known already; the copy is not
-//             used if that member is rewritten before then.
-//   -- barrier --
-//   control   counts the accepted bits, rank-selects one ("one flip at
-//             random", ascending bit order) or settles the jump, and
-//             publishes the decision.
-//   -- barrier --
-//   all       Flip: workers apply it to their registers and ballot "x
-//             dominates slot y" -- barrier -- every warp picks the target
-//             slot (Alg. 4 / Alg. 5); workers store their part of x (and of
-//             the fields, into the cache).
-//             Jump: workers take the member's fields from the prefetch
-//             buffer, the cache, or rebuild them as L_k = Fs_k (X D).
-//             Otherwise: raise the energy offset by beta.
+//   workers     the parallel trial of their bits; warp ballots give accept
+//               masks in (round, warp, lane) order = ascending bit order;
+//               accepted bits publish Delta E and their state bit.
+//   warp A      meanwhile: every 8 iterations the draws and schedule
+//               entries 8..15 iterations ahead; the jump record of t (the
+//               member a jump would land on -- its draw and |A| are known
+//               -- and whether its prefetched copy is usable).
+//   warp B      meanwhile (field cache on, replica not in a run of flips):
+//               a bulk copy (TMA, mbarrier) of the cached Delta E of the
+//               member a jump at t + lookahead would land on; with the
+//               cache read in place, an L2 prefetch of it instead.
+//   -- barrier counting the threads that accepted a bit --
+//   every warp  0: the jump (or escape) of warp A's record; otherwise the
+//               rank selection of one accepted bit ("one flip at random").
+//               Flip: workers apply it to their registers and ballot "x
+//               dominates slot y" -- barrier -- every warp picks the target
+//               slot (Alg. 4 / Alg. 5); workers store their part of x (and
+//               of Delta E, into the cache).  Jump: workers take the
+//               member's Delta E from the prefetch buffer, the cache, or
+//               rebuild it as L_k = Fs_k (X D).  Otherwise: raise the
+//               energy offset by beta.
 #include <cstdint>
 #include <type_traits>
 
@@ -273,8 +269,8 @@ struct SchEntry {
   double lod, hid;
 };
 
-// What iteration t does when no bit is accepted (Alg. 3), settled by the
-// control warp before the iteration's barrier.
+// What iteration t does when no bit is accepted (Alg. 3), settled by
+// control warp A before the iteration's barrier.
 struct JumpRec {
   int32_t kind;     // kJump or kNone
   int32_t slot;     // archive slot jumped to
@@ -344,9 +340,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   dE2_t *sDE = reinterpret_cast<dE2_t *>(smem + lay.dE);  // [bits]
   // state bit of each accepted bit, published beside its Delta E
   uint8_t *sXb = reinterpret_cast<uint8_t *>(smem + lay.dE) + sizeof(dE2_t) * (size_t)B * Tw;
-  // Prefetch bookkeeping of the control warp (after initialisation; shares
-  // the reduction space): sPf[target iteration % 8], and sWr[iteration % 8]
-  // = the archive slot that iteration wrote (-1 = none).
+  // Prefetch bookkeeping (after initialisation; shares the reduction
+  // space): sPf[target iteration % 8], the copies warp B started, and
+  // sWr[iteration % 8] = the archive slot that iteration wrote (-1 = none),
+  // kept by warp A.
   PfRec *sPf = reinterpret_cast<PfRec *>(smem + lay.red);
   int32_t *sWr = reinterpret_cast<int32_t *>(smem + lay.red + 8 * sizeof(PfRec));
   JumpRec *sJr = reinterpret_cast<JumpRec *>(smem + lay.jr);  // [t % 8]
@@ -560,7 +557,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   uint32_t last_t = 0;
   int last_target = -1;
   const uint32_t bits_lo = (uint32_t)(uintptr_t)gBits;  // low bits of the state array
-  // Archive snapshots (Fig. mdasl), taken by the control warp alone: the
+  // Archive snapshots (Fig. mdasl), taken by control warp A alone: the
   // archive as it stood after iteration t is copied right after the
   // barrier of iteration t + 1 (or after the loop), in that iteration's
   // decision; it cannot change before then, and the next change (a flip's

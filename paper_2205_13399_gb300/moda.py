@@ -35,7 +35,7 @@ ABI_FUNCTIONS = [
     "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak", "moda_scalarize",
     "moda_sbda_front", "moda_read_snapshot", "moda_qubo_create", "moda_qubo_destroy",
     "moda_qubo_anneal", "moda_qrun_wait", "moda_qrun_read", "moda_qrun_elapsed_ms",
-    "moda_qrun_destroy",
+    "moda_qrun_destroy", "moda_autotune",
 ]
 
 
@@ -169,6 +169,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.moda_qrun_elapsed_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.moda_qrun_destroy.restype = None
     lib.moda_qrun_destroy.argtypes = [P]
+    lib.moda_autotune.restype = st
+    lib.moda_autotune.argtypes = [P, ctypes.POINTER(Params), i32, P, ctypes.POINTER(Params),
+                                  ctypes.POINTER(ctypes.c_float)]
     lib.moda_anneal_noalloc.restype = st
     lib.moda_anneal_noalloc.argtypes = [i32, P, P, P, ctypes.POINTER(Penalty),
                                         ctypes.POINTER(Params), ctypes.POINTER(DeviceOutputs), P]
@@ -571,3 +574,16 @@ class QRun:
 
     def __del__(self):
         self.close()
+
+
+def autotune(inst: Instance, params: Params | None = None, trial_iters: int = 2000,
+             stream=None, **kw) -> tuple[Params, float]:
+    """``moda_autotune``: the fastest block shape and prefetch distance for
+    ``params`` on ``inst`` (short trials); returns (tuned params, trial ms)."""
+    if params is None:
+        params = make_params(**kw)
+    best = Params()
+    ms = ctypes.c_float()
+    _check(_lib.moda_autotune(inst._h, ctypes.byref(params), int(trial_iters),
+                              _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
+    return best, float(ms.value)

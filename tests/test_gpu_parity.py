@@ -252,3 +252,21 @@ def test_narrow_penalty_sum_above_2_31(n, fv, dv, acc):
     _, _, res, tr = gpu_run(inst, trace=True, **kw)
     _, orc = oracle_run(inst, trace=True, **kw)
     compare(res, range(16), orc, n * n, gpu_trace=tr)
+
+
+def test_autotune_picks_a_layout_with_identical_results():
+    """moda_autotune times the block shapes and prefetch distances; the
+    layout it returns runs and gives the same results as the default one."""
+    from paper_2205_13399_gb300 import moda
+    inst = inputs.uniform_instance(20, index=8, workload="P8")
+    g = moda.Instance(inst.F1, inst.F2, inst.D)
+    kw = dict(replicas=4, I_max=2500, seed=3, **FAST)
+    best, ms = moda.autotune(g, trial_iters=500, **kw)
+    assert best.block_threads % 32 == 0 and 32 <= best.block_threads <= 960
+    assert best.prefetch in (0, 2, 3) and ms > 0
+    assert best.replicas == 4 and best.I_max == 2500
+    a = moda.anneal(g, params=best).wait().read()
+    b = moda.anneal(g, **kw).wait().read()
+    for key in ("count", "E", "bits", "x", "E_final"):
+        assert np.array_equal(getattr(a, key), getattr(b, key)), key
+    assert np.array_equal(a.stats[:, :4], b.stats[:, :4])

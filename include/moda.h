@@ -123,6 +123,21 @@ typedef struct {
                             run (I_max / K snapshots, for the hypervolume
                             trace of Fig. mdasl; moda_read_snapshot);
                             0: none.  Not with moda_anneal_noalloc. */
+  int32_t fast_forward;  /* 1: stop iterating once the rest of the run is
+                            settled, with results identical to running every
+                            iteration (archive escape only; not with
+                            normalize or snapshot_every).  A trial at an
+                            archive member in which no bit had an acceptance
+                            penalty a <= hi_t marks that member as unable to
+                            accept: hi_t never rises, so no later trial
+                            there accepts either (until the slot is
+                            rewritten).  Once every member is so marked and
+                            the state about to be tried is a member, every
+                            remaining iteration is a jump, and the run
+                            lands on the final iteration's draw.  The
+                            counters, trace and final state are those of the
+                            full run; stats[6] counts the iterations not
+                            executed.  0: every iteration runs (default). */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */
@@ -184,10 +199,9 @@ moda_status moda_wait(moda_run run, int64_t timeout_ms);
  *   stats    [8]        accepted flips, jumps to the archive, escapes with an
  *                       empty archive, offset raises; then, for profiling,
  *                       jumps served by a prefetched field-cache record,
- *                       jumps that read the record directly, and (only in
- *                       builds with MODA_KERNEL_CLOCKS defined, else 0) SM
- *                       clock cycles spent waiting for prefetched records
- *                       and SM clock cycles of the iteration loop
+ *                       jumps that read the record directly, iterations
+ *                       settled without being executed (params.fast_forward),
+ *                       and 0
  * Any pointer may be NULL.  MODA_EBUSY while the run executes. */
 moda_status moda_read_replica(moda_run run, int32_t r, int32_t *count,
                               int64_t *E, uint32_t *bits, uint32_t *x,
@@ -263,8 +277,8 @@ moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t cou
  * moda_qubo_create copies K (1..3) matrices of m x m int32 (m <= 4096,
  * row-major, [K][m][m]) to the current device; MODA_EOVERFLOW when an
  * entry of Q + Q^T leaves int32.  moda_qubo_anneal enqueues params->replicas
- * runs on cuda_stream (params.normalize and params.snapshot_every must be
- * 0; params.field_cache == 2 turns the archive Delta E records off, jumps
+ * runs on cuda_stream (params.normalize, params.snapshot_every and
+ * params.fast_forward must be 0; params.field_cache == 2 turns the archive Delta E records off, jumps
  * then rebuild Delta E).  moda_qrun_read copies, for all replicas, any
  * non-NULL of: archive sizes [R], energies [R][s][K], states [R][s][W]
  * (W = ceil(m / 32), bit p in word p / 32), final states [R][W] and

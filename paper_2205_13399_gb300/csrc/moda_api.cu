@@ -452,6 +452,13 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   if (p->snapshot_every < 0) return fail(MODA_EINVAL, "snapshot_every must be >= 0");
   if (p->snapshot_every > 0 && p->I_max / p->snapshot_every > 1000000)
     return fail(MODA_EINVAL, "more than 10^6 snapshots");
+  if (p->fast_forward != 0 && p->fast_forward != 1)
+    return fail(MODA_EINVAL, "fast_forward must be 0 or 1");
+  if (p->fast_forward &&
+      (p->escape != MODA_ESC_ARCHIVE || p->normalize || p->snapshot_every))
+    return fail(MODA_EINVAL,
+                "fast_forward needs the archive escape, normalize = 0 and snapshot_every = 0");
+  const bool ff = p->fast_forward == 1;
   const bool narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2);
   // Field cache: one record of the fields per archive slot, so a jump to
   // the archive reloads the member's fields instead of rebuilding them.
@@ -480,7 +487,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
     for (int la = c ? la_hi : 0; la >= (c ? la_lo : 0) && !placed; --la)
       for (int opt = 0; opt < 3 && !placed; ++opt)
         for (int de = 1; de >= 0 && !placed; --de) {
-          const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1, narrow};
+          const moda::Placement pl{opt <= 1, opt == 0, c == 1, la, de == 1, narrow, ff};
           const moda::SmemLayout l =
               moda::smem_layout(inst->n, m, inst->W, s_cap, T, B, pl);
           if ((int64_t)l.total <= dev_smem) {
@@ -600,6 +607,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   a.stats = r->stats;
   a.trace = r->trace;
   a.error = r->error;
+  a.fast_forward = p->fast_forward;
 
   cudaError_t e = cudaEventCreate(&r->start);
   if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
@@ -933,7 +941,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     const Prepared &pl = pls[i];
     cudaGraphNode_t n0, n1, n2, n3;
     const void *func = nullptr;
-    e = moda::anneal_function(pl.rounds, pl.narrow, moda::uses_extensions(pl.args), pl.smem,
+    e = moda::anneal_function(pl.rounds, pl.narrow, moda::kernel_mode(pl.args), pl.smem,
                               &func);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, r->start);
     if (e == cudaSuccess) {
@@ -1339,6 +1347,7 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
   trial.delta0 = params->deltaf;
   trial.trace = 0;
   trial.snapshot_every = 0;
+  trial.fast_forward = 0;  // every trial iteration runs
   bool found = false;
   float fastest = 0.f;
   moda_params winner = *params;

@@ -86,6 +86,9 @@ struct AnnealArgs {
   int64_t *stats;           // [R][kStats]
   int64_t *trace;           // [R][I_max][3] or nullptr
   int32_t *error;           // device status word, kErrNone = fine
+  // 1: stop once every archive member is known unable to accept and the
+  // state about to be tried is a member (moda_params.fast_forward)
+  int32_t fast_forward;
 };
 
 // Placement choices of one launch (decided on the host).
@@ -96,12 +99,13 @@ struct Placement {
   int lookahead;          // prefetch distance, iterations
   bool de_in_smem;        // accepted bits publish Delta E in shared memory
   bool narrow;            // Delta E fits int32 (kernel variant)
+  bool ff;                // fast-forward bookkeeping (moda_params.fast_forward)
 };
 
 // Byte offsets of the shared-memory carve-up of one annealing block with
 // `workers` bit-owning threads (plus one control warp).
 struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, stat, init, mbar, dE, pf,
+  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, stat, ff, init, mbar, dE, pf,
       pf_slot, pfE, pfW, archE, archB, total;
 };
 
@@ -124,6 +128,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.bc = o;    o = align_up(o + 32, 16);
   L.jr = o;    o = align_up(o + 8 * 32, 16);                 // 8 entries
   L.stat = o;  o = align_up(o + 8 * 4, 16);                  // counters
+  // fast-forward: 4 iteration stamps, 4 words of bookkeeping, then one
+  // bit per archive slot
+  L.ff = o;    if (P.ff) o = align_up(o + 4 * (8 + ((size_t)s + 31) / 32), 16);
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
   L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits + bits, 16);  // + state bytes
@@ -169,6 +176,12 @@ inline bool uses_extensions(const AnnealArgs &a) {
   return a.normalize != 0 || a.snap_every > 0;
 }
 
+// Kernel variant of a launch: 0 plain, 1 with the extensions, 2 with the
+// fast-forward bookkeeping (never together with an extension).
+inline int kernel_mode(const AnnealArgs &a) {
+  return uses_extensions(a) ? 1 : a.fast_forward ? 2 : 0;
+}
+
 // Bits per thread the kernel is instantiated for.
 bool supported_rounds(int b);
 
@@ -181,7 +194,7 @@ cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
 // threads per replica, `smem` bytes of dynamic shared memory, which this
 // call allows), for launching from a CUDA graph node with one AnnealArgs
 // argument.
-cudaError_t anneal_function(int rounds, bool narrow, bool norm, size_t smem,
+cudaError_t anneal_function(int rounds, bool narrow, int mode, size_t smem,
                             const void **func);
 
 // Sets the thread-local message that moda_last_error() returns.

@@ -247,8 +247,9 @@ struct Bcast {
   int32_t pad;
 };
 
-// Kinds of iteration outcome (Alg. 3).
-enum : int32_t { kNone = 0, kFlip = 1, kJump = 2 };
+// Kinds of iteration outcome (Alg. 3).  kFinish: this and every later
+// iteration jump (fast-forward), the last one to the slot given.
+enum : int32_t { kNone = 0, kFlip = 1, kJump = 2, kFinish = 3 };
 
 // Prefetch bookkeeping entry for one target iteration.
 struct PfRec {
@@ -272,8 +273,8 @@ struct SchEntry {
 // What iteration t does when no bit is accepted (Alg. 3), settled by
 // control warp A before the iteration's barrier.
 struct JumpRec {
-  int32_t kind;     // kJump or kNone
-  int32_t slot;     // archive slot jumped to
+  int32_t kind;     // kJump, kNone or kFinish
+  int32_t slot;     // archive slot jumped to (kFinish: by iteration I_max)
   int32_t pbuf;     // prefetch buffer holding it, -1: read the cache record
   uint32_t parity;  // that buffer's mbarrier phase parity
   // pbuf >= 0: shared-memory byte offsets of the member's Delta E record,
@@ -284,12 +285,15 @@ struct JumpRec {
 // NARROW: Delta E in int32 and the acceptance penalty in uint32 (the host
 // checked |Delta E_k| < 2^31 for every state and objective); otherwise
 // int64.
-// EXT: the optional extensions -- QUBO normalisation (Sec. 4.2: objective
-// k's Delta E scaled by s_k inside the acceptance test, in IEEE double) and
-// archive snapshots -- compiled in; without them the loop carries neither.
-template <int B, bool NARROW, bool EXT>
+// MODE 1 (EXT): the optional extensions -- QUBO normalisation (Sec. 4.2:
+// objective k's Delta E scaled by s_k inside the acceptance test, in IEEE
+// double) and archive snapshots -- compiled in; without them the loop
+// carries neither.  MODE 2: the fast-forward bookkeeping compiled in.
+// MODE 0: neither.
+template <int B, bool NARROW, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
+  constexpr bool EXT = MODE == 1;
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
   using dE2_t = typename std::conditional<NARROW, int2, longlong2>::type;
   // acceptance penalty: a sum of two non-negative Delta E, so uint32 in
@@ -315,8 +319,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   // LA = -1: the cache is read in place, nothing is prefetched.
   const int NB = LA + 2;
   const bool pf = fc && LA >= 0;
+  // Fast-forward (no extensions): stop once the rest of the run is settled.
+  constexpr bool ff = MODE == 2;
   const Placement P{A.energies_in_smem != 0, A.bits_in_smem != 0, fc, LA,
-                    de_smem, NARROW};
+                    de_smem, NARROW, ff};
   const SmemLayout lay = smem_layout(n, m, W, s, Tw, B, P);
   const bool NORM_ON = EXT && A.normalize != 0;
   const SlotLayout sl = slot_layout(m, NARROW);
@@ -347,6 +353,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   PfRec *sPf = reinterpret_cast<PfRec *>(smem + lay.red);
   int32_t *sWr = reinterpret_cast<int32_t *>(smem + lay.red + 8 * sizeof(PfRec));
   JumpRec *sJr = reinterpret_cast<JumpRec *>(smem + lay.jr);  // [t % 8]
+  // Fast-forward: sLive[t % 4] == t when some bit of iteration t's trial
+  // had its acceptance penalty in (lo_t, hi_t].  Kept by control warp A's
+  // lane 0 alone: sFF[0] the archive slot whose state the current
+  // iteration tries (-1: the state is no member), sFF[1] the number of
+  // slots marked in sDead, and sDead bit y when slot y's state was tried
+  // and no bit had a penalty <= hi.  hi_t never rises, so no later trial
+  // of that state accepts a bit either, until the slot is rewritten.
+  uint32_t *sLive = reinterpret_cast<uint32_t *>(smem + lay.ff);
+  int32_t *sFF = reinterpret_cast<int32_t *>(sLive + 4);
+  uint32_t *sDead = sLive + 8;
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
@@ -529,13 +545,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     sPf[tid] = PfRec{0, 0, 0, 0};
     sWr[tid] = -1;
   }
+  if (ff)
+    for (int e = tid; e < 8 + ((s + 31) >> 5); e += T) sLive[e] = e == 4 ? 0xFFFFFFFFu : 0u;
   __syncthreads();
 
   int64_t Eoff = 0;
   int acount = 0;
   // Outcome counters, kept by control warp A's lane 0 in shared memory:
   // flips, jumps, empty escapes, offset raises, prefetched jumps, direct
-  // reads.
+  // reads, iterations fast-forwarded.
   uint32_t *sStat = reinterpret_cast<uint32_t *>(smem + lay.stat);
   if (tid < 8) sStat[tid] = 0;
   // A bounded wait gave up: the thread sets `fail` and the shared flag
@@ -556,6 +574,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   int pb_next = (int)((1u + (uint32_t)(LA > 0 ? LA : 0)) % (uint32_t)NB);
   uint32_t last_t = 0;
   int last_target = -1;
+  // Fast-forward: sets or clears slot y's mark (control warp A, lane 0).
+  auto mark_dead = [&](int y, bool on) {
+    const uint32_t w = sDead[y >> 5], b = 1u << (y & 31);
+    sDead[y >> 5] = on ? (w | b) : (w & ~b);
+    sFF[1] += (int)on - (int)((w & b) != 0);
+  };
   const uint32_t bits_lo = (uint32_t)(uintptr_t)gBits;  // low bits of the state array
   // Archive snapshots (Fig. mdasl), taken by control warp A alone: the
   // archive as it stood after iteration t is copied right after the
@@ -644,7 +668,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             v.x = e1;
             v.y = e2;
             sDE[k * Tw + tid] = v;
-          sXb[k * Tw + tid] = (uint8_t)((xmask >> k) & 1u);
             sXb[k * Tw + tid] = (uint8_t)((xmask >> k) & 1u);
           }
           const uint32_t bal = __ballot_sync(kFull, acc);
@@ -668,6 +691,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // iterations rarely take it)
         const bool need = in && a > lo && a <= hi;
         if (__any_sync(kFull, need)) {
+          if (ff && lane == 0) sLive[t & 3u] = t;
           const int p = k * Tw + tid;
           uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
           philox10(c, k0, k1);
@@ -719,6 +743,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             jr.bar = (uint32_t)lay.mbar + 8u * (uint32_t)jb;
           }
         }
+      }
+      if (ff) {
+        // Every member is marked and iteration t tries one of them: no
+        // bit is accepted in t or later, so t .. I_max all jump and the
+        // run ends on the member iteration I_max draws.
+        int fin = -1;
+        if (lane == 0 && acount > 0 && sFF[1] == acount && sFF[0] >= 0) {
+          uint32_t c[4] = {0u, I_max, rep, kTagRestart};
+          philox10(c, k0, k1);
+          fin = pick(c[0], acount);
+        }
+        fin = __shfl_sync(kFull, fin, 0);
+        if (fin >= 0) jr = JumpRec{kFinish, fin, -1, 0, 0, 0, 0, 0};
       }
       if (lane == 0) sJr[t & 7] = jr;
       if (++jb == NB) jb = 0;
@@ -814,6 +851,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
       } else if (ctlA) {
         kind = nacc > 0 ? kFlip : jr.kind;
+        // the state tried in t is member sFF[0] and no penalty was <= hi
+        if (ff && nacc == 0 && lane == 0 && sFF[0] >= 0 && sLive[t & 3u] != t)
+          mark_dead(sFF[0], true);
         // the archive as it stood after the previous iteration
         if (snap_due) take_snapshot();
         snap_due = snap_mark;
@@ -940,6 +980,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           last_t = t;
         }
       }
+      if (ff && ctlA && lane == 0) {  // the new state is member `target` (if stored)
+        if (target >= 0) mark_dead(target, false);
+        sFF[0] = target;
+      }
       E1 = nE1;
       E2 = nE2;
       Eoff = 0;
@@ -994,6 +1038,39 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         rebuild(aBits + (size_t)slot * W, s1, s2);
       }
       if (ctlA && lane == 0) ++sStat[1];
+      if (ff && ctlA && lane == 0) sFF[0] = slot;
+    } else if (ff && kind == kFinish) {
+      // Iterations t .. I_max each jump to the member their draw picks
+      // (the archive no longer changes); the state ends as member
+      // jr.slot.  Delta E is not needed any more.
+      const int slot = jr.slot;
+      const longlong2 se = aE[slot];
+      E1 = se.x;
+      E2 = se.y;
+      if (worker) {
+        const uint32_t *wsrc = aBits + (size_t)slot * W;
+        xmask = 0;
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+          if (valid(k)) xmask |= ((wsrc[k * NWB + warp] >> lane) & 1u) << k;
+      }
+      if (A.trace != nullptr) {
+        for (uint64_t q = (uint64_t)t + (uint64_t)tid; q <= (uint64_t)I_max; q += (uint64_t)T) {
+          uint32_t c[4] = {0u, (uint32_t)q, rep, kTagRestart};
+          philox10(c, k0, k1);
+          const int y = pick(c[0], acount);
+          const longlong2 v = aE[y];
+          int64_t *tr = A.trace + ((size_t)rb * (size_t)I_max + (size_t)(q - 1)) * 3;
+          tr[0] = v.x;
+          tr[1] = v.y;
+          tr[2] = -1 - (int64_t)y;
+        }
+      }
+      if (ctlA && lane == 0) {
+        sStat[1] += I_max - t + 1;
+        sStat[6] = I_max - t;
+      }
+      break;
     } else if (A.escape == 0) {
       if (ctlA && lane == 0) ++sStat[2];
     } else {
@@ -1044,8 +1121,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
   if (tid == Tw) {  // control warp A counted the outcomes
     int64_t *st = A.stats + (size_t)kStats * rb;
-    for (int q = 0; q < 6; ++q) st[q] = sStat[q];
-    st[6] = 0;
+    for (int q = 0; q < 7; ++q) st[q] = sStat[q];
     st[7] = 0;
     A.arch_count[rb] = acount;
   }
@@ -1055,33 +1131,45 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 }
 
-template <int B, bool NARROW, bool EXT>
+template <int B, bool NARROW, int MODE>
 cudaError_t launch_bn(const AnnealArgs &args, int replicas, int workers,
                       size_t smem, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(
-      anneal_kernel<B, NARROW, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      anneal_kernel<B, NARROW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  anneal_kernel<B, NARROW, EXT><<<replicas, workers + 64, smem, stream>>>(args);
+  anneal_kernel<B, NARROW, MODE><<<replicas, workers + 64, smem, stream>>>(args);
   return cudaGetLastError();
+}
+
+template <int B, bool NARROW>
+cudaError_t launch_bm(const AnnealArgs &args, int replicas, int workers,
+                      size_t smem, cudaStream_t stream) {
+  switch (kernel_mode(args)) {
+    case 1: return launch_bn<B, NARROW, 1>(args, replicas, workers, smem, stream);
+    case 2: return launch_bn<B, NARROW, 2>(args, replicas, workers, smem, stream);
+    default: return launch_bn<B, NARROW, 0>(args, replicas, workers, smem, stream);
+  }
 }
 
 template <int B>
 cudaError_t launch_b(const AnnealArgs &args, int replicas, int workers, bool narrow,
                      size_t smem, cudaStream_t stream) {
-  if (uses_extensions(args))
-    return narrow ? launch_bn<B, true, true>(args, replicas, workers, smem, stream)
-                  : launch_bn<B, false, true>(args, replicas, workers, smem, stream);
-  return narrow ? launch_bn<B, true, false>(args, replicas, workers, smem, stream)
-                : launch_bn<B, false, false>(args, replicas, workers, smem, stream);
+  return narrow ? launch_bm<B, true>(args, replicas, workers, smem, stream)
+                : launch_bm<B, false>(args, replicas, workers, smem, stream);
+}
+
+template <int B, bool NARROW>
+const void *kernel_of(int mode) {
+  switch (mode) {
+    case 1: return reinterpret_cast<const void *>(anneal_kernel<B, NARROW, 1>);
+    case 2: return reinterpret_cast<const void *>(anneal_kernel<B, NARROW, 2>);
+    default: return reinterpret_cast<const void *>(anneal_kernel<B, NARROW, 0>);
+  }
 }
 
 template <int B>
-cudaError_t function_b(bool narrow, bool norm, size_t smem, const void **func) {
-  const void *f =
-      norm ? (narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true, true>)
-                     : reinterpret_cast<const void *>(anneal_kernel<B, false, true>))
-           : (narrow ? reinterpret_cast<const void *>(anneal_kernel<B, true, false>)
-                     : reinterpret_cast<const void *>(anneal_kernel<B, false, false>));
+cudaError_t function_b(bool narrow, int mode, size_t smem, const void **func) {
+  const void *f = narrow ? kernel_of<B, true>(mode) : kernel_of<B, false>(mode);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) *func = f;
   return e;
@@ -1093,15 +1181,15 @@ bool supported_rounds(int b) {
   return b == 1 || b == 2 || b == 3 || b == 4 || b == 6 || b == 8;
 }
 
-cudaError_t anneal_function(int rounds, bool narrow, bool norm, size_t smem,
+cudaError_t anneal_function(int rounds, bool narrow, int mode, size_t smem,
                             const void **func) {
   switch (rounds) {
-    case 1: return function_b<1>(narrow, norm, smem, func);
-    case 2: return function_b<2>(narrow, norm, smem, func);
-    case 3: return function_b<3>(narrow, norm, smem, func);
-    case 4: return function_b<4>(narrow, norm, smem, func);
-    case 6: return function_b<6>(narrow, norm, smem, func);
-    case 8: return function_b<8>(narrow, norm, smem, func);
+    case 1: return function_b<1>(narrow, mode, smem, func);
+    case 2: return function_b<2>(narrow, mode, smem, func);
+    case 3: return function_b<3>(narrow, mode, smem, func);
+    case 4: return function_b<4>(narrow, mode, smem, func);
+    case 6: return function_b<6>(narrow, mode, smem, func);
+    case 8: return function_b<8>(narrow, mode, smem, func);
     default: return cudaErrorInvalidValue;
   }
 }

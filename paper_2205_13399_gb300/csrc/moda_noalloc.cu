@@ -165,6 +165,10 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
     return nofail(MODA_EINVAL, "normalize must be 0 or 1");
   if (p->snapshot_every != 0)
     return nofail(MODA_EUNSUPPORTED, "archive snapshots need allocated buffers");
+  if (p->fast_forward != 0 && p->fast_forward != 1)
+    return nofail(MODA_EINVAL, "fast_forward must be 0 or 1");
+  if (p->fast_forward && (p->escape != MODA_ESC_ARCHIVE || p->normalize))
+    return nofail(MODA_EINVAL, "fast_forward needs the archive escape and normalize = 0");
   int64_t e1max = 0, e2max = 0, edmax = 0;  // largest entries (normalisation)
   for (int e = 0; e < n * n; ++e) {
     e1max = std::max<int64_t>(e1max, fs1[e]);
@@ -215,7 +219,8 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   for (int la = cache ? 1 : 0; la >= (cache ? -1 : 0) && !placed; --la)
     for (int opt = 0; opt < 3 && !placed; ++opt)
       for (int de = 1; de >= 0 && !placed; --de) {
-        const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1, narrow};
+        const moda::Placement pl{opt <= 1, opt == 0, cache, la, de == 1, narrow,
+                                 p->fast_forward == 1};
         const moda::SmemLayout l = moda::smem_layout(n, m, W, s, T, B, pl);
         if ((int64_t)l.total <= dev_smem) {
           place = pl;
@@ -301,6 +306,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   a.stats = out->stats;
   a.trace = nullptr;
   a.error = out->error;
+  a.fast_forward = p->fast_forward;
   e = moda::launch_anneal(a, p->replicas, T, B, place.narrow, lay.total, stream);
   if (e != cudaSuccess) return nofail(MODA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return MODA_OK;

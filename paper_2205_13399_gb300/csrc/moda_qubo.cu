@@ -522,8 +522,9 @@ moda_status moda_qubo_anneal(moda_qubo q, const moda_params *p, void *cuda_strea
       (p->archive != MODA_EXPLORE && p->archive != MODA_EXPLOIT) ||
       (p->escape != MODA_ESC_ARCHIVE && p->escape != MODA_ESC_OFFSET))
     return qfail(MODA_EINVAL, "bad accept, archive or escape mode");
-  if (p->normalize || p->snapshot_every)
-    return qfail(MODA_EUNSUPPORTED, "normalisation and snapshots are bQAP-path options");
+  if (p->normalize || p->snapshot_every || p->fast_forward)
+    return qfail(MODA_EUNSUPPORTED,
+                 "normalisation, snapshots and fast-forward are bQAP-path options");
   int B = 0;
   for (int b : {1, 2, 4})
     if ((int64_t)b * kMaxQThreads >= m) {

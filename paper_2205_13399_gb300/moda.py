@@ -70,6 +70,7 @@ class Params(ctypes.Structure):
         ("prefetch", ctypes.c_int32),
         ("normalize", ctypes.c_int32),
         ("snapshot_every", ctypes.c_int32),
+        ("fast_forward", ctypes.c_int32),
     ]
 
 
@@ -349,14 +350,15 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 deltaf: float = 1e4, xi: float = 1e-3, beta: int | None = None,
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
                 trace: bool = False, field_cache: str = "auto", prefetch: int = 0,
-                normalize: bool = False, snapshot_every: int = 0) -> Params:
+                normalize: bool = False, snapshot_every: int = 0,
+                fast_forward: bool = False) -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
                   int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)),
-                  int(snapshot_every))
+                  int(snapshot_every), int(bool(fast_forward)))
 
 
 def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,

@@ -12,14 +12,15 @@ import oracle
 def gpu_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explore",
             escape="archive", delta0=1e9, deltaf=1e4, xi=1e-3, beta=None, archive_size=0,
             replica_base=0, block_threads=0, trace=False, w=None, stream=None,
-            field_cache="auto", prefetch=0, normalize=False):
+            field_cache="auto", prefetch=0, normalize=False, fast_forward=False):
     from paper_2205_13399_gb300 import moda
     inst = moda.Instance(inst_np.F1, inst_np.F2, inst_np.D, w=w)
     run = moda.anneal(inst, replicas=replicas, I_max=I_max, seed=seed, accept=accept,
                       archive=archive, escape=escape, delta0=delta0, deltaf=deltaf, xi=xi,
                       beta=beta, archive_size=archive_size, replica_base=replica_base,
                       block_threads=block_threads, trace=trace, stream=stream,
-                      field_cache=field_cache, prefetch=prefetch, normalize=normalize)
+                      field_cache=field_cache, prefetch=prefetch, normalize=normalize,
+                      fast_forward=fast_forward)
     run.wait()
     res = run.read()
     traces = None

@@ -80,9 +80,55 @@ __device__ __forceinline__ int pick(uint32_t u, int count) {
   return (int)(((uint64_t)u * (uint32_t)count) >> 32);
 }
 
+// Position of the r-th (0-based) set bit of `mask`, r < popc(mask): a
+// binary search on the set-bit counts of halves, quarters, ...
 __device__ __forceinline__ int nth_set_bit(uint32_t mask, int r) {
-  for (int q = 0; q < r; ++q) mask &= mask - 1;
-  return __ffs(mask) - 1;
+  int pos = 0;
+  int c = __popc(mask & 0xFFFFu);
+  if (r >= c) {
+    r -= c;
+    pos = 16;
+  }
+  uint32_t m = mask >> pos;
+  c = __popc(m & 0xFFu);
+  if (r >= c) {
+    r -= c;
+    pos += 8;
+    m >>= 8;
+  }
+  c = __popc(m & 0xFu);
+  if (r >= c) {
+    r -= c;
+    pos += 4;
+    m >>= 4;
+  }
+  c = __popc(m & 0x3u);
+  if (r >= c) {
+    r -= c;
+    pos += 2;
+    m >>= 2;
+  }
+  if (r >= (int)(m & 1u)) pos += 1;
+  return pos;
+}
+
+// Flat index round*Tw + warp*32 + lane of the lowest set bit over `items`
+// ballot masks in (round, warp) order, or -1 if none, in every lane.
+__device__ __forceinline__ int warp_mask_first(const uint32_t *masks, int items, int nw,
+                                               int Tw, int lane) {
+  for (int q0 = 0; q0 < items; q0 += 32) {
+    const int it = q0 + lane;
+    const uint32_t mk = it < items ? masks[it] : 0u;
+    const unsigned nz = __ballot_sync(kFull, mk != 0u);
+    if (nz) {
+      const int L = __ffs(nz) - 1;
+      const uint32_t w = __shfl_sync(kFull, mk, L);
+      const int k = (q0 + L) / nw;
+      const int wi = q0 + L - k * nw;
+      return k * Tw + wi * 32 + __ffs(w) - 1;
+    }
+  }
+  return -1;
 }
 
 __device__ __forceinline__ bool dominates(int64_t a1, int64_t a2, int64_t b1,
@@ -935,17 +981,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
       }
       anyd = __syncthreads_or(anyd);
-      int aincl, acnt;
-      const int nb = warp_mask_total(sAmask, items, lane, aincl, acnt);
       int target = -1;
       if (A.archive == 0) {
         // Alg. 4: replace the first dominated member, else append.
-        if (nb > 0)
-          target = warp_mask_select(sAmask, items, NWB, Tw, lane, aincl, acnt, 0);
-        else if (acount < s)
-          target = acount++;
+        target = warp_mask_first(sAmask, items, NWB, Tw, lane);
+        if (target < 0 && acount < s) target = acount++;
       } else if (!anyd) {
         // Alg. 5: replace a random dominated member, else append.
+        int aincl, acnt;
+        const int nb = warp_mask_total(sAmask, items, lane, aincl, acnt);
         if (nb > 0)
           target = warp_mask_select(sAmask, items, NWB, Tw, lane, aincl, acnt,
                                     pick(rnd[2], nb));

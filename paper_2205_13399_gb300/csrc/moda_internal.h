@@ -105,8 +105,8 @@ struct Placement {
 // Byte offsets of the shared-memory carve-up of one annealing block with
 // `workers` bit-owning threads (plus one control warp).
 struct SmemLayout {
-  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, stat, ff, init, mbar, dE, pf,
-      pf_slot, pfE, pfW, archE, archB, total;
+  size_t Fs, D, M, mask, amask, rnd, sch, RC, red, bc, jr, stat, ff, draw, init, mbar, dE,
+      pf, pf_slot, pfE, pfW, archE, archB, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
@@ -131,6 +131,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   // fast-forward: 4 iteration stamps, 4 words of bookkeeping, then one
   // bit per archive slot
   L.ff = o;    if (P.ff) o = align_up(o + 4 * (8 + ((size_t)s + 31) / 32), 16);
+  // one bit per thread: each warp's acceptance draws of 4 iterations (one
+  // Philox block per lane), then the first iteration they cover
+  L.draw = o;  if (rounds == 1) o = align_up(o + 16 * (size_t)workers + 4 * (workers / 32), 16);
   L.init = o;  o = align_up(o + 4 * (size_t)W, 16);
   L.mbar = o;  o = align_up(o + 8 * (kMaxLookahead + 2), 16);
   L.dE = o;    if (P.de_in_smem) o = align_up(o + (P.narrow ? 8 : 16) * bits + bits, 16);  // + state bytes

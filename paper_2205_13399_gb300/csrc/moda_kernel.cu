@@ -409,6 +409,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   uint32_t *sLive = reinterpret_cast<uint32_t *>(smem + lay.ff);
   int32_t *sFF = reinterpret_cast<int32_t *>(sLive + 4);
   uint32_t *sDead = sLive + 8;
+  // One bit per thread: bits 4g .. 4g + 3 take the four words of one
+  // acceptance Philox block (group g = p / 4), so a warp's 32 bits need 8
+  // blocks per iteration.  A warp that must draw computes the blocks of
+  // iterations t .. t + 3 at once (lane l: group 8 warp + l % 8, iteration
+  // t + l / 8) into sDraw[32 warp + l] and reuses them while they cover
+  // the iteration; sDrawT[warp] is t (0: none yet).
+  uint4 *sDraw = reinterpret_cast<uint4 *>(smem + lay.draw);
+  uint32_t *sDrawT = reinterpret_cast<uint32_t *>(smem + lay.draw + 16 * (size_t)Tw);
 
   const int rb = blockIdx.x;
   const uint32_t rep = A.replica_base + (uint32_t)rb;
@@ -593,6 +601,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
   if (ff)
     for (int e = tid; e < 8 + ((s + 31) >> 5); e += T) sLive[e] = e == 4 ? 0xFFFFFFFFu : 0u;
+  if (B == 1 && tid < NWB) sDrawT[tid] = 0;
   __syncthreads();
 
   int64_t Eoff = 0;
@@ -739,9 +748,27 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (__any_sync(kFull, need)) {
           if (ff && lane == 0) sLive[t & 3u] = t;
           const int p = k * Tw + tid;
-          uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
-          philox10(c, k0, k1);
-          const uint32_t w = word_of(c, p & 3);
+          uint32_t w;
+          if (B == 1) {
+            const uint32_t t0 = sDrawT[warp];
+            if (t0 == 0u || t - t0 >= 4u) {
+              uint32_t c[4] = {(uint32_t)(warp * 8 + (lane & 7)), t + (uint32_t)(lane >> 3), rep,
+                               kTagAccept};
+              philox10(c, k0, k1);
+              sDraw[warp * 32 + lane] = make_uint4(c[0], c[1], c[2], c[3]);
+              __syncwarp();
+              if (lane == 0) sDrawT[warp] = t;
+              w = reinterpret_cast<const uint32_t *>(sDraw)[(warp * 32 + (lane >> 2)) * 4 + (lane & 3)];
+            } else {
+              w = reinterpret_cast<const uint32_t *>(
+                  sDraw)[(warp * 32 + (int)(t - t0) * 8 + (lane >> 2)) * 4 + (lane & 3)];
+            }
+            __syncwarp();
+          } else {
+            uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
+            philox10(c, k0, k1);
+            w = word_of(c, p & 3);
+          }
           if (need) acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
         }
         if (acc && de_smem) {

@@ -687,6 +687,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       // ---- workers: the parallel trial of their bits --------------------
       const double delta = cur_delta;
       const pen_t lo = cur_lo, hi = cur_hi;
+      // 2 <= B <= 4: this lane's acceptance Philox block of the iteration
+      bool drawn = false;
+      uint32_t dc[4];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const dE_t e1 = D1[k], e2 = D2[k];
@@ -764,6 +767,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                   sDraw)[(warp * 32 + (int)(t - t0) * 8 + (lane >> 2)) * 4 + (lane & 3)];
             }
             __syncwarp();
+          } else if (B <= 4) {
+            // The warp's bits of round k form 8 groups, so one block per
+            // lane covers every round: lane l computes group l % 8 of round
+            // l / 8 (once per iteration), and bit lane l of round k takes
+            // word l % 4 from lane 8k + l / 4.
+            if (!drawn) {
+              const uint32_t kk = (uint32_t)(lane >> 3);
+              dc[0] = (kk * (uint32_t)Tw + (uint32_t)warp * 32u) / 4u + (uint32_t)(lane & 7);
+              dc[1] = t;
+              dc[2] = rep;
+              dc[3] = kTagAccept;
+              philox10(dc, k0, k1);
+              drawn = true;
+            }
+            const int src = k * 8 + (lane >> 2);
+            const uint32_t v0 = __shfl_sync(kFull, dc[0], src), v1 = __shfl_sync(kFull, dc[1], src),
+                           v2 = __shfl_sync(kFull, dc[2], src), v3 = __shfl_sync(kFull, dc[3], src);
+            const int wi = lane & 3;
+            w = wi == 0 ? v0 : wi == 1 ? v1 : wi == 2 ? v2 : v3;
           } else {
             uint32_t c[4] = {(uint32_t)p >> 2, t, rep, kTagAccept};
             philox10(c, k0, k1);

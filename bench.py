@@ -44,8 +44,8 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one annealing launch, from one ncu capture
 # of the default workload (profiles/anneal_kernel_P25_dram.md), valid only
 # for the kernel sources it was taken on (their SHA-256 below).
-KERNEL_TRAFFIC = {"workload": "P25", "sha256": "b4019b2204a8e450c6ab044077f0249de625f3dacfed09f9b6a5328fad3d9b14",
-                  "bytes": 11127799296 + 893649664}
+KERNEL_TRAFFIC = {"workload": "P25", "sha256": "fa54632434b9b67ee3c2b28dca07c3c9a22ce445a60309147c208e046c7f9935",
+                  "bytes": 10880991232 + 890554880}
 
 
 def kernel_sources_sha256() -> str:

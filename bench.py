@@ -90,6 +90,8 @@ def parse_args(argv=None):
     ap.add_argument("--field-cache", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--autotune", action="store_true",
                     help="pick block shape and prefetch distance by timed trials first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="BATCH: keep the default block shapes (tuned per instance size otherwise)")
     ap.add_argument("--normalize", action="store_true",
                     help="QUBO normalisation (Sec. 4.2) in the acceptance test")
     ap.add_argument("--I-max", dest="I_max", type=int, default=None,
@@ -274,6 +276,19 @@ def run_batch(args):
     warm = [moda.make_params(replicas=32, I_max=min(I_max, 1000), seed=k)
             for k in range(len(qis))]
     stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if not args.no_autotune:  # untimed: one tuning per instance size, shared by its instances
+        t0 = time.perf_counter()
+        by_n = {}
+        for q, inst, p, pw in zip(qis, insts, params, warm):
+            if q.n not in by_n:
+                best, _ = moda.autotune(inst, params=p, trial_iters=1000, stream=stream)
+                by_n[q.n] = (best.block_threads, best.prefetch)
+            for pp in (p, pw):
+                pp.block_threads, pp.prefetch = by_n[q.n]
+        tuned = {"sizes": len(by_n), "tuning_s": time.perf_counter() - t0,
+                 "trial_iters": 1000,
+                 "shapes": {str(n): list(v) for n, v in sorted(by_n.items())}}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def batch(ps, subset=None):
@@ -338,7 +353,8 @@ def run_batch(args):
                    "instances": len(qis), "replicas_each": 32, "I_max": I_max,
                    "mean_bits": statistics.mean(n * n for n in ns),
                    "warmup_I_max": min(I_max, 1000),
-                   "l2": "flushed between timed steps (512 MiB write)"},
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   **({"autotuned": tuned} if tuned else {})},
         "bit_trials_per_s": value * statistics.mean(n * n for n in ns),
         "vs_sequential": {"instances": k, "batched_ms": sub_ms, "sequential_ms": seq_ms,
                           "speedup": seq_ms / sub_ms},

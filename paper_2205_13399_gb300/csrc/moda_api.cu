@@ -941,7 +941,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     const Prepared &pl = pls[i];
     cudaGraphNode_t n0, n1, n2, n3;
     const void *func = nullptr;
-    e = moda::anneal_function(pl.rounds, pl.narrow, moda::kernel_mode(pl.args), pl.smem,
+    e = moda::anneal_function(pl.rounds, pl.narrow, moda::kernel_mode(pl.args, pl.rounds), pl.smem,
                               &func);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, r->start);
     if (e == cudaSuccess) {

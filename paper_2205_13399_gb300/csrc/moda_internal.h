@@ -23,7 +23,8 @@ enum : uint32_t { kTagAccept = 0, kTagSelect = 1, kTagRestart = 2,
                   kTagExploit = 3, kTagInit = 4 };
 
 // Device status codes written to AnnealArgs::error.
-enum : int32_t { kErrNone = 0, kErrCopyTimeout = 1 };
+// kErrVariant: a kernel variant was launched for a run it does not fit.
+enum : int32_t { kErrNone = 0, kErrCopyTimeout = 1, kErrVariant = 2 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) {
   return (v + a - 1) / a * a;
@@ -179,10 +180,22 @@ inline bool uses_extensions(const AnnealArgs &a) {
   return a.normalize != 0 || a.snap_every > 0;
 }
 
-// Kernel variant of a launch: 0 plain, 1 with the extensions, 2 with the
-// fast-forward bookkeeping (never together with an extension).
-inline int kernel_mode(const AnnealArgs &a) {
-  return uses_extensions(a) ? 1 : a.fast_forward ? 2 : 0;
+// Kernel variant of a launch with `rounds` bits per thread: 1 with the
+// extensions, 2 with the fast-forward bookkeeping (never together with an
+// extension), 3 the default algorithm (strict acceptance, Alg. 4 archive,
+// archive escape, no trace) compiled in, 4 that and the on-chip placement
+// (one bit per thread, field cache with prefetch distance 1, archive and
+// published Delta E in shared memory), else 0.
+inline int kernel_mode(const AnnealArgs &a, int rounds) {
+  if (uses_extensions(a)) return 1;
+  if (a.fast_forward) return 2;
+  if (a.accept == 0 && a.archive == 0 && a.escape == 0 && a.trace == nullptr) {
+    if (rounds == 1 && a.lookahead == 1 && a.de_in_smem && a.energies_in_smem &&
+        a.bits_in_smem && a.fcache != nullptr)
+      return 4;
+    return 3;
+  }
+  return 0;
 }
 
 // Bits per thread the kernel is instantiated for.
@@ -199,6 +212,13 @@ cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
 // argument.
 cudaError_t anneal_function(int rounds, bool narrow, int mode, size_t smem,
                             const void **func);
+
+// Modes 2 to 4 of launch_anneal and anneal_function (a second translation
+// unit, moda_kernel_special.cu).
+cudaError_t launch_anneal_special(const AnnealArgs &args, int replicas, int workers, int rounds,
+                                  bool narrow, int mode, size_t smem, cudaStream_t stream);
+cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t smem,
+                                    const void **func);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);

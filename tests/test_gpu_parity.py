@@ -270,3 +270,26 @@ def test_autotune_picks_a_layout_with_identical_results():
     for key in ("count", "E", "bits", "x", "E_final"):
         assert np.array_equal(getattr(a, key), getattr(b, key)), key
     assert np.array_equal(a.stats[:, :4], b.stats[:, :4])
+
+
+@pytest.mark.parametrize("n,bt,kw", [(25, 0, {}), (25, 0, dict(prefetch=1)), (25, 0, dict(prefetch=3)),
+                                     (25, 0, dict(field_cache="off")), (25, 320, {}),
+                                     (40, 0, {}), (50, 0, {}), (75, 0, {})])
+def test_default_algorithm_variants_equal_general_kernel(n, bt, kw):
+    """Runs of the default algorithm (strict, Alg. 4, archive escape) take
+    kernel variants with those settings compiled in -- and, with one bit per
+    thread and the on-chip placement, the placement too.  A traced run takes
+    the general variant; both must give the same archives, states, energies
+    and counters."""
+    inst = inputs.euclid_instance(n, -0.5, n >= 50, index=n, workload="P25")
+    run = dict(replicas=6, I_max=4000, seed=21, **FAST)
+    _, _, fast, _ = gpu_run(inst, block_threads=bt, **run, **kw)
+    _, _, gen, _ = gpu_run(inst, block_threads=bt, trace=True, **run, **kw)
+    assert np.array_equal(fast.count, gen.count)
+    for r in range(6):
+        c = int(gen.count[r])
+        assert np.array_equal(fast.E[r, :c], gen.E[r, :c]), r
+        assert np.array_equal(fast.bits[r, :c], gen.bits[r, :c]), r
+    assert np.array_equal(fast.x, gen.x)
+    assert np.array_equal(fast.E_final, gen.E_final)
+    assert np.array_equal(fast.stats[:, :4], gen.stats[:, :4])

@@ -304,3 +304,64 @@ def test_snapshots_are_prefix_archives():
             c = int(part["count"][r])
             assert np.array_equal(snap["E"][r, j, :c], part["E"][r, :c])
             assert np.array_equal(snap["bits"][r, j, :c], part["bits"][r, :c])
+
+
+def test_settled_runs_end_on_the_last_restart_draw():
+    """The premise of the kernel's fast-forward, on the oracle alone.
+    hi_t = floor(delta_t T_max) never rises (the schedule only cools), so an
+    archive member none of whose bits has a strict penalty
+    a = max(0, dE_1) + max(0, dE_2) <= hi_t never accepts again.  Every jump
+    of Alg. 3 goes to pick(restart draw of t, |A|); once the archive stops
+    changing and all its members are so, the run ends on the member that
+    iteration I_max's draw picks."""
+    FAST = dict(delta0=2e6, deltaf=3e3, xi=0.02)
+    I_max, seed, R = 4000, 18, 3
+    sched = oracle.schedule(FAST["delta0"], FAST["deltaf"], FAST["xi"], I_max)
+    hi = np.floor(sched * oracle.neglog_table()[0])
+    assert np.all(np.diff(hi) <= 0)
+    inst = inputs.uniform_instance(7, index=7, workload="P8")
+    n, m = 7, 49
+    oi = oracle.Instance(inst.F1, inst.F2, inst.D)
+    out = oracle.run(oi, I_max=I_max, replicas=R, seed=seed, trace=True, **FAST)
+    w1, w2 = oi.w
+    F1, F2, D = (np.asarray(a, dtype=np.int64) for a in (inst.F1, inst.F2, inst.D))
+    Fs1, Fs2 = F1 + F1.T, F2 + F2.T
+
+    def min_penalty(bits):
+        X = np.asarray(bits, dtype=np.int64).reshape(n, n)
+        r, c, sg = X.sum(1), X.sum(0), 1 - 2 * X
+        h = sg * (-1 + (r[:, None] - X) + (c[None, :] - X))
+        e1 = np.maximum(sg * (Fs1 @ X @ D) + w1 * h, 0)
+        e2 = np.maximum(sg * (Fs2 @ X @ D) + w2 * h, 0)
+        return int((e1 + e2).min())
+
+    def restart_pick(t, rep, count):
+        u = int(oracle.philox([0, t, rep, 2], [seed, 0])[0])
+        return (u * count) >> 32
+
+    settled = 0
+    for rep in range(R):
+        tr = out["trace"][rep]
+        archive = []
+        for t in range(1, I_max + 1):
+            ev = int(tr[t - 1, 2])
+            if ev >= 0:
+                archive = oracle.archive_update("explore", m, archive, (int(tr[t - 1, 0]), int(tr[t - 1, 1])))
+            elif ev != np.iinfo(np.int64).min:
+                assert -1 - ev == restart_pick(t, rep, len(archive)), (rep, t)
+        count = int(out["count"][rep])
+        assert len(archive) == count
+        flips = np.nonzero(tr[:, 2] >= 0)[0]
+        t_last = int(flips[-1]) + 1 if len(flips) else 0
+        pens = [min_penalty(out["bits"][rep, y]) for y in range(count)]
+        none = np.iinfo(np.int64).min
+        # iterations whose trial is at a member (the previous one jumped)
+        # while every member's smallest penalty exceeds hi_t
+        dead_from = [t for t in range(max(t_last, 1) + 1, I_max + 1)
+                     if min(pens, default=0) > hi[t - 1] and none != tr[t - 2, 2] < 0]
+        if count and dead_from:
+            settled += 1
+            y = restart_pick(I_max, rep, count)
+            assert np.array_equal(out["E_final"][rep], out["E"][rep, y])
+            assert np.array_equal(out["x"][rep], out["bits"][rep, y])
+    assert settled >= 2

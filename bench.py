@@ -44,8 +44,8 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one annealing launch, from one ncu capture
 # of the default workload (profiles/anneal_kernel_P25_dram.md), valid only
 # for the kernel sources it was taken on (their SHA-256 below).
-KERNEL_TRAFFIC = {"workload": "P25", "sha256": "f7db2dad7d7b3f78847fa6881a8cd1f73f52a18cd008927c0238c7487ab65df2",
-                  "bytes": 10927260160 + 889903360}
+KERNEL_TRAFFIC = {"workload": "P25", "sha256": "8b43fbf52741c0322d1dd50fad8f5df8188cfd697740eb69e7b43a41c55d39e3",
+                  "bytes": 10926261248 + 889593344}
 
 
 def kernel_sources_sha256() -> str:

@@ -185,14 +185,16 @@ inline bool uses_extensions(const AnnealArgs &a) {
 // extension), 3 the default algorithm (strict acceptance, Alg. 4 archive,
 // archive escape, no trace) compiled in, 4 that and the on-chip placement
 // (one bit per thread, field cache with prefetch distance 1, archive and
-// published Delta E in shared memory), else 0.
+// published Delta E in shared memory), 5 the same placement with the
+// archive states in global memory (2 to 4 bits per thread), else 0.
 inline int kernel_mode(const AnnealArgs &a, int rounds) {
   if (uses_extensions(a)) return 1;
   if (a.fast_forward) return 2;
   if (a.accept == 0 && a.archive == 0 && a.escape == 0 && a.trace == nullptr) {
-    if (rounds == 1 && a.lookahead == 1 && a.de_in_smem && a.energies_in_smem &&
-        a.bits_in_smem && a.fcache != nullptr)
-      return 4;
+    if (a.lookahead == 1 && a.de_in_smem && a.energies_in_smem && a.fcache != nullptr) {
+      if (rounds == 1 && a.bits_in_smem) return 4;
+      if (rounds >= 2 && rounds <= 4 && !a.bits_in_smem) return 5;
+    }
     return 3;
   }
   return 0;

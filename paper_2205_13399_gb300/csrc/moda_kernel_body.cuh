@@ -341,20 +341,21 @@ struct JumpRec {
 // (Eq. pacceptms), the explorative archive (Alg. 4), the escape by a jump
 // to the archive, no trace.  MODE 4 (B = 1): MODE 3 and the on-chip
 // placement -- field cache on, prefetch distance 1, archive energies,
-// archive states and published Delta E in shared memory.  The host picks
-// MODE 3 and 4 only for matching runs; a block given other arguments
-// reports kErrVariant and does nothing.  MODE 0: none of these.
+// archive states and published Delta E in shared memory.  MODE 5
+// (2 <= B <= 4): the same with the archive states in global memory.  The
+// host picks MODE 3 to 5 only for matching runs; a block given other
+// arguments reports kErrVariant and does nothing.  MODE 0: none of these.
 template <int B, bool NARROW, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     anneal_kernel(const AnnealArgs A) {
   constexpr bool EXT = MODE == 1;
-  constexpr bool DEF = MODE >= 3, DEFPL = MODE == 4;
+  constexpr bool DEF = MODE >= 3, DEFPL = MODE == 4 || MODE == 5;
   if (DEF) {
     bool match = A.accept == 0 && A.archive == 0 && A.escape == 0 && A.trace == nullptr &&
                  A.normalize == 0 && A.snap_every == 0 && A.fast_forward == 0;
     if (DEFPL)
       match = match && A.lookahead == 1 && A.de_in_smem != 0 && A.energies_in_smem != 0 &&
-              A.bits_in_smem != 0 && A.fcache != nullptr;
+              (A.bits_in_smem != 0) == (MODE == 4) && A.fcache != nullptr;
     if (!match) {
       if (threadIdx.x == 0) atomicExch(A.error, kErrVariant);
       return;
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const int cLookahead = DEFPL ? 1 : A.lookahead;
   const bool cDeSmem = DEFPL || A.de_in_smem != 0;
   const bool cEnergiesSmem = DEFPL || A.energies_in_smem != 0;
-  const bool cBitsSmem = DEFPL || A.bits_in_smem != 0;
+  const bool cBitsSmem = MODE == 4 || (MODE != 5 && A.bits_in_smem != 0);
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
   using dE2_t = typename std::conditional<NARROW, int2, longlong2>::type;
   // acceptance penalty: a sum of two non-negative Delta E, so uint32 in

@@ -375,7 +375,9 @@ const char *moda_last_error(void);
  *   make that first call before any stream capture.
  *   Asynchrony: returns once the work is enqueued on cuda_stream; the
  *   outputs are ready when that stream reaches this point.  The error word
- *   is set to 0 by the call and to a nonzero code by a device-side failure.
+ *   is set to 0 by the call and to a nonzero code by a device-side failure:
+ *   1 when a bounded wait for a field-cache copy gave up, 2 when a kernel
+ *   variant was launched for a run it does not fit (an internal error).
  */
 typedef struct {
   int64_t *arch_E;      /* [replicas][s][2] archive energies */

@@ -698,8 +698,12 @@ moda_status moda_wait(moda_run r, int64_t timeout_ms) {
   if (!r->checked) {
     int32_t err = 0;
     MODA_CUDA(cudaMemcpy(&err, r->error, sizeof(err), cudaMemcpyDeviceToHost));
-    if (err != 0) return fail(MODA_ECUDA, "device-side check failed: code " +
-                                              std::to_string(err));
+    if (err != 0)
+      return fail(MODA_ECUDA,
+                  "device-side check failed: code " + std::to_string(err) +
+                      (err == moda::kErrCopyTimeout ? " (a bounded wait for a field-cache copy gave up)"
+                       : err == moda::kErrVariant   ? " (kernel variant launched for a run it does not fit)"
+                                                    : ""));
     r->checked = true;
   }
   return MODA_OK;

@@ -145,3 +145,22 @@ def test_qubo_null_arguments(lib):
     lib.moda_qubo_destroy(None)
     lib.moda_qrun_destroy.restype = None
     lib.moda_qrun_destroy(None)
+
+
+def test_kernel_variant_choice(tmp_path):
+    """The host picks the kernel variants with the default algorithm or the
+    placement compiled in only for runs that match them (a host-only C++
+    check of moda::kernel_mode against the library's internal header)."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if gxx is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    here = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(os.path.dirname(here), "paper_2205_13399_gb300", "csrc")
+    exe = str(tmp_path / "kernel_mode_check")
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", csrc, "-I", cuda_inc,
+                    os.path.join(here, "kernel_mode_check.cc"), "-o", exe], check=True)
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout

@@ -362,17 +362,22 @@ const char *moda_last_error(void);
  * cooling schedule and the -ln(u) table live in fixed-size device arrays of
  * the library, held by every GPU that loads it until the process exits.
  *
- *   Limits (MODA_EUNSUPPORTED beyond them): n <= 128; replicas * s *
- *   12 * ceil8(n^2) bytes <= 64 MiB (s = archive size); at most 65,536
- *   schedule entries before delta reaches delta_f; params.trace = 0.
+ *   Limits (MODA_EUNSUPPORTED beyond them): n <= 128; with the archive
+ *   escape, replicas * s * r * ceil8(n^2) bytes <= 64 MiB (s = archive
+ *   size; r = 8 when every |Delta E_k| of the instance stays below 2^31,
+ *   i.e. B_k + w_k (2n + 1) < 2^31 with B_k the bound of moda_create_instance,
+ *   else 16); the offset escape uses no scratch; at most 65,536 schedule
+ *   entries before delta reaches delta_f; params.trace = 0.
  *   params.field_cache and params.prefetch are ignored (the cache is used
  *   whenever the escape jumps to the archive).
  *   Shared state: all calls share the library's arrays; two calls whose
  *   device work overlaps (other streams or host threads) race and give
  *   wrong results.  Serialise them, e.g. on one stream.
  *   Set-up: the first call on a device (the device current on the calling
- *   thread) looks up the arrays' device addresses and uploads the table;
- *   make that first call before any stream capture.
+ *   thread) looks up the arrays' device addresses and uploads the table.
+ *   Capture: no call may be made while cuda_stream is being captured into
+ *   a CUDA graph (MODA_EUNSUPPORTED): each call stages its instance and
+ *   schedule in host arrays that the next call overwrites.
  *   Asynchrony: returns once the work is enqueued on cuda_stream; the
  *   outputs are ready when that stream reaches this point.  The error word
  *   is set to 0 by the call and to a nonzero code by a device-side failure:

@@ -208,8 +208,8 @@ cudaError_t launch_anneal(const AnnealArgs &args, int replicas, int workers,
                           int rounds, bool narrow, size_t smem_bytes,
                           cudaStream_t stream);
 
-// The kernel for `rounds` bits per thread (one block of workers + 32
-// threads per replica, `smem` bytes of dynamic shared memory, which this
+// The kernel for `rounds` bits per thread (one block of workers + 64
+// threads, two control warps, per replica, `smem` bytes of dynamic shared memory, which this
 // call allows), for launching from a CUDA graph node with one AnnealArgs
 // argument.
 cudaError_t anneal_function(int rounds, bool narrow, int mode, size_t smem,

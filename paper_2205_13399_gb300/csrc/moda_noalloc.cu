@@ -10,9 +10,11 @@
 // instance's matrices -- lives in file-scope device arrays of fixed size,
 // which every GPU that loads this library holds until the process exits.
 //
-// Limits: n <= 128; replicas * s * (field-cache record of m bits) <=
-// kScratchBytes (64 MiB); at most kSchedMax schedule entries before the
-// temperature reaches delta_f.
+// Limits: n <= 128; with the archive escape, replicas * s * r * ceil8(m)
+// <= kScratchBytes (64 MiB), r = 8 bytes per bit when every |Delta E_k|
+// stays below 2^31 and 16 otherwise (the field-cache record of one archive
+// slot); at most kSchedMax schedule entries before the temperature reaches
+// delta_f.  No call may be made while its stream is being captured.
 //
 // The arrays are shared by every call: two calls whose device work
 // overlaps (different streams, or different host threads) race on them and
@@ -22,7 +24,7 @@
 //
 // Set-up: the first call on a device, with that device current, looks up
 // the device address of each array (cudaGetSymbolAddress) and uploads the
-// -ln(u) table; make that first call before any stream capture.
+// -ln(u) table.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -208,11 +210,13 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
     return nofail(MODA_ECUDA, "device attribute query failed");
   const bool narrow = moda::narrow_ok(n, f1max * dmax, f2max * dmax, w1, w2);
   const size_t rec = moda::slot_layout(m, narrow).bytes;
-  if ((size_t)p->replicas * (size_t)s * rec > kScratchBytes)
+  // The field cache (the only user of the scratch array) serves jumps to
+  // the archive; runs with the offset escape never touch the scratch.
+  const bool cache = p->escape == MODA_ESC_ARCHIVE;
+  if (cache && (size_t)p->replicas * (size_t)s * rec > kScratchBytes)
     return nofail(MODA_EUNSUPPORTED,
                   "replicas * archive slots * field record exceed the 64 MiB scratch array");
   // Shared-memory placement with the field cache on (escape by jumps) or off.
-  const bool cache = p->escape == MODA_ESC_ARCHIVE;
   moda::Placement place{};
   moda::SmemLayout lay{};
   bool placed = false;
@@ -247,6 +251,16 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
     }
   }
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // The uploads below read the static host staging arrays, which the
+    // next call overwrites: a captured call would replay another call's
+    // instance and schedule, so no call may be captured.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess)
+      return nofail(MODA_ECUDA, "cudaStreamIsCapturing failed");
+    if (cs != cudaStreamCaptureStatusNone)
+      return nofail(MODA_EUNSUPPORTED, "moda_anneal_noalloc cannot be captured into a graph");
+  }
   const size_t nn4 = sizeof(int32_t) * (size_t)m;
   cudaError_t e = cudaMemcpyAsync(S->fs1, fs1, nn4, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->fs2, fs2, nn4, cudaMemcpyHostToDevice, stream);

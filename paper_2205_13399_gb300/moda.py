@@ -374,6 +374,21 @@ def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, strea
     n = int(D.shape[0])
     F1 = np.ascontiguousarray(np.asarray(F1, dtype=np.int16))
     F2 = np.ascontiguousarray(np.asarray(F2, dtype=np.int16))
+    if D.shape != (n, n) or F1.shape != (n, n) or F2.shape != (n, n):
+        raise ValueError("F1, F2 and D must all be n x n")
+    # The C ABI cannot see buffer sizes: check those of tensor outputs here
+    # (bytes as documented in include/moda.h; int addresses are trusted).
+    m = n * n
+    W = (m + 31) // 32
+    R = int(params.replicas)
+    s = int(params.archive_size) if params.archive_size > 0 else m
+    need = {"arch_E": R * s * 16, "arch_bits": R * s * W * 4 + 32, "arch_count": R * 4,
+            "x_final": R * W * 4, "E_final": R * 16, "stats": R * 8 * 8, "error": 4}
+    for k, v in outputs.items():
+        if not isinstance(v, int) and k in need:
+            have = int(v.numel()) * int(v.element_size())
+            if have < need[k]:
+                raise ValueError(f"output {k} holds {have} bytes, needs {need[k]}")
     addr = {k: (v if isinstance(v, int) else int(v.data_ptr())) for k, v in outputs.items()}
     out = DeviceOutputs(addr["arch_E"], addr["arch_bits"], addr["arch_count"], addr["x_final"],
                         addr["E_final"], addr["stats"], addr["error"])

@@ -63,3 +63,27 @@ def compare(gpu_res, gpu_rows, orc, m, gpu_trace=None):
         assert np.array_equal(unpack_bits(gpu_res.x[g], m), orc["x"][k]), f"final state, row {g}"
         assert np.array_equal(gpu_res.E_final[g], orc["E_final"][k]), f"final energies, row {g}"
         assert np.array_equal(gpu_res.stats[g, :4], orc["stats"][k]), f"counters, row {g}"
+
+
+def oracle_merged_front(oi, orc):
+    """The result of Alg. 3 over all replicas (its last line, and Sec. 4.2's
+    merge of runs): the non-dominated members of the union of the oracle's
+    replica archives, taken in (replica, slot) order so that among equal
+    energy vectors the lowest (replica, slot) is kept (reading R16).  Each
+    point carries its penalised energies, QAP costs, constraint value,
+    feasibility, origin and decoded permutation, sorted by (E1, E2) as
+    moda_read_archive returns them."""
+    pts, where = [], []
+    for k in range(len(orc["count"])):
+        for slot in range(int(orc["count"][k])):
+            pts.append((int(orc["E"][k, slot, 0]), int(orc["E"][k, slot, 1])))
+            where.append((k, slot))
+    out = []
+    for i in oracle.nondominated(pts):
+        k, slot = where[i]
+        x = orc["bits"][k, slot]
+        g = oi.constraint(x)
+        out.append(dict(E1=pts[i][0], E2=pts[i][1], c1=oi.cost(0, x), c2=oi.cost(1, x), g=g,
+                        feasible=g == 0, replica=k, slot=slot,
+                        perm=oracle.decode_permutation(x) if g == 0 else None))
+    return sorted(out, key=lambda d: (d["E1"], d["E2"]))

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2205_13399_gb300 import inputs
-from parity import compare, gpu_run, oracle_run
+from parity import compare, gpu_run, oracle_merged_front, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -82,13 +82,43 @@ def test_penalty_matches_oracle():
 
 def test_p8_full_config():
     """n = 8 workload at its full size: 16 replicas, I_max = 10^4, the paper's
-    schedule (delta0 = 1e9, deltaf = 1e4, xi = 1e-3)."""
+    schedule (delta0 = 1e9, deltaf = 1e4, xi = 1e-3).  Besides every
+    replica's archive, the merged front over all replicas (Alg. 3's result,
+    moda_read_archive with r = -1) equals the oracle's, point for point, and
+    every feasible point lies on or above the exact Pareto front."""
     inst = inputs.workload_instance("P8")
     run = inputs.WORKLOAD_RUN["P8"]
-    _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=run["I_max"], seed=run["seed"])
-    _, orc = oracle_run(inst, replicas=range(run["replicas"]), I_max=run["I_max"],
-                        seed=run["seed"])
+    _, grun, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=run["I_max"],
+                              seed=run["seed"])
+    oi, orc = oracle_run(inst, replicas=range(run["replicas"]), I_max=run["I_max"],
+                         seed=run["seed"])
     compare(res, range(run["replicas"]), orc, 64)
+    front = grun.read_archive(-1)
+    assert front == oracle_merged_front(oi, orc)
+    exact = oracle.pareto_front_bruteforce(inst.F1, inst.F2, inst.D)
+    feasible = [p for p in front if p["feasible"]]
+    assert feasible
+    for p in feasible:
+        assert any(a <= p["c1"] and b <= p["c2"] for a, b in exact), p
+        assert p["c1"] == oracle.qap_cost(inst.F1, inst.D, p["perm"])
+        assert p["c2"] == oracle.qap_cost(inst.F2, inst.D, p["perm"])
+
+
+@pytest.mark.parametrize("n,acc,arc", [(7, "lenient", "exploit"), (7, "strict", "explore"),
+                                       (13, "lenient", "explore"), (13, "strict", "exploit")])
+def test_merged_front_matches_oracle(n, acc, arc):
+    """The merged non-dominated front over several replicas (the tie rule
+    of reading R16 included) on ragged sizes under both acceptance rules
+    and both archive updates, against the oracle's merge of its own
+    replica archives."""
+    inst = inputs.uniform_instance(n, index=200 + n, workload="P8")
+    kw = dict(replicas=6, I_max=3000, seed=31 + n, accept=acc, archive=arc, **FAST)
+    _, grun, res, _ = gpu_run(inst, **kw)
+    oi, orc = oracle_run(inst, **kw)
+    compare(res, range(6), orc, n * n)
+    front = grun.read_archive(-1)
+    assert front == oracle_merged_front(oi, orc)
+    assert len({p["replica"] for p in front}) >= 1
 
 
 def test_p25_full_config_sampled_replicas():

@@ -72,12 +72,47 @@ def test_noalloc_matches_anneal_twice():
 
 
 def test_noalloc_rejects_oversized_scratch():
+    """Runs whose field cache would not fit the 64 MiB scratch array are
+    refused; the same run with the offset escape, which uses no scratch,
+    is not.  Real output buffers are passed, so nothing could be written
+    out of bounds even if a check were missing."""
+    torch = pytest.importorskip("torch")
     from paper_2205_13399_gb300 import moda
     inst = inputs.workload_instance("P25")
-    fake = {k: 16 for k in ("arch_E", "arch_bits", "arch_count", "x_final", "E_final",
-                            "stats", "error")}
+    m, W, R = 625, 20, 128
+    bufs = _buffers(torch, R, m, W)
     with pytest.raises(moda.MODAError) as ei:
-        # 128 replicas x 625 slots x 7.5 KB records > 64 MiB
-        moda.anneal_noalloc(inst.F1, inst.F2, inst.D, fake, replicas=128, I_max=10)
+        # 128 replicas x 625 slots x 8 bytes x 632 bits (about 5 KB per
+        # record, the int32 Delta E variant) = 405 MB > 64 MiB
+        moda.anneal_noalloc(inst.F1, inst.F2, inst.D, bufs, replicas=R, I_max=10)
     assert ei.value.status == moda.EUNSUPPORTED
     assert "64 MiB" in str(ei.value)
+    stream = torch.cuda.current_stream()
+    moda.anneal_noalloc(inst.F1, inst.F2, inst.D, bufs, stream=stream, replicas=R, I_max=10,
+                        escape="offset")
+    stream.synchronize()
+    assert int(bufs["error"].item()) == 0
+    assert int(bufs["stats"].view(R, 8)[:, :4].sum().item()) == R * 10
+
+
+def test_noalloc_refuses_stream_capture():
+    """A call made while its stream is captured into a CUDA graph is
+    refused: the call stages its instance in host arrays that the next call
+    overwrites, so a replayed graph would anneal another call's instance."""
+    torch = pytest.importorskip("torch")
+    from paper_2205_13399_gb300 import moda
+    inst = inputs.uniform_instance(6, index=6, workload="P8")
+    bufs = _buffers(torch, 2, 36, 2)
+    side = torch.cuda.Stream()
+    x = torch.zeros(1, device=bufs["error"].device)
+    g = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(g, stream=side):
+        x.add_(1)
+        try:
+            moda.anneal_noalloc(inst.F1, inst.F2, inst.D, bufs, stream=side, replicas=2,
+                                I_max=100, **FAST)
+        except moda.MODAError as e:
+            err = e
+    assert err is not None and err.status == moda.EUNSUPPORTED
+    assert "captured" in str(err)

@@ -88,6 +88,8 @@ def parse_args(argv=None):
     ap.add_argument("--prefetch", type=int, default=0,
                     help="field-cache prefetch distance + 1 (0: automatic)")
     ap.add_argument("--field-cache", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "block", "warp"],
+                    help="one thread block or one warp per replica (auto: warp when possible)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick block shape and prefetch distance by timed trials first")
     ap.add_argument("--no-autotune", action="store_true",
@@ -696,7 +698,7 @@ def main(argv=None):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(replicas=R, replica_base=base, I_max=I_max, seed=run["seed"],
               block_threads=args.block_threads, prefetch=args.prefetch,
-              field_cache=args.field_cache, normalize=args.normalize)
+              field_cache=args.field_cache, normalize=args.normalize, engine=args.engine)
     tuned = None
     if args.autotune:  # untimed: trials on the cold end of the schedule
         best, trial_ms = moda.autotune(g, **kw)
@@ -740,7 +742,8 @@ def main(argv=None):
         for k in range(args.warmup + args.steps):
             flush.zero_()
             torch.cuda.synchronize()
-            r = moda.anneal(g, stream=stream, fast_forward=True, **kw).wait()
+            r = moda.anneal(g, stream=stream, fast_forward=True,
+                            **{**kw, "engine": "block"}).wait()
             if k >= args.warmup:
                 ff_ms.append(r.elapsed_ms())
                 skipped += int(r.read().stats[:, 6].sum())

@@ -138,6 +138,23 @@ typedef struct {
                             counters, trace and final state are those of the
                             full run; stats[6] counts the iterations not
                             executed.  0: every iteration runs (default). */
+  int32_t engine;        /* which kernel runs the replicas; results are
+                            identical:
+                            1 block: one thread block per replica (all
+                              options; lowest latency per iteration);
+                            2 warp: one warp per replica, replicas of many
+                              runs pulled from one device work list (the
+                              archive escape only, without normalize,
+                              snapshot_every or fast_forward;
+                              MODA_EUNSUPPORTED otherwise).  Its field cache
+                              holds min(s, 1024) slots per resident warp by
+                              default (field_cache = 1: all s slots; 2:
+                              none); a jump to a slot without records
+                              rebuilds its fields.  prefetch k in 1..3 copies
+                              a jump's target k - 1 iterations ahead (0:
+                              auto, 2 iterations).
+                            0 auto: warp when the options allow it and
+                              block_threads is 0, else block. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */

@@ -194,18 +194,70 @@ struct moda_run_s {
   int32_t *snap_count = nullptr;
   int64_t *snap_E = nullptr;
   uint32_t *snap_bits = nullptr;
+  bool warp = false;  // run by the warp annealer
+  // the warp-annealer launch's shared device buffers (work list, field
+  // caches), freed with the last run of that launch
+  std::shared_ptr<struct WarpScratch> wscratch;
 };
 
 namespace {
 
-void free_run_buffers(moda_run r) {
+// Device memory of runs comes from the stream-ordered allocator: it is
+// allocated on the stream that uses it and given back with cudaFreeAsync,
+// which (unlike cudaFree) does not wait for every kernel on the device, so
+// retiring one run never stalls the others.  The default pool of each
+// device keeps freed memory for reuse.
+std::mutex g_pool_mutex;
+std::map<int, cudaStream_t> g_free_streams;
+
+// Per device: a library stream for frees of finished runs, and the pool
+// set to keep its memory.
+cudaStream_t free_stream(int dev) {
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  auto it = g_free_streams.find(dev);
+  if (it != g_free_streams.end()) return it->second;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  g_free_streams[dev] = st;
+  return st;
+}
+
+// Free device memory including what the pool holds unused.
+cudaError_t free_memory(int dev, size_t *free_b) {
+  size_t f = 0, total = 0;
+  cudaError_t e = cudaMemGetInfo(&f, &total);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) ==
+            cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+        reserved > used)
+      f += (size_t)(reserved - used);
+  }
+  *free_b = f;
+  return cudaSuccess;
+}
+
+// `done`: the run's work has finished (or never started), so the memory
+// may go back on the library's stream; otherwise it is freed in the order
+// of the run's own stream.
+void free_run_buffers(moda_run r, bool done = false) {
   void *ptrs[] = {r->arch_E, r->arch_bits, r->arch_count, r->x_final,
                   r->E_final, r->stats, r->trace, r->error, r->fcache,
                   r->snap_count, r->snap_E, r->snap_bits};
+  cudaStream_t fs = done ? free_stream(r->inst->device) : r->stream;
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, fs);
   if (r->start) cudaEventDestroy(r->start);
   if (r->stop) cudaEventDestroy(r->stop);
+  r->wscratch.reset();
 }
 
 bool run_done(moda_run r) { return cudaEventQuery(r->stop) == cudaSuccess; }
@@ -216,7 +268,39 @@ struct Prepared {
   int workers, rounds;
   bool narrow;
   size_t smem;
+  moda::WarpRun wrun;  // the warp annealer's view of the run (r->warp)
 };
+
+// The device buffers one warp-annealer launch shares among its runs.
+}  // namespace
+struct WarpScratch {
+  int device = 0;
+  void *list = nullptr;   // run descriptors, work items, item counter
+  void *cache = nullptr;  // field caches of the resident warps
+  ~WarpScratch() {
+    cudaStream_t fs = free_stream(device);
+    if (list) cudaFreeAsync(list, fs);
+    if (cache) cudaFreeAsync(cache, fs);
+  }
+};
+namespace {
+
+// Options the warp annealer runs: the archive escape, without
+// normalisation, snapshots or fast-forward.
+bool warp_options(const moda_params *p) {
+  return p->escape == MODA_ESC_ARCHIVE && p->normalize == 0 && p->snapshot_every == 0 &&
+         p->fast_forward == 0;
+}
+
+// Whether prepare_run gives a request to the warp annealer.
+bool uses_warp(const moda_params *p) {
+  return p->engine == 2 || (p->engine == 0 && warp_options(p) && p->block_threads == 0);
+}
+
+// Archive slots with field-cache records per resident warp by default.
+constexpr int kWarpCacheSlots = 1024;
+// Archive energies kept in shared memory per warp, at most.
+constexpr int kWarpSmemEnergies = 512;
 
 }  // namespace
 
@@ -387,6 +471,102 @@ moda_status moda_instance_info(moda_instance inst, int32_t *n, int64_t *w1,
 
 namespace {
 
+// The warp annealer's part of prepare_run: validated params, the run's
+// buffers, and its WarpRun descriptor (field-cache slots, on-chip archive
+// energies and the work list are settled when the launch is planned).
+moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStream_t stream,
+                             moda_run *out, Prepared *pl) {
+  const int m = inst->m;
+  if (p->field_cache < 0 || p->field_cache > 2)
+    return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
+  if (p->prefetch < 0 || p->prefetch > moda::kWarpMaxLA + 1)
+    return fail(MODA_EINVAL, "prefetch must be in [0, 3] for the warp engine");
+  if (p->block_threads != 0)
+    return fail(MODA_EINVAL, "block_threads applies to the block engine only");
+  cudaSetDevice(inst->device);
+  moda_run r = new (std::nothrow) moda_run_s;
+  if (!r) return fail(MODA_ENOMEM, "host allocation");
+  r->inst = inst;
+  r->prm = *p;
+  r->R = p->replicas;
+  r->s = p->archive_size > 0 ? p->archive_size : m;
+  r->stream = stream;
+  r->warp = true;
+  const size_t R = r->R, s = r->s, W = inst->W;
+  moda_status st = MODA_OK;
+  size_t bytes = 0;
+  auto alloc = [&](void **ptr, size_t nb) {
+    if (st != MODA_OK) return;
+    bytes += nb;
+    cudaError_t e = cudaMallocAsync(ptr, nb, stream);
+    if (e != cudaSuccess)
+      st = fail(MODA_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+  };
+  alloc((void **)&r->arch_E, R * s * 2 * sizeof(int64_t));
+  alloc((void **)&r->arch_bits, R * s * W * sizeof(uint32_t) + 32);
+  alloc((void **)&r->arch_count, R * sizeof(int32_t));
+  alloc((void **)&r->x_final, R * W * sizeof(uint32_t));
+  alloc((void **)&r->E_final, R * 2 * sizeof(int64_t));
+  alloc((void **)&r->stats, R * moda::kStats * sizeof(int64_t));
+  alloc((void **)&r->error, sizeof(int32_t));
+  if (p->trace && p->I_max > 0)
+    alloc((void **)&r->trace, R * (size_t)p->I_max * 3 * sizeof(int64_t));
+  DeviceData *dd = nullptr;
+  DeviceData::Sched sch;
+  if (st == MODA_OK) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    st = device_table(inst->device, &dd);
+    if (st == MODA_OK) st = device_schedule(*dd, p->delta0, p->deltaf, p->xi, p->I_max, &sch);
+  }
+  if (st == MODA_OK) {
+    cudaError_t e = cudaEventCreate(&r->start);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->stop);
+    if (e != cudaSuccess) st = cuda_fail(e, "event");
+  }
+  if (st != MODA_OK) {
+    free_run_buffers(r);
+    delete r;
+    return st;
+  }
+  moda::WarpRun w{};
+  w.n = inst->n;
+  w.m = m;
+  w.W = inst->W;
+  w.s = r->s;
+  w.narrow = moda::narrow_ok(inst->n, inst->b1, inst->b2, inst->w1, inst->w2) ? 1 : 0;
+  w.accept = p->accept;
+  w.archive = p->archive;
+  w.nsched = sch.count;
+  w.replicas = p->replicas;
+  w.replica_base = (uint32_t)p->replica_base;
+  w.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
+  w.seed_hi = (uint32_t)(p->seed >> 32);
+  w.magic = (uint32_t)(0xFFFFFFFFu / (uint32_t)inst->n) + 1u;
+  w.I_max = p->I_max;
+  w.w1 = inst->w1;
+  w.w2 = inst->w2;
+  w.sch_delta = sch.delta;
+  w.sch_lo = sch.lo;
+  w.sch_hi = sch.hi;
+  w.table = dd->table;
+  w.Fs1 = inst->dFs1;
+  w.Fs2 = inst->dFs2;
+  w.D = inst->dD;
+  w.arch_E = r->arch_E;
+  w.arch_bits = r->arch_bits;
+  w.arch_count = r->arch_count;
+  w.x_final = r->x_final;
+  w.E_final = r->E_final;
+  w.stats = r->stats;
+  w.trace = r->trace;
+  w.error = r->error;
+  pl->wrun = w;
+  pl->narrow = w.narrow != 0;
+  r->bytes = bytes;
+  *out = r;
+  return MODA_OK;
+}
+
 // Validates a request, chooses the block shape and shared-memory placement,
 // allocates the run's buffers and fills the kernel arguments; nothing is
 // enqueued.  On failure nothing is left allocated.  `budgeted`: the caller
@@ -414,6 +594,13 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
     return fail(MODA_EINVAL, "escape must be MODA_ESC_ARCHIVE or MODA_ESC_OFFSET");
   if ((uint64_t)p->replica_base + (uint64_t)p->replicas > 0x100000000ull)
     return fail(MODA_EINVAL, "replica indices must fit 32 bits");
+  if (p->engine < 0 || p->engine > 2)
+    return fail(MODA_EINVAL, "engine must be 0 (auto), 1 (block) or 2 (warp)");
+  if (p->engine == 2 && !warp_options(p))
+    return fail(MODA_EUNSUPPORTED,
+                "the warp engine needs the archive escape without normalize, "
+                "snapshot_every or fast_forward");
+  if (uses_warp(p)) return prepare_warp_run(inst, p, stream, out, pl);
 
   // Block shape: B rounds of T threads own the bits, B * T >= m.
   static const int kRounds[] = {1, 2, 3, 4, 6, 8};
@@ -468,8 +655,8 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
       (size_t)p->replicas * s_cap * moda::slot_layout(m, narrow).bytes;
   bool want_cache = p->escape == MODA_ESC_ARCHIVE && p->field_cache != 2;
   if (want_cache && p->field_cache == 0 && !budgeted) {
-    size_t free_b = 0, total_b = 0;
-    MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t free_b = 0;
+    MODA_CUDA(free_memory(inst->device, &free_b));
     want_cache = cache_bytes <= free_b / 10 * 6;
   }
   // Shared-memory placement, best first: the field cache (if wanted), the
@@ -518,7 +705,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   auto alloc = [&](void **ptr, size_t nb) {
     if (st != MODA_OK) return;
     bytes += nb;
-    cudaError_t e = cudaMalloc(ptr, nb);
+    cudaError_t e = cudaMallocAsync(ptr, nb, stream);
     if (e != cudaSuccess) st = fail(MODA_ENOMEM, std::string("device allocation: ") +
                                                      cudaGetErrorString(e));
   };
@@ -635,14 +822,187 @@ size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
   size_t b = R * s * 2 * sizeof(int64_t) + R * s * W * sizeof(uint32_t) + 32 +
              R * sizeof(int32_t) + R * W * sizeof(uint32_t) + R * 2 * sizeof(int64_t) +
              R * moda::kStats * sizeof(int64_t) + sizeof(int32_t);
-  if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2)
+  if (cache && uses_warp(&p)) {
+    // the field caches of up to R resident warps
+    const int cs = p.field_cache == 2 ? 0 : p.field_cache == 1 ? (int)s
+                                                                : std::min((int)s, kWarpCacheSlots);
+    b += R * moda::align_up(moda::warp_cache_bytes(inst->n, (int)m, cs), 256);
+  } else if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2) {
     b += R * s * moda::slot_layout((int)m, narrow).bytes;
+  }
   if (p.trace && p.I_max > 0) b += R * (size_t)p.I_max * 3 * sizeof(int64_t);
   if (p.snapshot_every > 0) {
     const size_t ns = (size_t)(p.I_max / p.snapshot_every);
     b += R * ns * (sizeof(int32_t) + s * 2 * sizeof(int64_t) + s * W * sizeof(uint32_t));
   }
   return b;
+}
+
+// A planned launch of the warp annealer.
+struct WarpGroup {
+  std::vector<int> idx;  // its runs
+  moda::WarpLaunch L{};
+  bool narrow = true;
+  int grid = 0, warps = 0;
+  std::shared_ptr<WarpScratch> scratch;
+};
+
+// Plans one launch of the warp annealer over runs[G.idx[k]] (all of one
+// variant, narrow or not): the block shape, the field-cache slots and
+// on-chip archive energies of each run within `cache_budget` bytes; then
+// allocates and uploads, on `stream`, the work list (replicas of the
+// largest runs first), clears the item counter and each run's status word.
+// The runs share the launch's buffers until the last of them is destroyed.
+moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &pls,
+                            WarpGroup &G, cudaStream_t stream, size_t cache_budget) {
+  const std::vector<int> &idx = G.idx;
+  const moda_run r0 = runs[idx[0]];
+  const int dev = r0->inst->device;
+  const bool narrow = pls[idx[0]].narrow;
+  int n_max = 2, m_max = 4, s_max = 1, la = 2;
+  int64_t items_total = 0;
+  {
+    const int pf = r0->prm.prefetch;
+    la = pf > 0 ? pf - 1 : moda::kWarpMaxLA;
+  }
+  for (int k : idx) {
+    const moda_run r = runs[k];
+    n_max = std::max(n_max, r->inst->n);
+    m_max = std::max(m_max, r->inst->m);
+    s_max = std::max(s_max, r->s);
+    items_total += r->R;
+  }
+  int sms = 1, optin = 0;
+  MODA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MODA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // Block shape: the most resident warps (ties: more warps per block),
+  // shrinking the on-chip archive energies, then the prefetch distance,
+  // until one warp's shared memory fits.
+  int best_w = 0, best_blocks = 0, se_max = std::min(s_max, kWarpSmemEnergies);
+  moda::WarpSmem sm{};
+  for (int attempt = 0; attempt < 8 && best_w == 0; ++attempt) {
+    sm = moda::warp_smem(n_max, m_max, se_max, la + 2);
+    for (int nw : {4, 2, 1}) {
+      const size_t smem = (size_t)nw * sm.total;
+      if ((int64_t)smem > optin) continue;
+      int blocks = 0;
+      if (moda::warp_occupancy(narrow, nw, smem, &blocks) != cudaSuccess || blocks < 1) continue;
+      if (blocks * nw > best_blocks * best_w) {
+        best_w = nw;
+        best_blocks = blocks;
+      }
+    }
+    if (best_w == 0) {
+      if (se_max > 64) se_max = 64;
+      else if (la > 0) --la;
+      else break;
+    }
+  }
+  if (best_w == 0) return fail(MODA_EUNSUPPORTED, "warp engine: shared memory need exceeds the device");
+  const int64_t resident = (int64_t)best_blocks * sms;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, (items_total + best_w - 1) / best_w));
+  const size_t warps = (size_t)grid * best_w;
+  // Field-cache slots per run: all (field_cache = 1), none (2), or up to
+  // kWarpCacheSlots, fewer if the launch's caches would exceed the budget.
+  std::vector<int> cs(idx.size());
+  auto stride_of = [&]() {
+    size_t st = 0;
+    for (size_t k = 0; k < idx.size(); ++k) {
+      const moda_run r = runs[idx[k]];
+      st = std::max(st, moda::warp_cache_bytes(r->inst->n, r->inst->m, cs[k]));
+    }
+    return moda::align_up(st, 256);
+  };
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const moda_run r = runs[idx[k]];
+    const int fc = r->prm.field_cache;
+    cs[k] = fc == 2 ? 0 : fc == 1 ? r->s : std::min(r->s, kWarpCacheSlots);
+  }
+  size_t stride = stride_of();
+  while (warps * stride > cache_budget) {
+    bool shrunk = false;
+    for (size_t k = 0; k < idx.size(); ++k)
+      if (runs[idx[k]]->prm.field_cache == 0 && cs[k] > 16) {
+        cs[k] = cs[k] * 3 / 4;
+        shrunk = true;
+      }
+    if (!shrunk) return fail(MODA_ENOMEM, "warp engine: field caches exceed the memory budget");
+    stride = stride_of();
+  }
+  // Run descriptors and the work list.
+  std::vector<moda::WarpRun> descs(idx.size());
+  std::vector<std::pair<int, int>> order;  // (m, k) largest first
+  for (size_t k = 0; k < idx.size(); ++k) {
+    moda::WarpRun w = pls[idx[k]].wrun;
+    w.cslots = cs[k];
+    w.se = std::min(runs[idx[k]]->s, se_max);
+    descs[k] = w;
+    order.emplace_back(-runs[idx[k]]->inst->m, (int)k);
+  }
+  std::stable_sort(order.begin(), order.end());
+  std::vector<int2> items;
+  items.reserve((size_t)items_total);
+  for (const auto &o : order)
+    for (int q = 0; q < runs[idx[o.second]]->R; ++q) items.push_back(make_int2(o.second, q));
+  auto scratch = std::make_shared<WarpScratch>();
+  scratch->device = dev;
+  // on failure after this point, work already enqueued may still use the
+  // scratch: wait for the stream before it is freed
+  struct SyncOnFail {
+    cudaStream_t s;
+    bool armed;
+    ~SyncOnFail() {
+      if (armed) cudaStreamSynchronize(s);
+    }
+  } guard{stream, true};
+  const size_t d_bytes = moda::align_up(sizeof(moda::WarpRun) * descs.size(), 256);
+  const size_t i_bytes = moda::align_up(sizeof(int2) * items.size(), 256);
+  MODA_CUDA(cudaMallocAsync(&scratch->list, d_bytes + i_bytes + 256, stream));
+  if (warps * stride > 0) {
+    cudaError_t e = cudaMallocAsync(&scratch->cache, warps * stride, stream);
+    if (e != cudaSuccess)
+      return fail(MODA_ENOMEM, std::string("warp engine field caches: ") + cudaGetErrorString(e));
+  }
+  unsigned char *base = static_cast<unsigned char *>(scratch->list);
+  MODA_CUDA(cudaMemcpyAsync(base, descs.data(), sizeof(moda::WarpRun) * descs.size(),
+                            cudaMemcpyHostToDevice, stream));
+  MODA_CUDA(cudaMemcpyAsync(base + d_bytes, items.data(), sizeof(int2) * items.size(),
+                            cudaMemcpyHostToDevice, stream));
+  MODA_CUDA(cudaMemsetAsync(base + d_bytes + i_bytes, 0, sizeof(int32_t), stream));
+  moda::WarpLaunch L{};
+  L.runs = reinterpret_cast<const moda::WarpRun *>(base);
+  L.items = reinterpret_cast<const int2 *>(base + d_bytes);
+  L.nitems = (int32_t)items.size();
+  L.lookahead = la;
+  L.nbuf = la + 2;
+  L.counter = reinterpret_cast<int32_t *>(base + d_bytes + i_bytes);
+  L.cache = static_cast<unsigned char *>(scratch->cache);
+  L.cache_stride = stride;
+  L.sm = sm;
+  for (int k : idx) {
+    moda_run r = runs[k];
+    MODA_CUDA(cudaMemsetAsync(r->error, 0, sizeof(int32_t), stream));
+    r->wscratch = scratch;
+    r->threads = best_w;  // warps per block
+    r->bpt = grid;
+  }
+  G.L = L;
+  G.narrow = narrow;
+  G.grid = grid;
+  G.warps = best_w;
+  G.scratch = scratch;
+  guard.armed = false;
+  return MODA_OK;
+}
+
+// Launches a planned group on `stream` between its runs' start and stop
+// events.
+moda_status launch_warp_group(std::vector<moda_run> &runs, const WarpGroup &G,
+                              cudaStream_t stream) {
+  for (int k : G.idx) MODA_CUDA(cudaEventRecord(runs[k]->start, stream));
+  MODA_CUDA(moda::launch_warp(G.L, G.narrow, G.grid, G.warps, stream));
+  for (int k : G.idx) MODA_CUDA(cudaEventRecord(runs[k]->stop, stream));
+  return MODA_OK;
 }
 
 // Enqueues a prepared run on its stream: clear the status word, start
@@ -669,11 +1029,24 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   moda_run r = nullptr;
   moda_status st = prepare_run(inst, p, static_cast<cudaStream_t>(cuda_stream), &r, &pl);
   if (st != MODA_OK) return st;
-  st = enqueue_run(r, pl);
+  if (r->warp) {
+    size_t free_b = 0;
+    MODA_CUDA(free_memory(inst->device, &free_b));
+    std::vector<moda_run> rs{r};
+    std::vector<Prepared> ps{pl};
+    WarpGroup G;
+    G.idx = {0};
+    st = plan_warp_group(rs, ps, G, r->stream, free_b / 10 * 6);
+    if (st == MODA_OK) st = launch_warp_group(rs, G, r->stream);
+  } else {
+    st = enqueue_run(r, pl);
+  }
   if (st != MODA_OK) {
-    free_run_buffers(r);
+    const std::string msg = g_error;
+    cudaStreamSynchronize(r->stream);
+    free_run_buffers(r, true);
     delete r;
-    return st;
+    return fail(st, msg);
   }
   *out = r;
   return MODA_OK;
@@ -873,7 +1246,7 @@ void moda_destroy_run(moda_run r) {
   cudaGetDevice(&prev);
   cudaSetDevice(r->inst->device);
   if (r->stop) cudaEventSynchronize(r->stop);
-  free_run_buffers(r);
+  free_run_buffers(r, true);
   if (r->acct) r->acct->in_use -= r->bytes;
   cudaSetDevice(prev);
   delete r;
@@ -892,13 +1265,15 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       return fail(MODA_EINVAL, "every instance must exist and live on one device");
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // Device memory for the whole batch: every run's own buffers first; then
-  // field caches (automatic ones) in order of size, smallest first, while
-  // they fit in 60 % of the free memory.
+  // the field caches of block-engine runs (automatic ones) in order of
+  // size, smallest first, while they fit in 60 % of the free memory; what
+  // is left goes to the warp-engine launches.
   std::vector<moda_params> prm(params, params + count);
+  size_t warp_budget = 0;
   {
     cudaSetDevice(insts[0]->device);
-    size_t free_b = 0, total_b = 0;
-    MODA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t free_b = 0;
+    MODA_CUDA(free_memory(insts[0]->device, &free_b));
     size_t lean = 0;
     for (int32_t i = 0; i < count; ++i) lean += run_bytes(insts[i], prm[i], false);
     if (lean > free_b / 10 * 9)
@@ -907,7 +1282,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     size_t budget = free_b / 10 * 6 > lean ? free_b / 10 * 6 - lean : 0;
     std::vector<std::pair<size_t, int32_t>> want;
     for (int32_t i = 0; i < count; ++i)
-      if (prm[i].field_cache == 0 && prm[i].escape == MODA_ESC_ARCHIVE)
+      if (!uses_warp(&prm[i]) && prm[i].field_cache == 0 && prm[i].escape == MODA_ESC_ARCHIVE)
         want.emplace_back(run_bytes(insts[i], prm[i], true) - run_bytes(insts[i], prm[i], false),
                           i);
     std::sort(want.begin(), want.end());
@@ -917,6 +1292,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       else
         prm[w.second].field_cache = 2;
     }
+    warp_budget = budget;
   }
   std::vector<moda_run> runs(count, nullptr);
   std::vector<Prepared> pls(count);
@@ -935,13 +1311,42 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       return fail(st, msg);
     }
   }
-  // One chain per run (start event, status word cleared, kernel, stop
-  // event); the chains share no edge, so blocks of many runs share the GPU.
+  // Warp-engine runs: one launch per (variant, size class, prefetch
+  // distance), a class spanning at most a factor of two in 128-bit chunks
+  // so that no warp's shared memory is sized far beyond its run.
+  std::map<std::tuple<int, int, int>, std::vector<int>> classes;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!runs[i]->warp) continue;
+    const int nc = (runs[i]->inst->m + 127) / 128;
+    int cls = 0;
+    while ((2 << cls) <= nc) ++cls;
+    classes[std::make_tuple(pls[i].narrow ? 1 : 0, -cls, runs[i]->prm.prefetch)].push_back(i);
+  }
+  std::vector<WarpGroup> groups;
+  for (auto &kv : classes) {
+    WarpGroup G;
+    G.idx = kv.second;
+    groups.push_back(std::move(G));
+  }
+  for (WarpGroup &G : groups) {
+    moda_status st = plan_warp_group(runs, pls, G, stream, warp_budget / groups.size());
+    if (st != MODA_OK) {
+      const std::string msg = g_error;
+      cudaStreamSynchronize(stream);
+      release();
+      return fail(st, msg);
+    }
+  }
+  // One CUDA graph: per block-engine run a chain (start event, status word
+  // cleared, kernel, stop event); per warp-engine launch its runs' start
+  // events, the persistent kernel, their stop events.  The chains share no
+  // edge, so the GPU runs them side by side.
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
     moda_run r = runs[i];
+    if (r->warp) continue;
     const Prepared &pl = pls[i];
     cudaGraphNode_t n0, n1, n2, n3;
     const void *func = nullptr;
@@ -969,6 +1374,36 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       e = cudaGraphAddKernelNode(&n2, g, &n1, 1, &kp);
     }
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n3, g, &n2, 1, r->stop);
+  }
+  for (const WarpGroup &G : groups) {
+    if (e != cudaSuccess) break;
+    std::vector<cudaGraphNode_t> starts;
+    for (int k : G.idx) {
+      cudaGraphNode_t nd;
+      e = cudaGraphAddEventRecordNode(&nd, g, nullptr, 0, runs[k]->start);
+      if (e != cudaSuccess) break;
+      starts.push_back(nd);
+    }
+    const void *func = nullptr;
+    const size_t smem = (size_t)G.warps * G.L.sm.total;
+    if (e == cudaSuccess) e = moda::warp_function(G.narrow, smem, &func);
+    cudaGraphNode_t kn;
+    if (e == cudaSuccess) {
+      void *kargs[1] = {const_cast<moda::WarpLaunch *>(&G.L)};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void *>(func);
+      kp.gridDim = dim3((unsigned)G.grid);
+      kp.blockDim = dim3((unsigned)(32 * G.warps));
+      kp.sharedMemBytes = (unsigned)smem;
+      kp.kernelParams = kargs;
+      kp.extra = nullptr;
+      e = cudaGraphAddKernelNode(&kn, g, starts.data(), starts.size(), &kp);
+    }
+    for (int k : G.idx) {
+      if (e != cudaSuccess) break;
+      cudaGraphNode_t nd;
+      e = cudaGraphAddEventRecordNode(&nd, g, &kn, 1, runs[k]->stop);
+    }
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
   if (e == cudaSuccess) e = cudaGraphLaunch(ex, stream);
@@ -1090,9 +1525,20 @@ void server_loop(moda_server_s *S) {
       // the cache was budgeted above (prm.field_cache == 2 when it does not fit)
       moda_status rs = prepare_run(q->inst, &prm, st, &r, &pl, true);
       if (rs == MODA_OK) {
-        rs = enqueue_run(r, pl);
+        if (r->warp) {
+          std::vector<moda_run> rs1{r};
+          std::vector<Prepared> ps1{pl};
+          WarpGroup G;
+          G.idx = {0};
+          const size_t cache_b = run_bytes(q->inst, prm, true) - run_bytes(q->inst, prm, false);
+          rs = plan_warp_group(rs1, ps1, G, st, cache_b);
+          if (rs == MODA_OK) rs = launch_warp_group(rs1, G, st);
+        } else {
+          rs = enqueue_run(r, pl);
+        }
         if (rs != MODA_OK) {
-          free_run_buffers(r);
+          cudaStreamSynchronize(st);
+          free_run_buffers(r, true);
           delete r;
           r = nullptr;
         }
@@ -1132,8 +1578,8 @@ moda_status moda_server_create(size_t hbm_budget, void *cuda_stream, moda_server
   cudaGetDevice(&S->device);
   S->budget = hbm_budget;
   if (S->budget == 0) {  // free memory less a reserve of 1/8 (at least 1 GiB)
-    size_t free_b = 0, total_b = 0;
-    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    size_t free_b = 0;
+    cudaError_t e = free_memory(S->device, &free_b);
     if (e != cudaSuccess) {
       delete S;
       return cuda_fail(e, "cudaMemGetInfo");
@@ -1326,6 +1772,34 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
   if (trial_iters < 1) return fail(MODA_EINVAL, "trial_iters must be >= 1");
   const int m = inst->m;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  if (uses_warp(params)) {
+    // Warp engine: the prefetch distances 0, 1 and 2, each timed on the
+    // request's own replicas at the cold end of the schedule.
+    moda_params trial = *params;
+    trial.I_max = trial_iters;
+    trial.delta0 = params->deltaf;
+    trial.trace = 0;
+    bool found = false;
+    float fastest = 0.f;
+    moda_params winner = *params;
+    for (int32_t pf : {1, 2, 3}) {
+      trial.prefetch = pf;
+      moda_run r = nullptr;
+      if (moda_anneal(inst, &trial, stream, &r) != MODA_OK) continue;
+      float ms = 0.f;
+      const bool ok = moda_wait(r, -1) == MODA_OK && moda_run_elapsed_ms(r, &ms) == MODA_OK;
+      moda_destroy_run(r);
+      if (ok && (!found || ms < fastest)) {
+        found = true;
+        fastest = ms;
+        winner.prefetch = pf;
+      }
+    }
+    if (!found) return fail(MODA_EUNSUPPORTED, "no prefetch distance runs this instance");
+    *best = winner;
+    if (best_ms) *best_ms = fastest;
+    return MODA_OK;
+  }
   // Candidates: every block shape the kernel has (B bits per thread, the
   // fewest threads that hold m bits) and, when the escape jumps to the
   // archive, prefetch distances 1 and 2 besides the automatic choice.

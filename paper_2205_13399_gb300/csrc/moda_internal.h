@@ -222,6 +222,130 @@ cudaError_t launch_anneal_special(const AnnealArgs &args, int replicas, int work
 cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t smem,
                                     const void **func);
 
+// ---- the warp annealer: one warp per replica -------------------------------
+//
+// A throughput form of the same loop: each warp runs one replica by itself
+// (no block barriers), pulling (run, replica) work items from a device
+// list.  Bit p of a replica belongs to lane (p % 128) / 4 of chunk p / 128,
+// so a lane holds 4 consecutive bits of every chunk (one acceptance Philox
+// block: bits 4g .. 4g + 3 take the words of block g).  The state a trial
+// reads is, per bit, its acceptance penalty a (strict: sum_k max(0, dE_k);
+// lenient: min_k max(0, dE_k)) saturated to uint32; the integer cost fields
+// L_k (int32 pairs) live in global memory and are read only by flips.
+
+constexpr int kWarpRing = 64;   // draw / schedule ring entries (iterations)
+constexpr int kWarpMaxLA = 2;   // prefetch distance (iterations ahead)
+
+// Records of one archive slot for a run of n, m (the field cache of the
+// warp annealer):
+//   jump record  a[mp] uint32 penalties, the state words [mp / 32], the row
+//                and column counts [2n] uint8 (16-byte padded), (E1, E2)
+//                int64 -- brought into shared memory by one bulk copy when
+//                the replica jumps to the slot;
+//   field record (L1, L2) int32 pairs [mp].
+// mp = 128 ceil(m / 128): bits past m carry a = 0xFFFFFFFF and no state.
+struct WarpRec {
+  int32_t nc, mp;                        // chunks of 128 bits, padded bits
+  uint32_t off_xw, off_rc, off_E, jr;    // jump-record offsets and bytes
+  uint32_t lr;                           // field-record bytes
+};
+__host__ __device__ inline WarpRec warp_rec(int n, int m) {
+  WarpRec r;
+  r.nc = (m + 127) / 128;
+  r.mp = 128 * r.nc;
+  r.off_xw = 4u * (uint32_t)r.mp;
+  r.off_rc = r.off_xw + 4u * (uint32_t)(r.mp / 32);
+  r.off_E = r.off_rc + (uint32_t)align_up((size_t)(2 * n), 16);
+  r.jr = r.off_E + 16u;
+  r.lr = 8u * (uint32_t)r.mp;
+  return r;
+}
+
+// Shared-memory carve-up of one warp (byte offsets), sized for the largest
+// run of a launch: nbuf jump-record buffers, their mbarriers, the ring of
+// draws and schedule entries, the archive energies of slots < se, the
+// flow and distance rows of a flip, the accepted-chunk list and the
+// prefetch bookkeeping.
+struct WarpSmem {
+  uint32_t jr;     // buffer stride
+  uint32_t buf, mbar, ring, aE, rows, acc, pf, total;
+  int32_t nc_max;
+};
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf) {
+  const WarpRec r = warp_rec(n_max, m_max);
+  WarpSmem L;
+  size_t o = 0;
+  L.jr = r.jr;
+  L.nc_max = r.nc;
+  L.buf = 0;                 o = align_up(o + (size_t)nbuf * r.jr, 16);
+  L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nbuf, 16);
+  L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
+  L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
+  L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
+  L.acc = (uint32_t)o;       o = align_up(o + 20 * (size_t)r.nc, 16);
+  L.pf = (uint32_t)o;        o = align_up(o + 16 * 4 + 4 * 4, 16);
+  L.total = (uint32_t)o;
+  return L;
+}
+
+// One run of a warp-annealer launch (device memory; every pointer a
+// device pointer).
+struct WarpRun {
+  int32_t n, m, W, s;
+  int32_t cslots;            // slots < cslots have field-cache records; a
+                             // jump to a later slot rebuilds the fields
+  int32_t se;                // archive energies of slots < se on chip
+  int32_t narrow;            // |Delta E_k| < 2^31 for every state
+  int32_t accept, archive;   // moda_accept, moda_archive (escape: archive)
+  int32_t nsched, replicas;
+  uint32_t replica_base, seed_lo, seed_hi, magic;
+  int32_t pad;
+  int64_t I_max;
+  int64_t w1, w2;
+  const double *sch_delta;
+  const int64_t *sch_lo, *sch_hi;
+  const double *table;
+  const int32_t *Fs1, *Fs2, *D;
+  int64_t *arch_E;
+  uint32_t *arch_bits;
+  int32_t *arch_count;
+  uint32_t *x_final;
+  int64_t *E_final;
+  int64_t *stats;
+  int64_t *trace;            // [R][I_max][3] or nullptr
+  int32_t *error;
+};
+
+// Kernel argument of a warp-annealer launch.
+struct WarpLaunch {
+  const WarpRun *runs;
+  const int2 *items;         // (run, replica row), largest runs first
+  int32_t nitems;
+  int32_t nbuf;              // jump-record buffers per warp: lookahead + 2
+  int32_t lookahead;         // prefetch distance, 0 .. kWarpMaxLA
+  int32_t pad;
+  int32_t *counter;          // next item; zero before the launch
+  unsigned char *cache;      // field-cache region of each resident warp
+  size_t cache_stride;       // bytes per warp
+  WarpSmem sm;               // per-warp shared memory
+};
+
+// Field-cache bytes of one warp for a run: cslots jump and field records
+// plus a working field record.
+inline size_t warp_cache_bytes(int n, int m, int cslots) {
+  const WarpRec r = warp_rec(n, m);
+  return (size_t)cslots * ((size_t)r.jr + r.lr) + r.lr;
+}
+
+// Launches the warp annealer: `grid` blocks of `warps` warps.
+cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int warps,
+                        cudaStream_t stream);
+// The warp annealer's kernel (one WarpLaunch argument) for a CUDA graph
+// node, with `smem` bytes of dynamic shared memory allowed.
+cudaError_t warp_function(bool narrow, size_t smem, const void **func);
+// Resident blocks per SM of the warp annealer for this shape.
+cudaError_t warp_occupancy(bool narrow, int warps, size_t smem, int *blocks);
+
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);
 inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }

@@ -1,0 +1,715 @@
+// The warp annealer: Alg. 3 of arXiv 2205.13399 (the multi-objective
+// Digital Annealer, Sec. 3.3) for the bi-objective QAP with one warp per
+// replica.  A persistent grid of warps pulls (run, replica) work items from
+// a device list (largest runs first), so replicas of many instances of
+// uneven n share the GPU in one launch, and no warp ever waits at a block
+// barrier.
+//
+// State of a replica, the current point x of Alg. 3:
+//   shared memory  its jump record: per bit the acceptance penalty
+//                  a(p) = sum_k max(0, dE_k(p)) (strict, Eq. pacceptms) or
+//                  min_k max(0, dE_k(p)) (lenient, Eq. pacceptml),
+//                  saturated to uint32; the state words; the row and column
+//                  counts R_i, C_u;
+//   global memory  its cost fields L_k(i,u) = sum_(j,v) Fs^k_ij d_uv x_jv
+//                  (Fs^k = F^k + F^k^T), int32 pairs;
+//   registers      E_1, E_2 and |A|.
+// With h = R_i + C_u - 1 - 2 x_p and alpha_k = w_k / 2 (Eq. wqubom),
+//   dE_k(p) = (1 - 2 x_p) (L_k(p) + w_k h)                         (Eq. cale),
+// so a trial needs only a(p): bit p is accepted iff (double) a <=
+// delta_t T[idx] (R7), decided by a <= lo_t or a > hi_t without a draw
+// (R21).  Bit p of chunk c = p / 128 belongs to lane (p % 128) / 4, which
+// owns bits 4g .. 4g + 3 of Philox group g = p / 4: one block per lane.
+//
+// A flip of bit (j, v) with s = +1 when it turns on adds s Fs^k_ij d_uv to
+// every L_k(i, u) -- the outer product of flow row j and distance row v, so
+// Q is never stored -- then recomputes every a(p) from L, the new counts
+// and the new state.  Every archive slot keeps its jump and field records
+// (the field cache); a jump to slot y takes y's jump record, prefetched by a
+// bulk copy (TMA, mbarrier) `lookahead` iterations early when y is already
+// known (the restart draw and |A| are), and y's field record in place.  A
+// slot without records (beyond the cache) is rebuilt: M = X D, then
+// L_k = Fs_k M.
+#include <cstdint>
+#include <type_traits>
+
+#include "moda_device.cuh"
+#include "moda_internal.h"
+
+namespace moda {
+namespace {
+
+// Ring entry of one iteration: delta_t, its thresholds and the draws of the
+// select, restart and exploit purposes.
+struct WRing {
+  double delta;
+  int64_t lo, hi;
+  uint32_t sel, rst, exp, pad;
+};
+static_assert(sizeof(WRing) == 40, "ring entry layout");
+
+template <bool NARROW>
+struct WarpAnnealer {
+  using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
+
+  // Penalty of a bit with Delta E (e1, e2), saturated to uint32.  In the
+  // narrow variant each |dE_k| < 2^31, so the sum stays below 2^32 - 1.
+  __device__ __forceinline__ static uint32_t penalty(dE_t e1, dE_t e2, bool lenient) {
+    const dE_t u1 = e1 > 0 ? e1 : (dE_t)0, u2 = e2 > 0 ? e2 : (dE_t)0;
+    if (NARROW) {
+      return lenient ? (uint32_t)(u1 < u2 ? u1 : u2) : (uint32_t)u1 + (uint32_t)u2;
+    } else {
+      const int64_t a = lenient ? (int64_t)(u1 < u2 ? u1 : u2) : (int64_t)u1 + (int64_t)u2;
+      return a >= 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)a;
+    }
+  }
+};
+
+// Runs replica `row` of run R on this warp for all I_max iterations.
+// `par` holds the phase parity of the warp's mbarriers across items.
+// Returns false when a bounded wait gave up (the error word is set).
+template <bool NARROW>
+__device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, const WarpLaunch &Lc,
+                         unsigned char *cache, const int lane, uint32_t &par) {
+  using WA = WarpAnnealer<NARROW>;
+  using dE_t = typename WA::dE_t;
+  const int n = R.n, m = R.m, W = R.W, s = R.s;
+  const WarpRec rec = warp_rec(n, m);
+  const int NC = rec.nc;
+  const int cslots = R.cslots, se = R.se;
+  const uint32_t rep = R.replica_base + (uint32_t)row;
+  const uint32_t k0 = R.seed_lo, k1 = R.seed_hi;
+  const uint32_t I_max = (uint32_t)R.I_max;
+  const uint32_t nsched = (uint32_t)R.nsched;
+  const int64_t w1l = R.w1, w2l = R.w2;
+  const dE_t w1 = (dE_t)w1l, w2 = (dE_t)w2l;
+  const bool lenient = R.accept != 0;
+  const bool exploit = R.archive != 0;
+  const uint32_t magic = R.magic;
+  const int LA = Lc.lookahead, NB = Lc.nbuf;
+  const WarpSmem &SL = Lc.sm;
+
+  unsigned char *sbuf = ws + SL.buf;
+  uint64_t *sbar = reinterpret_cast<uint64_t *>(ws + SL.mbar);
+  WRing *ring = reinterpret_cast<WRing *>(ws + SL.ring);
+  longlong2 *sAE = reinterpret_cast<longlong2 *>(ws + SL.aE);
+  int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
+  uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
+  int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
+  // prefetch bookkeeping: sPf[tt & 3] = {buffer or -1, slot, issuing
+  // iteration} of the copy for target iteration tt; sWr[x & 3] = the slot
+  // iteration x wrote (-1: none)
+  int4 *sPf = reinterpret_cast<int4 *>(ws + SL.pf);
+  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 64);
+
+  int64_t *gE = R.arch_E + (size_t)row * s * 2;
+  uint32_t *gB = R.arch_bits + (size_t)row * s * W;
+  unsigned char *gJR = cache;                                           // [cslots] jump records
+  int2 *gLR = reinterpret_cast<int2 *>(cache + (size_t)cslots * rec.jr);  // [cslots][mp]
+  int2 *gWork = gLR + (size_t)cslots * rec.mp;                            // [mp] working fields
+  const int32_t *Fs1 = R.Fs1, *Fs2 = R.Fs2, *Dm = R.D;
+
+  auto bA = [&](int b) { return reinterpret_cast<uint32_t *>(sbuf + (size_t)b * SL.jr); };
+  auto bX = [&](int b) {
+    return reinterpret_cast<uint32_t *>(sbuf + (size_t)b * SL.jr + rec.off_xw);
+  };
+  auto bRC = [&](int b) { return sbuf + (size_t)b * SL.jr + rec.off_rc; };
+  auto bE = [&](int b) {
+    return reinterpret_cast<int64_t *>(sbuf + (size_t)b * SL.jr + rec.off_E);
+  };
+  auto divn = [&](int p) { return (int)__umulhi((uint32_t)p, magic); };
+
+  // Iterations first .. first + 31 into the ring: schedule entry (Alg. 3's
+  // cooling, the last entry held once delta reaches delta_f) and the draws
+  // (0, q, replica, tag) of the select, restart and exploit purposes.
+  auto fill = [&](uint32_t first) {
+    const uint32_t q = first + (uint32_t)lane;
+    const uint32_t sn = (q <= nsched ? q : nsched) - 1u;
+    WRing e;
+    e.delta = R.sch_delta[sn];
+    e.lo = R.sch_lo[sn];
+    e.hi = R.sch_hi[sn];
+    uint32_t c[4] = {0u, q, rep, kTagSelect};
+    philox10(c, k0, k1);
+    e.sel = c[0];
+    uint32_t d[4] = {0u, q, rep, kTagRestart};
+    philox10(d, k0, k1);
+    e.rst = d[0];
+    e.exp = 0u;
+    if (exploit) {
+      uint32_t x[4] = {0u, q, rep, kTagExploit};
+      philox10(x, k0, k1);
+      e.exp = x[0];
+    }
+    e.pad = 0u;
+    ring[q % kWarpRing] = e;
+  };
+
+  // Row and column counts of the state in buffer b.
+  auto counts = [&](int b) {
+    const uint32_t *xw = bX(b);
+    unsigned char *rc = bRC(b);
+    for (int i = lane; i < n; i += 32) {
+      int cr = 0, cc = 0;
+      for (int u = 0; u < n; ++u) {
+        const int p = i * n + u, q = u * n + i;
+        cr += (int)((xw[p >> 5] >> (p & 31)) & 1u);
+        cc += (int)((xw[q >> 5] >> (q & 31)) & 1u);
+      }
+      rc[i] = (unsigned char)cr;
+      rc[n + i] = (unsigned char)cc;
+    }
+    __syncwarp();
+  };
+
+  // Fields and penalties of the state in buffer b from scratch (Alg. 3's
+  // initial state, or a jump to a slot without records): M = X D in the
+  // a-array of buffer sc, then L_k(i,u) = sum_j Fs^k_ij M_ju into gL and
+  // a(p) into buffer b.  Returns sum over set bits of L_1, of L_2 (2 c_k)
+  // and g (Eq. gqap), warp totals.
+  auto rebuild = [&](int b, int sc, int2 *gL, int64_t &t1, int64_t &t2, int64_t &gp) {
+    counts(b);
+    const uint32_t *xw = bX(b);
+    const unsigned char *rc = bRC(b);
+    int32_t *M = reinterpret_cast<int32_t *>(bA(sc));
+    for (int e = lane; e < n * n; e += 32) {
+      const int j = divn(e), u = e - j * n;
+      int32_t acc = 0;
+      for (int v = 0; v < n; ++v) {
+        const int p = j * n + v;
+        if ((xw[p >> 5] >> (p & 31)) & 1u) acc += __ldg(&Dm[v * n + u]);
+      }
+      M[e] = acc;
+    }
+    __syncwarp();
+    uint32_t *ab = bA(b);
+    t1 = 0;
+    t2 = 0;
+    for (int p = lane; p < rec.mp; p += 32) {
+      uint32_t a = 0xFFFFFFFFu;
+      int2 L = make_int2(0, 0);
+      if (p < m) {
+        const int i = divn(p), u = p - i * n;
+        int32_t a1 = 0, a2 = 0;
+        for (int j = 0; j < n; ++j) {
+          const int32_t mm = M[j * n + u];
+          a1 += __ldg(&Fs1[i * n + j]) * mm;
+          a2 += __ldg(&Fs2[i * n + j]) * mm;
+        }
+        L = make_int2(a1, a2);
+        const int xv = (int)((xw[p >> 5] >> (p & 31)) & 1u);
+        const dE_t g = (dE_t)(1 - 2 * xv);
+        const dE_t h = (dE_t)rc[i] + (dE_t)rc[n + u] - 1 - 2 * xv;
+        a = WA::penalty(g * ((dE_t)a1 + w1 * h), g * ((dE_t)a2 + w2 * h), lenient);
+        if (xv) {
+          t1 += a1;
+          t2 += a2;
+        }
+      }
+      gL[p] = L;
+      ab[p] = a;
+    }
+    gp = 0;
+    for (int i = lane; i < n; i += 32) {
+      const int64_t dr = 1 - (int64_t)rc[i], dc = 1 - (int64_t)rc[n + i];
+      gp += dr * dr + dc * dc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t1 += __shfl_xor_sync(kFull, t1, o);
+      t2 += __shfl_xor_sync(kFull, t2, o);
+      gp += __shfl_xor_sync(kFull, gp, o);
+    }
+    __syncwarp();
+  };
+
+  // Exact penalty of bit p of the state in buffer b with fields gL (only
+  // for a saturated a(p) in the int64 variant).
+  auto exact_penalty = [&](int b, const int2 *gL, int p) -> int64_t {
+    const int2 L = gL[p];
+    const int i = divn(p), u = p - i * n;
+    const uint32_t *xw = bX(b);
+    const unsigned char *rc = bRC(b);
+    const int xv = (int)((xw[p >> 5] >> (p & 31)) & 1u);
+    const int64_t g = 1 - 2 * xv, h = (int64_t)rc[i] + rc[n + u] - 1 - 2 * xv;
+    const int64_t e1 = g * ((int64_t)L.x + w1l * h), e2 = g * ((int64_t)L.y + w2l * h);
+    const int64_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
+    return lenient ? (u1 < u2 ? u1 : u2) : u1 + u2;
+  };
+
+  bool fail = false;
+  auto wait_buf = [&](int b) {
+    const bool ok = mbar_wait(&sbar[b], (par >> b) & 1u);
+    if (!__all_sync(kFull, ok)) fail = true;
+    par ^= 1u << b;
+  };
+
+  // ---- initial state (Alg. 3: "a random binary solution", R10) ----------
+  // Chunk c's 128 bits are the four words of Philox block (c, 0, replica,
+  // init): state word 4c + w is word w.
+  int cur = 0;
+  {
+    uint32_t *x0 = bX(0);
+    for (int c = lane; c < NC; c += 32) {
+      uint32_t b[4] = {(uint32_t)c, 0u, rep, kTagInit};
+      philox10(b, k0, k1);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int lo = 32 * (4 * c + w);
+        uint32_t v = b[w];
+        if (lo >= m) v = 0u;
+        else if (lo + 32 > m) v &= (1u << (m - lo)) - 1u;
+        x0[4 * c + w] = v;
+      }
+    }
+    __syncwarp();
+  }
+  int64_t E1, E2;
+  {
+    int64_t t1, t2, gp;
+    rebuild(0, 1, gWork, t1, t2, gp);
+    E1 = t1 / 2 + w1l * (gp / 2);
+    E2 = t2 / 2 + w2l * (gp / 2);
+  }
+  const int2 *curL = gWork;
+  int acount = 0;
+  // free buffers (bit b), copies in flight (bit b)
+  uint32_t freeb = ((1u << NB) - 1u) & ~1u, pend = 0u;
+  int flip_streak = 0;
+  uint32_t nflip = 0, njump = 0, nempty = 0, npref = 0, ndirect = 0;
+  if (lane < 4) {
+    sPf[lane] = make_int4(-1, 0, 0, 0);
+    sWr[lane] = -1;
+  }
+  fill(1);
+  fill(33);
+  __syncwarp();
+
+  for (uint32_t t = 1; t <= I_max; ++t) {
+    if ((t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
+    if (lane == 0) sWr[t & 3u] = -1;
+    __syncwarp();
+    const WRing e = ring[t % kWarpRing];
+
+    // ---- prefetch: the jump record of the member a jump at t + LA would
+    // land on (its draw and |A| are known), unless the replica is in a run
+    // of flips
+    if (LA > 0) {
+      const uint32_t tt = t + (uint32_t)LA;
+      int4 rec_pf = make_int4(-1, 0, 0, 0);
+      if (acount > 0 && flip_streak < 3 && tt <= I_max) {
+        const int sp = pick(ring[tt % kWarpRing].rst, acount);
+        if (sp < cslots) {
+          const int b = __ffs(freeb) - 1;  // exists: LA + 1 buffers are held
+          freeb &= ~(1u << b);
+          if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
+            wait_buf(b);
+            pend &= ~(1u << b);
+          }
+          if (lane == 0) {
+            fence_proxy_async_shared();
+            mbar_expect_tx(&sbar[b], rec.jr);
+            bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
+          }
+          pend |= 1u << b;
+          rec_pf = make_int4(b, sp, (int)t, 0);
+        }
+      }
+      if (lane == 0) sPf[tt & 3u] = rec_pf;
+    }
+
+    // ---- the parallel trial of every bit (Eq. pacceptms / pacceptml) -----
+    const double delta = e.delta;
+    const int64_t lo = e.lo, hi = e.hi;
+    const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
+    const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(cur));
+    int total = 0, nl = 0;
+#pragma unroll 4
+    for (int c = 0; c < NC; ++c) {
+      const uint4 a4 = a4p[c * 32 + lane];
+      const uint32_t amin = min(min(a4.x, a4.y), min(a4.z, a4.w));
+      if (__any_sync(kFull, amin <= hi32)) {
+        // some bit of the chunk may be accepted: exact decisions
+        const int p0 = c * 128 + lane * 4;
+        const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+        int64_t ax[4];
+        bool acc[4], need[4];
+        bool anyneed = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[j] = false;
+          need[j] = false;
+          ax[j] = (int64_t)av[j];
+          if (p0 + j < m && av[j] <= hi32) {
+            if (!NARROW && av[j] == 0xFFFFFFFFu) ax[j] = exact_penalty(cur, curL, p0 + j);
+            if (ax[j] <= lo)
+              acc[j] = true;
+            else if (ax[j] <= hi)
+              need[j] = true;
+          }
+          anyneed |= need[j];
+        }
+        if (__any_sync(kFull, anyneed)) {
+          // a in (lo, hi]: the draw decides (R7, R21); group 32c + lane
+          uint32_t d[4] = {(uint32_t)(c * 32 + lane), t, rep, kTagAccept};
+          philox10(d, k0, k1);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (need[j]) acc[j] = (double)ax[j] <= __dmul_rn(delta, __ldg(&R.table[d[j] >> 16]));
+        }
+        const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
+                       b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
+        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+        if (cnt > 0) {
+          if (lane == 0) {
+            sAccW[nl] = make_uint4(b0, b1, b2, b3);
+            sAccC[nl] = c;
+          }
+          ++nl;
+          total += cnt;
+        }
+      }
+    }
+    __syncwarp();
+
+    // the copy for this iteration: taken by a jump below, else given back
+    const int4 pr = LA > 0 ? sPf[t & 3u] : make_int4(-1, 0, 0, 0);
+    int kind = 0;  // 1 flip, 2 jump, 0 neither
+    int event_slot = 0, ps = 0;
+    if (total > 0) {
+      // ---- one accepted flip at random (R11): rank r in ascending bit order
+      if (pr.x >= 0) freeb |= 1u << pr.x;
+      kind = 1;
+      const int r = pick(e.sel, total);
+      int q = 0, before = 0;
+      uint4 bw = sAccW[0];
+      for (;;) {
+        const int k = __popc(bw.x) + __popc(bw.y) + __popc(bw.z) + __popc(bw.w);
+        if (r < before + k) break;
+        before += k;
+        bw = sAccW[++q];
+      }
+      const int c = sAccC[q];
+      // lane l's accepted bits (4l .. 4l + 3 of the chunk) as a nibble
+      const uint32_t nib = ((bw.x >> lane) & 1u) | (((bw.y >> lane) & 1u) << 1) |
+                           (((bw.z >> lane) & 1u) << 2) | (((bw.w >> lane) & 1u) << 3);
+      const int cl = __popc(nib);
+      const int incl = warp_incl_scan(cl, lane);
+      const int rr = r - before;
+      const bool mine = rr >= incl - cl && rr < incl;
+      const unsigned who = __ballot_sync(kFull, mine);
+      const int owner = __ffs(who) - 1;
+      int jj = mine ? nth_set_bit(nib, rr - (incl - cl)) : 0;
+      jj = __shfl_sync(kFull, jj, owner);
+      ps = c * 128 + owner * 4 + jj;
+
+      uint32_t *xw = bX(cur);
+      unsigned char *rc = bRC(cur);
+      const int xps = (int)((xw[ps >> 5] >> (ps & 31)) & 1u);
+      const int sgn = 1 - 2 * xps;  // +1: the bit turns on
+      const int j = divn(ps), v = ps - j * n;
+      const int2 Lp = curL[ps];
+      const int64_t hps = (int64_t)rc[j] + (int64_t)rc[n + v] - 1 - 2 * xps;
+      const int64_t nE1 = E1 + (int64_t)sgn * ((int64_t)Lp.x + w1l * hps);
+      const int64_t nE2 = E2 + (int64_t)sgn * ((int64_t)Lp.y + w2l * hps);
+
+      // ---- archive update: Alg. 4 (explore) or Alg. 5 (exploit)
+      int target = -1;
+      if (!exploit) {
+        // the first member x dominates is replaced; else x is appended
+        for (int base = 0; base < acount; base += 32) {
+          const int y = base + lane;
+          bool dom = false;
+          if (y < acount) {
+            const longlong2 ye = y < se ? sAE[y] : make_longlong2(gE[2 * y], gE[2 * y + 1]);
+            dom = dominates(nE1, nE2, ye.x, ye.y);
+          }
+          const unsigned bal = __ballot_sync(kFull, dom);
+          if (bal) {
+            target = base + __ffs(bal) - 1;
+            break;
+          }
+        }
+        if (target < 0 && acount < s) target = acount++;
+      } else {
+        // no member may dominate x; then a random dominated member is
+        // replaced (tag 3 draw, slot order), else x is appended
+        int nb = 0;
+        bool anyd = false;
+        for (int base = 0; base < acount; base += 32) {
+          const int y = base + lane;
+          bool dom = false, domd = false;
+          if (y < acount) {
+            const longlong2 ye = y < se ? sAE[y] : make_longlong2(gE[2 * y], gE[2 * y + 1]);
+            dom = dominates(nE1, nE2, ye.x, ye.y);
+            domd = dominates(ye.x, ye.y, nE1, nE2);
+          }
+          nb += __popc(__ballot_sync(kFull, dom));
+          anyd |= __any_sync(kFull, domd);
+        }
+        if (!anyd) {
+          if (nb > 0) {
+            int want = pick(e.exp, nb);
+            for (int base = 0; base < acount; base += 32) {
+              const int y = base + lane;
+              bool dom = false;
+              if (y < acount) {
+                const longlong2 ye = y < se ? sAE[y] : make_longlong2(gE[2 * y], gE[2 * y + 1]);
+                dom = dominates(nE1, nE2, ye.x, ye.y);
+              }
+              const unsigned bal = __ballot_sync(kFull, dom);
+              const int k = __popc(bal);
+              if (want < k) {
+                target = base + nth_set_bit(bal, want);
+                break;
+              }
+              want -= k;
+            }
+          } else if (acount < s) {
+            target = acount++;
+          }
+        }
+      }
+
+      // ---- apply the flip: outer product of flow row j and distance row v
+      for (int i = lane; i < n; i += 32) {
+        sRow[i] = __ldg(&Fs1[j * n + i]);  // Fs symmetric: row j = column j
+        sRow[kMaxN + i] = __ldg(&Fs2[j * n + i]);
+        sRow[2 * kMaxN + i] = __ldg(&Dm[v * n + i]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        rc[j] = (unsigned char)((int)rc[j] + sgn);
+        rc[n + v] = (unsigned char)((int)rc[n + v] + sgn);
+      }
+      __syncwarp();
+      const bool cached = target >= 0 && target < cslots;
+      int2 *dstL = cached ? gLR + (size_t)target * rec.mp : gWork;
+      uint4 *dA = cached ? reinterpret_cast<uint4 *>(gJR + (size_t)target * rec.jr) : nullptr;
+      uint4 *sa4 = reinterpret_cast<uint4 *>(bA(cur));
+      for (int cc = 0; cc < NC; ++cc) {
+        const int p0 = cc * 128 + lane * 4;
+        const int4 *src = reinterpret_cast<const int4 *>(curL + p0);
+        const int4 l01 = src[0], l23 = src[1];
+        const uint32_t nibx = (xw[p0 >> 5] >> (p0 & 31)) & 15u;
+        int Lx[4] = {l01.x, l01.z, l23.x, l23.z};
+        int Ly[4] = {l01.y, l01.w, l23.y, l23.w};
+        uint32_t an[4];
+        int i = divn(p0), u = p0 - i * n;
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int p = p0 + q2;
+          if (p < m) {
+            const int32_t dd = sRow[2 * kMaxN + u];
+            Lx[q2] += sgn * sRow[i] * dd;
+            Ly[q2] += sgn * sRow[kMaxN + i] * dd;
+            const int xq = (int)((nibx >> q2) & 1u) ^ (p == ps ? 1 : 0);
+            const dE_t g = (dE_t)(1 - 2 * xq);
+            const dE_t h = (dE_t)rc[i] + (dE_t)rc[n + u] - 1 - 2 * xq;
+            an[q2] = WA::penalty(g * ((dE_t)Lx[q2] + w1 * h), g * ((dE_t)Ly[q2] + w2 * h), lenient);
+          } else {
+            an[q2] = 0xFFFFFFFFu;
+          }
+          if (++u == n) {
+            u = 0;
+            ++i;
+          }
+        }
+        int4 *dst = reinterpret_cast<int4 *>(dstL + p0);
+        dst[0] = make_int4(Lx[0], Ly[0], Lx[1], Ly[1]);
+        dst[1] = make_int4(Lx[2], Ly[2], Lx[3], Ly[3]);
+        const uint4 a4n = make_uint4(an[0], an[1], an[2], an[3]);
+        sa4[cc * 32 + lane] = a4n;
+        if (cached) dA[cc * 32 + lane] = a4n;
+      }
+      __syncwarp();
+      if (lane == 0) xw[ps >> 5] ^= 1u << (ps & 31);
+      __syncwarp();
+      if (target >= 0) {
+        if (lane == 0) {
+          gE[2 * target] = nE1;
+          gE[2 * target + 1] = nE2;
+          if (target < se) sAE[target] = make_longlong2(nE1, nE2);
+          sWr[t & 3u] = target;
+        }
+        for (int q2 = lane; q2 < W; q2 += 32) gB[(size_t)target * W + q2] = xw[q2];
+        if (cached) {
+          unsigned char *jr = gJR + (size_t)target * rec.jr;
+          uint32_t *jx = reinterpret_cast<uint32_t *>(jr + rec.off_xw);
+          for (int q2 = lane; q2 < rec.mp / 32; q2 += 32) jx[q2] = xw[q2];
+          const uint32_t *rcw = reinterpret_cast<const uint32_t *>(rc);
+          uint32_t *jrc = reinterpret_cast<uint32_t *>(jr + rec.off_rc);
+          for (int q2 = lane; q2 < (int)(rec.off_E - rec.off_rc) / 4; q2 += 32) jrc[q2] = rcw[q2];
+          if (lane == 0) {
+            int64_t *je = reinterpret_cast<int64_t *>(jr + rec.off_E);
+            je[0] = nE1;
+            je[1] = nE2;
+          }
+          fence_proxy_async_global();  // later bulk copies read these records
+        }
+      }
+      __syncwarp();
+      curL = dstL;
+      E1 = nE1;
+      E2 = nE2;
+      event_slot = target;
+      ++nflip;
+    } else if (acount > 0) {
+      // ---- no bit accepted: jump to a random archive member (Alg. 3)
+      kind = 2;
+      const int slot = pick(e.rst, acount);
+      event_slot = slot;
+      bool ok = pr.x >= 0 && pr.y == slot;
+      if (ok)
+        for (uint32_t xi = (uint32_t)pr.z; xi < t; ++xi)
+          if (sWr[xi & 3u] == slot) ok = false;  // rewritten after the copy began
+      int nbuf;
+      if (ok) {
+        nbuf = pr.x;
+        wait_buf(nbuf);
+        pend &= ~(1u << nbuf);
+        ++npref;
+      } else {
+        if (pr.x >= 0) freeb |= 1u << pr.x;
+        nbuf = __ffs(freeb) - 1;
+        freeb &= ~(1u << nbuf);
+        if ((pend >> nbuf) & 1u) {
+          wait_buf(nbuf);
+          pend &= ~(1u << nbuf);
+        }
+        if (slot < cslots) {
+          if (lane == 0) {
+            fence_proxy_async_shared();
+            mbar_expect_tx(&sbar[nbuf], rec.jr);
+            bulk_g2s(sbuf + (size_t)nbuf * SL.jr, gJR + (size_t)slot * rec.jr, rec.jr,
+                     &sbar[nbuf]);
+          }
+          wait_buf(nbuf);
+        } else {
+          // no records for this slot: rebuild from its state (the old
+          // state's buffer is the scratch)
+          uint32_t *xn = bX(nbuf);
+          for (int q2 = lane; q2 < rec.mp / 32; q2 += 32)
+            xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
+          __syncwarp();
+          int64_t t1, t2, gp;
+          rebuild(nbuf, cur, gWork, t1, t2, gp);
+        }
+        ++ndirect;
+      }
+      freeb |= 1u << cur;
+      cur = nbuf;
+      if (slot < cslots) {
+        curL = gLR + (size_t)slot * rec.mp;
+        const int64_t *be = bE(cur);
+        E1 = be[0];
+        E2 = be[1];
+      } else {
+        curL = gWork;
+        E1 = gE[2 * slot];
+        E2 = gE[2 * slot + 1];
+      }
+      ++njump;
+    } else {
+      if (pr.x >= 0) freeb |= 1u << pr.x;
+      ++nempty;  // empty archive: the state stays (R12)
+    }
+    flip_streak = kind == 1 ? flip_streak + 1 : 0;
+    if (R.trace != nullptr && lane == 0) {
+      int64_t *tr = R.trace + ((size_t)row * (size_t)I_max + (size_t)(t - 1)) * 3;
+      tr[0] = E1;
+      tr[1] = E2;
+      tr[2] = kind == 1 ? (int64_t)ps : kind == 2 ? -1 - (int64_t)event_slot : INT64_MIN;
+    }
+    if (fail) break;
+    __syncwarp();
+  }
+  // no bulk copy may be in flight when the item ends
+  for (int b = 0; b < NB; ++b)
+    if ((pend >> b) & 1u) wait_buf(b);
+  if (fail) {
+    if (lane == 0) atomicExch(R.error, kErrCopyTimeout);
+    return false;
+  }
+  const uint32_t *xw = bX(cur);
+  for (int q2 = lane; q2 < W; q2 += 32) R.x_final[(size_t)row * W + q2] = xw[q2];
+  if (lane == 0) {
+    R.E_final[2 * row] = E1;
+    R.E_final[2 * row + 1] = E2;
+    R.arch_count[row] = acount;
+    int64_t *st = R.stats + (size_t)kStats * row;
+    st[0] = nflip;
+    st[1] = njump;
+    st[2] = nempty;
+    st[3] = 0;
+    st[4] = npref;
+    st[5] = ndirect;
+    st[6] = 0;
+    st[7] = 0;
+  }
+  __syncwarp();
+  return true;
+}
+
+template <bool NARROW>
+__global__ void __launch_bounds__(256) warp_anneal_kernel(const WarpLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  unsigned char *ws = smem + (size_t)wid * L.sm.total;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L.sm.mbar);
+  if (lane == 0) {
+    for (int b = 0; b < L.nbuf; ++b) mbar_init(&bar[b], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  unsigned char *cache = L.cache + (size_t)(blockIdx.x * NW + wid) * L.cache_stride;
+  uint32_t par = 0;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(L.counter, 1);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= L.nitems) break;
+    const int2 item = L.items[it];
+    const WarpRun &R = L.runs[item.x];
+    if ((R.narrow != 0) != NARROW) {  // the host launches matching variants only
+      if (lane == 0) atomicExch(R.error, kErrVariant);
+      continue;
+    }
+    if (!warp_run<NARROW>(R, item.y, ws, L, cache, lane, par)) break;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int warps,
+                        cudaStream_t stream) {
+  if (warps < 1 || warps > 8 || grid < 1) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)warps * L.sm.total;
+  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
+                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (narrow)
+    warp_anneal_kernel<true><<<grid, 32 * warps, smem, stream>>>(L);
+  else
+    warp_anneal_kernel<false><<<grid, 32 * warps, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t warp_function(bool narrow, size_t smem, const void **func) {
+  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
+                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) *func = f;
+  return e;
+}
+
+cudaError_t warp_occupancy(bool narrow, int warps, size_t smem, int *blocks) {
+  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
+                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, 32 * warps, smem);
+}
+
+}  // namespace moda

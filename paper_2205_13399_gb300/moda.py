@@ -24,6 +24,7 @@ ACCEPT = {"strict": 0, "lenient": 1}
 ARCHIVE = {"explore": 0, "exploit": 1}
 ESCAPE = {"archive": 0, "offset": 1}
 FIELD_CACHE = {"auto": 0, "on": 1, "off": 2}
+ENGINE = {"auto": 0, "block": 1, "warp": 2}
 
 # Functions declared in include/moda.h.
 ABI_FUNCTIONS = [
@@ -71,6 +72,7 @@ class Params(ctypes.Structure):
         ("normalize", ctypes.c_int32),
         ("snapshot_every", ctypes.c_int32),
         ("fast_forward", ctypes.c_int32),
+        ("engine", ctypes.c_int32),
     ]
 
 
@@ -351,14 +353,14 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
                 trace: bool = False, field_cache: str = "auto", prefetch: int = 0,
                 normalize: bool = False, snapshot_every: int = 0,
-                fast_forward: bool = False) -> Params:
+                fast_forward: bool = False, engine: str = "auto") -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
                   int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)),
-                  int(snapshot_every), int(bool(fast_forward)))
+                  int(snapshot_every), int(bool(fast_forward)), ENGINE[engine])
 
 
 def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,

@@ -12,7 +12,8 @@ import oracle
 def gpu_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explore",
             escape="archive", delta0=1e9, deltaf=1e4, xi=1e-3, beta=None, archive_size=0,
             replica_base=0, block_threads=0, trace=False, w=None, stream=None,
-            field_cache="auto", prefetch=0, normalize=False, fast_forward=False):
+            field_cache="auto", prefetch=0, normalize=False, fast_forward=False,
+            engine="auto"):
     from paper_2205_13399_gb300 import moda
     inst = moda.Instance(inst_np.F1, inst_np.F2, inst_np.D, w=w)
     run = moda.anneal(inst, replicas=replicas, I_max=I_max, seed=seed, accept=accept,
@@ -20,7 +21,7 @@ def gpu_run(inst_np, *, replicas, I_max, seed=0, accept="strict", archive="explo
                       beta=beta, archive_size=archive_size, replica_base=replica_base,
                       block_threads=block_threads, trace=trace, stream=stream,
                       field_cache=field_cache, prefetch=prefetch, normalize=normalize,
-                      fast_forward=fast_forward)
+                      fast_forward=fast_forward, engine=engine)
     run.wait()
     res = run.read()
     traces = None

@@ -7,9 +7,17 @@ import pytest
 
 import oracle
 from paper_2205_13399_gb300 import inputs
-from parity import compare, gpu_run, oracle_merged_front, oracle_run
+from parity import compare, oracle_merged_front, oracle_run
+from parity import gpu_run as _gpu_run
 
 pytestmark = pytest.mark.gpu
+
+
+def gpu_run(*args, **kw):
+    """These tests cover the block engine (one thread block per replica);
+    tests/test_gpu_warp.py covers the warp engine."""
+    kw.setdefault("engine", "block")
+    return _gpu_run(*args, **kw)
 
 VARIANTS = [(acc, arc, esc) for acc in ("strict", "lenient")
             for arc in ("explore", "exploit") for esc in ("archive", "offset")]
@@ -291,12 +299,19 @@ def test_autotune_picks_a_layout_with_identical_results():
     inst = inputs.uniform_instance(20, index=8, workload="P8")
     g = moda.Instance(inst.F1, inst.F2, inst.D)
     kw = dict(replicas=4, I_max=2500, seed=3, **FAST)
-    best, ms = moda.autotune(g, trial_iters=500, **kw)
+    best, ms = moda.autotune(g, trial_iters=500, engine="block", **kw)
     assert best.block_threads % 32 == 0 and 32 <= best.block_threads <= 960
     assert best.prefetch in (0, 2, 3) and ms > 0
     assert best.replicas == 4 and best.I_max == 2500
     a = moda.anneal(g, params=best).wait().read()
     b = moda.anneal(g, **kw).wait().read()
+    for key in ("count", "E", "bits", "x", "E_final"):
+        assert np.array_equal(getattr(a, key), getattr(b, key)), key
+    assert np.array_equal(a.stats[:, :4], b.stats[:, :4])
+    # the warp engine: a prefetch distance, no block shape
+    best, ms = moda.autotune(g, trial_iters=500, **kw)
+    assert best.block_threads == 0 and best.prefetch in (1, 2, 3) and ms > 0
+    a = moda.anneal(g, params=best).wait().read()
     for key in ("count", "E", "bits", "x", "E_final"):
         assert np.array_equal(getattr(a, key), getattr(b, key)), key
     assert np.array_equal(a.stats[:, :4], b.stats[:, :4])

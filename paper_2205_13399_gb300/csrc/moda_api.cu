@@ -875,14 +875,15 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   int sms = 1, optin = 0;
   MODA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   MODA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Block shape: the most resident warps (ties: more warps per block),
+  // Block shape: the most resident warps (ties: fewer warps per block, so
+  // that a launch with fewer replicas than SMs spreads one warp per SM),
   // shrinking the on-chip archive energies, then the prefetch distance,
   // until one warp's shared memory fits.
   int best_w = 0, best_blocks = 0, se_max = std::min(s_max, kWarpSmemEnergies);
   moda::WarpSmem sm{};
   for (int attempt = 0; attempt < 8 && best_w == 0; ++attempt) {
     sm = moda::warp_smem(n_max, m_max, se_max, la + 2);
-    for (int nw : {4, 2, 1}) {
+    for (int nw : {1, 2, 4}) {
       const size_t smem = (size_t)nw * sm.total;
       if ((int64_t)smem > optin) continue;
       int blocks = 0;

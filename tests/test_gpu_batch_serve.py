@@ -158,3 +158,30 @@ def test_server_rejects_a_request_larger_than_the_budget():
                 break
             time.sleep(0.005)
     srv.close()
+
+
+def test_server_overlaps_staggered_arrivals():
+    """Continuous batching: requests submitted one by one while earlier ones
+    are on the GPU are admitted at once and run beside them (the server
+    reports two or more running at some moment), and every result equals
+    the request's plain run, bit for bit."""
+    from paper_2205_13399_gb300 import moda
+    qis = [inputs.uniform_instance(n, index=500 + n, workload="P8") for n in (20, 26, 14, 31, 9, 23)]
+    insts = [moda.Instance(q.F1, q.F2, q.D) for q in qis]
+    kws = [dict(replicas=16 + 4 * k, I_max=60000, seed=70 + k, accept=("strict", "lenient")[k % 2],
+                archive=("explore", "exploit")[k // 3], **FAST) for k in range(len(qis))]
+    srv = moda.Server()
+    seen = []
+    tickets = []
+    for k, (inst, kw) in enumerate(zip(insts, kws)):
+        tickets.append(srv.submit(inst, **kw))
+        # the next request arrives while this one (and its predecessors) run
+        t0 = time.time()
+        while time.time() - t0 < 0.01:
+            seen.append(srv.info()["running"])
+            time.sleep(0.001)
+    done = _drain(srv, tickets, watch=lambda i: seen.append(i["running"]))
+    assert max(seen) >= 2, seen
+    for t, inst, kw in zip(tickets, insts, kws):
+        _same(done[t], _plain(inst, kw))
+    srv.close()

@@ -38,7 +38,10 @@ def test_warp_prefetch_distances(prefetch):
     _, _, res, tr = gpu_run(inst, trace=True, prefetch=prefetch, engine="warp", **kw)
     _, orc = oracle_run(inst, trace=True, **kw)
     compare(res, range(5), orc, 23 * 23, gpu_trace=tr)
-    assert res.stats[:, 4].sum() > 0  # some jumps took a prefetched record
+    if prefetch > 1:  # copies started ahead: some jumps took a prefetched record
+        assert res.stats[:, 4].sum() > 0
+    else:
+        assert res.stats[:, 4].sum() == 0
 
 
 def test_warp_small_archive_and_replica_base():

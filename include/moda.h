@@ -152,7 +152,11 @@ typedef struct {
                               none); a jump to a slot without records
                               rebuilds its fields.  prefetch k in 1..3 copies
                               a jump's target k - 1 iterations ahead (0:
-                              auto, 2 iterations).
+                              auto, 2 iterations).  A team of G warps (1 to
+                              8) runs each replica: automatically the
+                              largest G that keeps every replica resident
+                              at once, else 1; block_threads = 32 G
+                              prescribes it.
                             0 auto: warp when the options allow it and
                               block_threads is 0, else block. */
 } moda_params;

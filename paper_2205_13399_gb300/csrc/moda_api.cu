@@ -481,8 +481,8 @@ moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStrea
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kWarpMaxLA + 1)
     return fail(MODA_EINVAL, "prefetch must be in [0, 3] for the warp engine");
-  if (p->block_threads != 0)
-    return fail(MODA_EINVAL, "block_threads applies to the block engine only");
+  if (p->block_threads < 0 || p->block_threads % 32 || p->block_threads > 256)
+    return fail(MODA_EINVAL, "warp engine: block_threads must be 32 G, G in 1..8 (0: auto)");
   cudaSetDevice(inst->device);
   moda_run r = new (std::nothrow) moda_run_s;
   if (!r) return fail(MODA_ENOMEM, "host allocation");
@@ -875,34 +875,57 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   int sms = 1, optin = 0;
   MODA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   MODA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Block shape: the most resident warps (ties: fewer warps per block, so
-  // that a launch with fewer replicas than SMs spreads one warp per SM),
-  // shrinking the on-chip archive energies, then the prefetch distance,
-  // until one warp's shared memory fits.
+  // Team shape (one team of G warps per block): the largest G (at most one
+  // warp per 128-bit chunk) and prefetch distance whose resident teams hold
+  // every replica at once, so that few replicas run with short
+  // iterations; when even single warps cannot hold them all, single warps
+  // (the most replicas in flight).  The on-chip archive energies shrink if
+  // nothing fits.
   int best_w = 0, best_blocks = 0, se_max = std::min(s_max, kWarpSmemEnergies);
+  const int nc_max = (m_max + 127) / 128;
+  const int la_max = la;
   moda::WarpSmem sm{};
-  for (int attempt = 0; attempt < 8 && best_w == 0; ++attempt) {
-    sm = moda::warp_smem(n_max, m_max, se_max, la + 2);
-    for (int nw : {1, 2, 4}) {
-      const size_t smem = (size_t)nw * sm.total;
-      if ((int64_t)smem > optin) continue;
+  auto resident = [&](int G, int la_try, int se_try, int *blocks, moda::WarpSmem *out) {
+    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, la_try + 2, G);
+    *blocks = 0;
+    if ((int64_t)L.total > optin) return false;
+    if (moda::warp_occupancy(narrow, 32 * G, L.total, blocks) != cudaSuccess || *blocks < 1)
+      return false;
+    *out = L;
+    return true;
+  };
+  // params.block_threads = 32 G prescribes the team size
+  const int forced = r0->prm.block_threads / 32;
+  for (int gsz = forced > 0 ? forced : std::min(8, nc_max); gsz >= 1 && best_w == 0; --gsz)
+    for (int la_try = la_max; la_try >= 0 && best_w == 0; --la_try) {
       int blocks = 0;
-      if (moda::warp_occupancy(narrow, nw, smem, &blocks) != cudaSuccess || blocks < 1) continue;
-      if (blocks * nw > best_blocks * best_w) {
-        best_w = nw;
+      moda::WarpSmem L{};
+      if (resident(gsz, la_try, se_max, &blocks, &L) &&
+          ((int64_t)blocks * sms >= items_total || forced > 0)) {
+        best_w = gsz;
         best_blocks = blocks;
+        la = la_try;
+        sm = L;
       }
     }
-    if (best_w == 0) {
-      if (se_max > 64) se_max = 64;
-      else if (la > 0) --la;
-      else break;
+  for (int attempt = 0; attempt < 2 && best_w == 0; ++attempt) {
+    // throughput: single warps, the most resident
+    for (int la_try = la_max; la_try >= 0; --la_try) {
+      int blocks = 0;
+      moda::WarpSmem L{};
+      if (resident(1, la_try, se_max, &blocks, &L) && blocks > best_blocks) {
+        best_w = 1;
+        best_blocks = blocks;
+        la = la_try;
+        sm = L;
+      }
     }
+    if (best_w == 0) se_max = std::min(se_max, 64);
   }
   if (best_w == 0) return fail(MODA_EUNSUPPORTED, "warp engine: shared memory need exceeds the device");
-  const int64_t resident = (int64_t)best_blocks * sms;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, (items_total + best_w - 1) / best_w));
-  const size_t warps = (size_t)grid * best_w;
+  const int64_t resident_teams = (int64_t)best_blocks * sms;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_teams, items_total));
+  const size_t warps = (size_t)grid;  // teams, one per block
   // Field-cache slots per run: all (field_cache = 1), none (2), or up to
   // kWarpCacheSlots, fewer if the launch's caches would exceed the budget.
   std::vector<int> cs(idx.size());
@@ -976,6 +999,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.nitems = (int32_t)items.size();
   L.lookahead = la;
   L.nbuf = la + 2;
+  L.team = best_w;
   L.counter = reinterpret_cast<int32_t *>(base + d_bytes + i_bytes);
   L.cache = static_cast<unsigned char *>(scratch->cache);
   L.cache_stride = stride;
@@ -984,13 +1008,13 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
     moda_run r = runs[k];
     MODA_CUDA(cudaMemsetAsync(r->error, 0, sizeof(int32_t), stream));
     r->wscratch = scratch;
-    r->threads = best_w;  // warps per block
+    r->threads = best_w;  // warps per replica
     r->bpt = grid;
   }
   G.L = L;
   G.narrow = narrow;
   G.grid = grid;
-  G.warps = best_w;
+  G.warps = 1;  // teams per block
   G.scratch = scratch;
   guard.armed = false;
   return MODA_OK;
@@ -1394,7 +1418,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
       cudaKernelNodeParams kp{};
       kp.func = const_cast<void *>(func);
       kp.gridDim = dim3((unsigned)G.grid);
-      kp.blockDim = dim3((unsigned)(32 * G.warps));
+      kp.blockDim = dim3((unsigned)(32 * G.warps * G.L.team));
       kp.sharedMemBytes = (unsigned)smem;
       kp.kernelParams = kargs;
       kp.extra = nullptr;

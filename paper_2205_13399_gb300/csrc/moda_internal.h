@@ -222,13 +222,15 @@ cudaError_t launch_anneal_special(const AnnealArgs &args, int replicas, int work
 cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t smem,
                                     const void **func);
 
-// ---- the warp annealer: one warp per replica -------------------------------
+// ---- the warp annealer: a team of G warps per replica ----------------------
 //
-// A throughput form of the same loop: each warp runs one replica by itself
-// (no block barriers), pulling (run, replica) work items from a device
-// list.  Bit p of a replica belongs to lane (p % 128) / 4 of chunk p / 128,
-// so a lane holds 4 consecutive bits of every chunk (one acceptance Philox
-// block: bits 4g .. 4g + 3 take the words of block g).  The state a trial
+// A throughput form of the same loop: each team of G warps (G = 1 .. 8)
+// runs one replica, synchronised by a named barrier of its own (no block
+// barriers), pulling (run, replica) work items from a device list.  Warp w
+// of a team owns a contiguous range of 128-bit chunks; bit p of a chunk
+// belongs to lane (p % 128) / 4, so a lane holds 4 consecutive bits of
+// each chunk (one acceptance Philox block: bits 4g .. 4g + 3 take the words
+// of block g).  The state a trial
 // reads is, per bit, its acceptance penalty a (strict: sum_k max(0, dE_k);
 // lenient: min_k max(0, dE_k)) saturated to uint32; the integer cost fields
 // L_k (int32 pairs) live in global memory and are read only by flips.
@@ -261,17 +263,20 @@ __host__ __device__ inline WarpRec warp_rec(int n, int m) {
   return r;
 }
 
-// Shared-memory carve-up of one warp (byte offsets), sized for the largest
-// run of a launch: nbuf jump-record buffers, their mbarriers, the ring of
-// draws and schedule entries, the archive energies of slots < se, the
-// flow and distance rows of a flip, the accepted-chunk list and the
-// prefetch bookkeeping.
+// Shared-memory carve-up of one team (the G warps that run one replica),
+// sized for the largest run of a launch: nbuf jump-record buffers, their
+// mbarriers, the ring of draws and schedule entries, the archive energies
+// of slots < se, the prefetch bookkeeping and the warps' accepted counts;
+// then per warp its accepted-chunk list, the flow and distance rows of a
+// flip and its copy of the row and column counts.
 struct WarpSmem {
   uint32_t jr;     // buffer stride
-  uint32_t buf, mbar, ring, aE, rows, acc, pf, total;
+  uint32_t buf, mbar, ring, aE, cnt, team;        // team part (bytes: team)
+  uint32_t acc, rows, rc, pf, warp;               // warp part (bytes: warp)
   int32_t nc_max;
+  uint32_t total;  // team + G warps
 };
-__host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf) {
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G) {
   const WarpRec r = warp_rec(n_max, m_max);
   WarpSmem L;
   size_t o = 0;
@@ -281,10 +286,17 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nbuf, 16);
   L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
   L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
+  // accepted counts of the warps by iteration parity [2][8], the work
+  // item, the warps' partial sums of a rebuild [8][2]
+  L.cnt = (uint32_t)o;       o = align_up(o + 64 + 16 + 128, 16);
+  L.team = (uint32_t)o;
+  o = 0;
+  L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
-  L.acc = (uint32_t)o;       o = align_up(o + 20 * (size_t)r.nc, 16);
+  L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
   L.pf = (uint32_t)o;        o = align_up(o + 16 * 4 + 4 * 4, 16);
-  L.total = (uint32_t)o;
+  L.warp = (uint32_t)o;
+  L.total = L.team + (uint32_t)G * L.warp;
   return L;
 }
 
@@ -321,30 +333,30 @@ struct WarpLaunch {
   const WarpRun *runs;
   const int2 *items;         // (run, replica row), largest runs first
   int32_t nitems;
-  int32_t nbuf;              // jump-record buffers per warp: lookahead + 2
+  int32_t nbuf;              // jump-record buffers per team: lookahead + 2
   int32_t lookahead;         // prefetch distance, 0 .. kWarpMaxLA
-  int32_t pad;
+  int32_t team;              // G: warps per replica (1 .. 8)
   int32_t *counter;          // next item; zero before the launch
-  unsigned char *cache;      // field-cache region of each resident warp
-  size_t cache_stride;       // bytes per warp
-  WarpSmem sm;               // per-warp shared memory
+  unsigned char *cache;      // field-cache region of each resident team
+  size_t cache_stride;       // bytes per team
+  WarpSmem sm;               // shared memory of one team
 };
 
-// Field-cache bytes of one warp for a run: cslots jump and field records
+// Field-cache bytes of one team for a run: cslots jump and field records
 // plus a working field record.
 inline size_t warp_cache_bytes(int n, int m, int cslots) {
   const WarpRec r = warp_rec(n, m);
   return (size_t)cslots * ((size_t)r.jr + r.lr) + r.lr;
 }
 
-// Launches the warp annealer: `grid` blocks of `warps` warps.
-cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int warps,
+// Launches the warp annealer: `grid` blocks of `teams` teams of L.team warps.
+cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
                         cudaStream_t stream);
 // The warp annealer's kernel (one WarpLaunch argument) for a CUDA graph
 // node, with `smem` bytes of dynamic shared memory allowed.
 cudaError_t warp_function(bool narrow, size_t smem, const void **func);
-// Resident blocks per SM of the warp annealer for this shape.
-cudaError_t warp_occupancy(bool narrow, int warps, size_t smem, int *blocks);
+// Resident blocks per SM of the warp annealer for blocks of `threads`.
+cudaError_t warp_occupancy(bool narrow, int threads, size_t smem, int *blocks);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);

@@ -1,25 +1,30 @@
 // The warp annealer: Alg. 3 of arXiv 2205.13399 (the multi-objective
-// Digital Annealer, Sec. 3.3) for the bi-objective QAP with one warp per
-// replica.  A persistent grid of warps pulls (run, replica) work items from
-// a device list (largest runs first), so replicas of many instances of
-// uneven n share the GPU in one launch, and no warp ever waits at a block
-// barrier.
+// Digital Annealer, Sec. 3.3) for the bi-objective QAP with a team of G
+// warps (G = 1 .. 8) per replica.  A persistent grid of teams pulls (run,
+// replica) work items from a device list (largest runs first), so replicas
+// of many instances of uneven n share the GPU in one launch; a team
+// synchronises on a named barrier of its own, never on a block barrier.
+// G = 1 suits launches with many more replicas than SMs (each warp a
+// replica); larger G shortens one replica's iteration when replicas are
+// few.
 //
 // State of a replica, the current point x of Alg. 3:
 //   shared memory  its jump record: per bit the acceptance penalty
 //                  a(p) = sum_k max(0, dE_k(p)) (strict, Eq. pacceptms) or
 //                  min_k max(0, dE_k(p)) (lenient, Eq. pacceptml),
 //                  saturated to uint32; the state words; the row and column
-//                  counts R_i, C_u;
+//                  counts R_i, C_u (each warp keeps its own copy of these);
 //   global memory  its cost fields L_k(i,u) = sum_(j,v) Fs^k_ij d_uv x_jv
 //                  (Fs^k = F^k + F^k^T), int32 pairs;
-//   registers      E_1, E_2 and |A|.
+//   registers      E_1, E_2, |A| and the buffer bookkeeping, the same in
+//                  every warp of the team.
 // With h = R_i + C_u - 1 - 2 x_p and alpha_k = w_k / 2 (Eq. wqubom),
 //   dE_k(p) = (1 - 2 x_p) (L_k(p) + w_k h)                         (Eq. cale),
 // so a trial needs only a(p): bit p is accepted iff (double) a <=
 // delta_t T[idx] (R7), decided by a <= lo_t or a > hi_t without a draw
-// (R21).  Bit p of chunk c = p / 128 belongs to lane (p % 128) / 4, which
-// owns bits 4g .. 4g + 3 of Philox group g = p / 4: one block per lane.
+// (R21).  Warp w of a team owns a contiguous range of 128-bit chunks; bit p
+// of chunk c = p / 128 belongs to lane (p % 128) / 4, which owns bits
+// 4g .. 4g + 3 of Philox group g = p / 4: one block per lane.
 //
 // A flip of bit (j, v) with s = +1 when it turns on adds s Fs^k_ij d_uv to
 // every L_k(i, u) -- the outer product of flow row j and distance row v, so
@@ -48,6 +53,22 @@ struct WRing {
 };
 static_assert(sizeof(WRing) == 40, "ring entry layout");
 
+// Named barrier `id` (1 .. 15) of `threads` threads; returns whether `v`
+// held in any of them.
+__device__ __forceinline__ bool team_sync_or(int id, int threads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(threads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void team_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 template <bool NARROW>
 struct WarpAnnealer {
   using dE_t = typename std::conditional<NARROW, int32_t, int64_t>::type;
@@ -65,17 +86,31 @@ struct WarpAnnealer {
   }
 };
 
-// Runs replica `row` of run R on this warp for all I_max iterations.
-// `par` holds the phase parity of the warp's mbarriers across items.
-// Returns false when a bounded wait gave up (the error word is set).
+// The team's shape within its block.
+struct Team {
+  int G, wt, lane;     // warps per team, this warp's index in it, lane
+  int bar;             // named barrier id (G > 1)
+  unsigned char *ts;   // team shared memory
+  unsigned char *ws0;  // warp 0's shared memory (warp w at ws0 + w * SL.warp)
+};
+
+// Runs replica `row` of run R on this team for all I_max iterations.
+// `par` holds the phase parity of the team's mbarriers across items (the
+// same in every warp).  Returns false when a bounded wait gave up (the
+// error word is set).
 template <bool NARROW>
-__device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, const WarpLaunch &Lc,
-                         unsigned char *cache, const int lane, uint32_t &par) {
+__device__ bool team_run(const WarpRun &R, const int row, const Team &T, const WarpLaunch &Lc,
+                         unsigned char *cache, uint32_t &par) {
   using WA = WarpAnnealer<NARROW>;
   using dE_t = typename WA::dE_t;
+  const int lane = T.lane, G = T.G, wt = T.wt;
+  const bool leader = wt == 0;
   const int n = R.n, m = R.m, W = R.W, s = R.s;
   const WarpRec rec = warp_rec(n, m);
   const int NC = rec.nc;
+  // this warp's chunks [c0, c1): contiguous, so the team's accepted bits
+  // in (warp, chunk, lane) order are in ascending bit order
+  const int c0 = wt * NC / G, c1 = (wt + 1) * NC / G;
   const int cslots = R.cslots, se = R.se;
   const uint32_t rep = R.replica_base + (uint32_t)row;
   const uint32_t k0 = R.seed_lo, k1 = R.seed_hi;
@@ -88,23 +123,41 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
   const uint32_t magic = R.magic;
   const int LA = Lc.lookahead, NB = Lc.nbuf;
   const WarpSmem &SL = Lc.sm;
+  const double *const table = R.table;
+  int64_t *const trace = R.trace;
+  const int team_threads = 32 * G;
+  auto sync = [&]() {
+    if (G > 1) team_sync(T.bar, team_threads);
+    else __syncwarp();
+  };
+  auto sync_or = [&](bool v) -> bool {
+    if (G > 1) return team_sync_or(T.bar, team_threads, v);
+    return __any_sync(kFull, v);
+  };
 
-  unsigned char *sbuf = ws + SL.buf;
-  uint64_t *sbar = reinterpret_cast<uint64_t *>(ws + SL.mbar);
-  WRing *ring = reinterpret_cast<WRing *>(ws + SL.ring);
-  longlong2 *sAE = reinterpret_cast<longlong2 *>(ws + SL.aE);
-  int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
-  uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
-  int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
-  // prefetch bookkeeping: sPf[tt & 3] = {buffer or -1, slot, issuing
-  // iteration} of the copy for target iteration tt; sWr[x & 3] = the slot
-  // iteration x wrote (-1: none)
+  unsigned char *ts = T.ts;
+  unsigned char *sbuf = ts + SL.buf;
+  uint64_t *sbar = reinterpret_cast<uint64_t *>(ts + SL.mbar);
+  WRing *ring = reinterpret_cast<WRing *>(ts + SL.ring);
+  longlong2 *sAE = reinterpret_cast<longlong2 *>(ts + SL.aE);
+  // accepted counts of the warps, [iteration parity][warp]: a warp may
+  // write its next count while another still reads this iteration's
+  int32_t *sCnt = reinterpret_cast<int32_t *>(ts + SL.cnt);
+  int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 80);  // [G][2] rebuild sums
+  unsigned char *ws = T.ws0 + (size_t)wt * SL.warp;
+  // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 3]
+  // = {buffer or -1, slot, issuing iteration} of the copy for target
+  // iteration tt; sWr[x & 3] = the slot iteration x wrote (-1: none)
   int4 *sPf = reinterpret_cast<int4 *>(ws + SL.pf);
   int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 64);
+  uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
+  int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
+  int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
+  unsigned char *rcp = ws + SL.rc;  // this warp's row and column counts of the state
 
   int64_t *gE = R.arch_E + (size_t)row * s * 2;
   uint32_t *gB = R.arch_bits + (size_t)row * s * W;
-  unsigned char *gJR = cache;                                           // [cslots] jump records
+  unsigned char *gJR = cache;                                             // [cslots] jump records
   int2 *gLR = reinterpret_cast<int2 *>(cache + (size_t)cslots * rec.jr);  // [cslots][mp]
   int2 *gWork = gLR + (size_t)cslots * rec.mp;                            // [mp] working fields
   const int32_t *Fs1 = R.Fs1, *Fs2 = R.Fs2, *Dm = R.D;
@@ -119,9 +172,10 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
   };
   auto divn = [&](int p) { return (int)__umulhi((uint32_t)p, magic); };
 
-  // Iterations first .. first + 31 into the ring: schedule entry (Alg. 3's
-  // cooling, the last entry held once delta reaches delta_f) and the draws
-  // (0, q, replica, tag) of the select, restart and exploit purposes.
+  // Iterations first .. first + 31 into the ring (leader warp): schedule
+  // entry (Alg. 3's cooling, the last entry held once delta reaches
+  // delta_f) and the draws (0, q, replica, tag) of the select, restart and
+  // exploit purposes.
   auto fill = [&](uint32_t first) {
     const uint32_t q = first + (uint32_t)lane;
     const uint32_t sn = (q <= nsched ? q : nsched) - 1u;
@@ -145,11 +199,17 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
     ring[q % kWarpRing] = e;
   };
 
-  // Row and column counts of the state in buffer b.
-  auto counts = [&](int b) {
+  // Fields and penalties of the state in buffer b from scratch (Alg. 3's
+  // initial state, or a jump to a slot without records), by the whole
+  // team: the row and column counts into the buffer and every warp's copy,
+  // M = X D in the a-array of buffer sc, then L_k(i,u) = sum_j Fs^k_ij M_ju
+  // into gL and a(p) into buffer b.  Returns sum over set bits of L_1 and
+  // of L_2 (2 c_k) and g (Eq. gqap), team totals.  Ends on a team barrier.
+  auto rebuild = [&](int b, int sc, int2 *gL, int64_t &t1, int64_t &t2, int64_t &gp) {
     const uint32_t *xw = bX(b);
     unsigned char *rc = bRC(b);
-    for (int i = lane; i < n; i += 32) {
+    const int tid = wt * 32 + lane;
+    for (int i = tid; i < n; i += team_threads) {
       int cr = 0, cc = 0;
       for (int u = 0; u < n; ++u) {
         const int p = i * n + u, q = u * n + i;
@@ -159,20 +219,8 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       rc[i] = (unsigned char)cr;
       rc[n + i] = (unsigned char)cc;
     }
-    __syncwarp();
-  };
-
-  // Fields and penalties of the state in buffer b from scratch (Alg. 3's
-  // initial state, or a jump to a slot without records): M = X D in the
-  // a-array of buffer sc, then L_k(i,u) = sum_j Fs^k_ij M_ju into gL and
-  // a(p) into buffer b.  Returns sum over set bits of L_1, of L_2 (2 c_k)
-  // and g (Eq. gqap), warp totals.
-  auto rebuild = [&](int b, int sc, int2 *gL, int64_t &t1, int64_t &t2, int64_t &gp) {
-    counts(b);
-    const uint32_t *xw = bX(b);
-    const unsigned char *rc = bRC(b);
     int32_t *M = reinterpret_cast<int32_t *>(bA(sc));
-    for (int e = lane; e < n * n; e += 32) {
+    for (int e = tid; e < n * n; e += team_threads) {
       const int j = divn(e), u = e - j * n;
       int32_t acc = 0;
       for (int v = 0; v < n; ++v) {
@@ -181,11 +229,13 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       }
       M[e] = acc;
     }
+    sync();
+    for (int e = lane; e < 2 * n; e += 32) rcp[e] = rc[e];
     __syncwarp();
     uint32_t *ab = bA(b);
     t1 = 0;
     t2 = 0;
-    for (int p = lane; p < rec.mp; p += 32) {
+    for (int p = c0 * 128 + lane; p < c1 * 128; p += 32) {
       uint32_t a = 0xFFFFFFFFu;
       int2 L = make_int2(0, 0);
       if (p < m) {
@@ -199,7 +249,7 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
         L = make_int2(a1, a2);
         const int xv = (int)((xw[p >> 5] >> (p & 31)) & 1u);
         const dE_t g = (dE_t)(1 - 2 * xv);
-        const dE_t h = (dE_t)rc[i] + (dE_t)rc[n + u] - 1 - 2 * xv;
+        const dE_t h = (dE_t)rcp[i] + (dE_t)rcp[n + u] - 1 - 2 * xv;
         a = WA::penalty(g * ((dE_t)a1 + w1 * h), g * ((dE_t)a2 + w2 * h), lenient);
         if (xv) {
           t1 += a1;
@@ -209,18 +259,28 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       gL[p] = L;
       ab[p] = a;
     }
-    gp = 0;
-    for (int i = lane; i < n; i += 32) {
-      const int64_t dr = 1 - (int64_t)rc[i], dc = 1 - (int64_t)rc[n + i];
-      gp += dr * dr + dc * dc;
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       t1 += __shfl_xor_sync(kFull, t1, o);
       t2 += __shfl_xor_sync(kFull, t2, o);
-      gp += __shfl_xor_sync(kFull, gp, o);
     }
-    __syncwarp();
+    if (lane == 0) {
+      sSum[2 * wt] = t1;
+      sSum[2 * wt + 1] = t2;
+    }
+    sync();
+    t1 = 0;
+    t2 = 0;
+    for (int w = 0; w < G; ++w) {
+      t1 += sSum[2 * w];
+      t2 += sSum[2 * w + 1];
+    }
+    gp = 0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t dr = 1 - (int64_t)rcp[i], dc = 1 - (int64_t)rcp[n + i];
+      gp += dr * dr + dc * dc;
+    }
+    sync();  // the scratch and the sums may be reused after this
   };
 
   // Exact penalty of bit p of the state in buffer b with fields gL (only
@@ -229,9 +289,8 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
     const int2 L = gL[p];
     const int i = divn(p), u = p - i * n;
     const uint32_t *xw = bX(b);
-    const unsigned char *rc = bRC(b);
     const int xv = (int)((xw[p >> 5] >> (p & 31)) & 1u);
-    const int64_t g = 1 - 2 * xv, h = (int64_t)rc[i] + rc[n + u] - 1 - 2 * xv;
+    const int64_t g = 1 - 2 * xv, h = (int64_t)rcp[i] + rcp[n + u] - 1 - 2 * xv;
     const int64_t e1 = g * ((int64_t)L.x + w1l * h), e2 = g * ((int64_t)L.y + w2l * h);
     const int64_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
     return lenient ? (u1 < u2 ? u1 : u2) : u1 + u2;
@@ -243,6 +302,14 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
     if (!__all_sync(kFull, ok)) fail = true;
     par ^= 1u << b;
   };
+  // the leader's lane 0 starts the copy of slot y's jump record into b
+  auto copy_record = [&](int b, int y) {
+    if (leader && lane == 0) {
+      fence_proxy_async_shared();
+      mbar_expect_tx(&sbar[b], rec.jr);
+      bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)y * rec.jr, rec.jr, &sbar[b]);
+    }
+  };
 
   // ---- initial state (Alg. 3: "a random binary solution", R10) ----------
   // Chunk c's 128 bits are the four words of Philox block (c, 0, replica,
@@ -250,7 +317,7 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
   int cur = 0;
   {
     uint32_t *x0 = bX(0);
-    for (int c = lane; c < NC; c += 32) {
+    for (int c = c0 + lane; c < c1; c += 32) {
       uint32_t b[4] = {(uint32_t)c, 0u, rep, kTagInit};
       philox10(b, k0, k1);
 #pragma unroll
@@ -262,7 +329,15 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
         x0[4 * c + w] = v;
       }
     }
-    __syncwarp();
+    if (lane < 4) {
+      sPf[lane] = make_int4(-1, 0, 0, 0);
+      sWr[lane] = -1;
+    }
+    if (leader) {
+      fill(1);
+      fill(33);
+    }
+    sync();
   }
   int64_t E1, E2;
   {
@@ -277,16 +352,9 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
   uint32_t freeb = ((1u << NB) - 1u) & ~1u, pend = 0u;
   int flip_streak = 0;
   uint32_t nflip = 0, njump = 0, nempty = 0, npref = 0, ndirect = 0;
-  if (lane < 4) {
-    sPf[lane] = make_int4(-1, 0, 0, 0);
-    sWr[lane] = -1;
-  }
-  fill(1);
-  fill(33);
-  __syncwarp();
 
   for (uint32_t t = 1; t <= I_max; ++t) {
-    if ((t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
+    if (leader && (t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
     if (lane == 0) sWr[t & 3u] = -1;
     __syncwarp();
     const WRing e = ring[t % kWarpRing];
@@ -299,18 +367,17 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       int4 rec_pf = make_int4(-1, 0, 0, 0);
       if (acount > 0 && flip_streak < 3 && tt <= I_max) {
         const int sp = pick(ring[tt % kWarpRing].rst, acount);
-        if (sp < cslots) {
+        // a slot written in the previous iteration is left alone: warps
+        // still writing it are ordered before the copy only by the next
+        // barrier
+        if (sp < cslots && sWr[(t - 1u) & 3u] != sp) {
           const int b = __ffs(freeb) - 1;  // exists: LA + 1 buffers are held
           freeb &= ~(1u << b);
           if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
             wait_buf(b);
             pend &= ~(1u << b);
           }
-          if (lane == 0) {
-            fence_proxy_async_shared();
-            mbar_expect_tx(&sbar[b], rec.jr);
-            bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
-          }
+          copy_record(b, sp);
           pend |= 1u << b;
           rec_pf = make_int4(b, sp, (int)t, 0);
         }
@@ -322,30 +389,42 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
     const double delta = e.delta;
     const int64_t lo = e.lo, hi = e.hi;
     const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
+    const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
     const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(cur));
-    int total = 0, nl = 0;
+    int cnt_w = 0, nl = 0;
 #pragma unroll 4
-    for (int c = 0; c < NC; ++c) {
+    for (int c = c0; c < c1; ++c) {
       const uint4 a4 = a4p[c * 32 + lane];
       const uint32_t amin = min(min(a4.x, a4.y), min(a4.z, a4.w));
       if (__any_sync(kFull, amin <= hi32)) {
         // some bit of the chunk may be accepted: exact decisions
         const int p0 = c * 128 + lane * 4;
         const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
-        int64_t ax[4];
         bool acc[4], need[4];
+        double ad[4];
         bool anyneed = false;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           acc[j] = false;
           need[j] = false;
-          ax[j] = (int64_t)av[j];
+          ad[j] = 0.0;
           if (p0 + j < m && av[j] <= hi32) {
-            if (!NARROW && av[j] == 0xFFFFFFFFu) ax[j] = exact_penalty(cur, curL, p0 + j);
-            if (ax[j] <= lo)
-              acc[j] = true;
-            else if (ax[j] <= hi)
-              need[j] = true;
+            if (NARROW) {
+              // a < 2^32 - 1: the clamped thresholds decide exactly
+              if (av[j] <= lo32)
+                acc[j] = true;
+              else
+                need[j] = true;
+              ad[j] = (double)av[j];
+            } else {
+              const int64_t ax =
+                  av[j] == 0xFFFFFFFFu ? exact_penalty(cur, curL, p0 + j) : (int64_t)av[j];
+              if (ax <= lo)
+                acc[j] = true;
+              else if (ax <= hi)
+                need[j] = true;
+              ad[j] = (double)ax;
+            }
           }
           anyneed |= need[j];
         }
@@ -355,7 +434,7 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
           philox10(d, k0, k1);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (need[j]) acc[j] = (double)ax[j] <= __dmul_rn(delta, __ldg(&R.table[d[j] >> 16]));
+            if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
         }
         const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
                        b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
@@ -366,11 +445,19 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
             sAccC[nl] = c;
           }
           ++nl;
-          total += cnt;
+          cnt_w += cnt;
         }
       }
     }
-    __syncwarp();
+    int32_t *cntp = sCnt + 8 * (int)(t & 1u);
+    if (lane == 0) cntp[wt] = cnt_w;
+    // every warp's count, and whether any warp gave up a wait
+    if (sync_or(fail)) {
+      fail = true;
+      break;
+    }
+    int total = 0;
+    for (int w = 0; w < G; ++w) total += cntp[w];
 
     // the copy for this iteration: taken by a jump below, else given back
     const int4 pr = LA > 0 ? sPf[t & 3u] : make_int4(-1, 0, 0, 0);
@@ -380,16 +467,21 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       // ---- one accepted flip at random (R11): rank r in ascending bit order
       if (pr.x >= 0) freeb |= 1u << pr.x;
       kind = 1;
-      const int r = pick(e.sel, total);
+      int r = pick(e.sel, total);
+      int ow = 0;
+      while (r >= cntp[ow]) r -= cntp[ow++];  // the warp holding rank r
+      const unsigned char *ows = T.ws0 + (size_t)ow * SL.warp;
+      const uint4 *oAccW = reinterpret_cast<const uint4 *>(ows + SL.acc);
+      const int32_t *oAccC = reinterpret_cast<const int32_t *>(ows + SL.acc + 16 * (size_t)SL.nc_max);
       int q = 0, before = 0;
-      uint4 bw = sAccW[0];
+      uint4 bw = oAccW[0];
       for (;;) {
         const int k = __popc(bw.x) + __popc(bw.y) + __popc(bw.z) + __popc(bw.w);
         if (r < before + k) break;
         before += k;
-        bw = sAccW[++q];
+        bw = oAccW[++q];
       }
-      const int c = sAccC[q];
+      const int c = oAccC[q];
       // lane l's accepted bits (4l .. 4l + 3 of the chunk) as a nibble
       const uint32_t nib = ((bw.x >> lane) & 1u) | (((bw.y >> lane) & 1u) << 1) |
                            (((bw.z >> lane) & 1u) << 2) | (((bw.w >> lane) & 1u) << 3);
@@ -404,16 +496,16 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       ps = c * 128 + owner * 4 + jj;
 
       uint32_t *xw = bX(cur);
-      unsigned char *rc = bRC(cur);
       const int xps = (int)((xw[ps >> 5] >> (ps & 31)) & 1u);
       const int sgn = 1 - 2 * xps;  // +1: the bit turns on
       const int j = divn(ps), v = ps - j * n;
       const int2 Lp = curL[ps];
-      const int64_t hps = (int64_t)rc[j] + (int64_t)rc[n + v] - 1 - 2 * xps;
+      const int64_t hps = (int64_t)rcp[j] + (int64_t)rcp[n + v] - 1 - 2 * xps;
       const int64_t nE1 = E1 + (int64_t)sgn * ((int64_t)Lp.x + w1l * hps);
       const int64_t nE2 = E2 + (int64_t)sgn * ((int64_t)Lp.y + w2l * hps);
 
-      // ---- archive update: Alg. 4 (explore) or Alg. 5 (exploit)
+      // ---- archive update: Alg. 4 (explore) or Alg. 5 (exploit), decided
+      // the same way by every warp of the team
       int target = -1;
       if (!exploit) {
         // the first member x dominates is replaced; else x is appended
@@ -471,26 +563,46 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
         }
       }
 
-      // ---- apply the flip: outer product of flow row j and distance row v
+      // every warp has read the archive and the accepted lists: they may
+      // change now
+      sync();
+      if (lane == 0) sWr[t & 3u] = target;
+      if (target >= 0 && leader && lane == 0) {
+        gE[2 * target] = nE1;
+        gE[2 * target + 1] = nE2;
+        if (target < se) sAE[target] = make_longlong2(nE1, nE2);
+      }
+
+      // ---- apply the flip to this warp's chunks: outer product of flow
+      // row j and distance row v; the counts read are the old ones, so
+      // bits of row j or column v add the change
       for (int i = lane; i < n; i += 32) {
         sRow[i] = __ldg(&Fs1[j * n + i]);  // Fs symmetric: row j = column j
         sRow[kMaxN + i] = __ldg(&Fs2[j * n + i]);
         sRow[2 * kMaxN + i] = __ldg(&Dm[v * n + i]);
       }
       __syncwarp();
-      if (lane == 0) {
-        rc[j] = (unsigned char)((int)rc[j] + sgn);
-        rc[n + v] = (unsigned char)((int)rc[n + v] + sgn);
-      }
-      __syncwarp();
       const bool cached = target >= 0 && target < cslots;
       int2 *dstL = cached ? gLR + (size_t)target * rec.mp : gWork;
-      uint4 *dA = cached ? reinterpret_cast<uint4 *>(gJR + (size_t)target * rec.jr) : nullptr;
+      unsigned char *jrec = cached ? gJR + (size_t)target * rec.jr : nullptr;
+      uint4 *dA = reinterpret_cast<uint4 *>(jrec);
       uint4 *sa4 = reinterpret_cast<uint4 *>(bA(cur));
-      for (int cc = 0; cc < NC; ++cc) {
+      int c_next = c0;
+      int4 nx01 = make_int4(0, 0, 0, 0), nx23 = nx01;
+      if (c0 < c1) {
+        const int4 *src = reinterpret_cast<const int4 *>(curL + c0 * 128 + lane * 4);
+        nx01 = src[0];
+        nx23 = src[1];
+      }
+      for (int cc = c0; cc < c1; ++cc) {
         const int p0 = cc * 128 + lane * 4;
-        const int4 *src = reinterpret_cast<const int4 *>(curL + p0);
-        const int4 l01 = src[0], l23 = src[1];
+        const int4 l01 = nx01, l23 = nx23;
+        c_next = cc + 1;
+        if (c_next < c1) {  // the next chunk's fields, loaded while this one computes
+          const int4 *src = reinterpret_cast<const int4 *>(curL + c_next * 128 + lane * 4);
+          nx01 = src[0];
+          nx23 = src[1];
+        }
         const uint32_t nibx = (xw[p0 >> 5] >> (p0 & 31)) & 15u;
         int Lx[4] = {l01.x, l01.z, l23.x, l23.z};
         int Ly[4] = {l01.y, l01.w, l23.y, l23.w};
@@ -505,7 +617,8 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
             Ly[q2] += sgn * sRow[kMaxN + i] * dd;
             const int xq = (int)((nibx >> q2) & 1u) ^ (p == ps ? 1 : 0);
             const dE_t g = (dE_t)(1 - 2 * xq);
-            const dE_t h = (dE_t)rc[i] + (dE_t)rc[n + u] - 1 - 2 * xq;
+            const dE_t h = (dE_t)rcp[i] + (dE_t)rcp[n + u] +
+                           (dE_t)(sgn * ((i == j ? 1 : 0) + (u == v ? 1 : 0))) - 1 - 2 * xq;
             an[q2] = WA::penalty(g * ((dE_t)Lx[q2] + w1 * h), g * ((dE_t)Ly[q2] + w2 * h), lenient);
           } else {
             an[q2] = 0xFFFFFFFFu;
@@ -522,33 +635,38 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
         sa4[cc * 32 + lane] = a4n;
         if (cached) dA[cc * 32 + lane] = a4n;
       }
-      __syncwarp();
-      if (lane == 0) xw[ps >> 5] ^= 1u << (ps & 31);
-      __syncwarp();
+      // this warp's state words of x' (bit ps toggled) into the archive
+      const int qps = ps >> 5;
+      const uint32_t bps = 1u << (ps & 31);
       if (target >= 0) {
-        if (lane == 0) {
-          gE[2 * target] = nE1;
-          gE[2 * target + 1] = nE2;
-          if (target < se) sAE[target] = make_longlong2(nE1, nE2);
-          sWr[t & 3u] = target;
-        }
-        for (int q2 = lane; q2 < W; q2 += 32) gB[(size_t)target * W + q2] = xw[q2];
-        if (cached) {
-          unsigned char *jr = gJR + (size_t)target * rec.jr;
-          uint32_t *jx = reinterpret_cast<uint32_t *>(jr + rec.off_xw);
-          for (int q2 = lane; q2 < rec.mp / 32; q2 += 32) jx[q2] = xw[q2];
-          const uint32_t *rcw = reinterpret_cast<const uint32_t *>(rc);
-          uint32_t *jrc = reinterpret_cast<uint32_t *>(jr + rec.off_rc);
-          for (int q2 = lane; q2 < (int)(rec.off_E - rec.off_rc) / 4; q2 += 32) jrc[q2] = rcw[q2];
-          if (lane == 0) {
-            int64_t *je = reinterpret_cast<int64_t *>(jr + rec.off_E);
-            je[0] = nE1;
-            je[1] = nE2;
-          }
-          fence_proxy_async_global();  // later bulk copies read these records
+        for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32) {
+          const uint32_t wv = xw[q2] ^ (q2 == qps ? bps : 0u);
+          if (q2 < W) gB[(size_t)target * W + q2] = wv;
+          if (cached) reinterpret_cast<uint32_t *>(jrec + rec.off_xw)[q2] = wv;
         }
       }
       __syncwarp();
+      // the warp owning bit ps toggles it (no other warp reads that word
+      // before the next barrier); every warp updates its own counts
+      if (lane == 0) {
+        if (qps >= 4 * c0 && qps < 4 * c1) xw[qps] ^= bps;
+        rcp[j] = (unsigned char)((int)rcp[j] + sgn);
+        rcp[n + v] = (unsigned char)((int)rcp[n + v] + sgn);
+      }
+      __syncwarp();
+      if (target >= 0 && leader) {
+        if (cached) {
+          const uint32_t *rcw = reinterpret_cast<const uint32_t *>(rcp);
+          uint32_t *jrc = reinterpret_cast<uint32_t *>(jrec + rec.off_rc);
+          for (int q2 = lane; q2 < (int)(rec.off_E - rec.off_rc) / 4; q2 += 32) jrc[q2] = rcw[q2];
+          if (lane == 0) {
+            int64_t *je = reinterpret_cast<int64_t *>(jrec + rec.off_E);
+            je[0] = nE1;
+            je[1] = nE2;
+          }
+        }
+      }
+      if (cached) fence_proxy_async_global();  // later bulk copies read these records
       curL = dstL;
       E1 = nE1;
       E2 = nE2;
@@ -578,20 +696,15 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
           pend &= ~(1u << nbuf);
         }
         if (slot < cslots) {
-          if (lane == 0) {
-            fence_proxy_async_shared();
-            mbar_expect_tx(&sbar[nbuf], rec.jr);
-            bulk_g2s(sbuf + (size_t)nbuf * SL.jr, gJR + (size_t)slot * rec.jr, rec.jr,
-                     &sbar[nbuf]);
-          }
+          copy_record(nbuf, slot);
           wait_buf(nbuf);
         } else {
           // no records for this slot: rebuild from its state (the old
           // state's buffer is the scratch)
           uint32_t *xn = bX(nbuf);
-          for (int q2 = lane; q2 < rec.mp / 32; q2 += 32)
+          for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
             xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
-          __syncwarp();
+          sync();
           int64_t t1, t2, gp;
           rebuild(nbuf, cur, gWork, t1, t2, gp);
         }
@@ -604,6 +717,9 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
         const int64_t *be = bE(cur);
         E1 = be[0];
         E2 = be[1];
+        const unsigned char *rc = bRC(cur);
+        for (int q2 = lane; q2 < 2 * n; q2 += 32) rcp[q2] = rc[q2];
+        __syncwarp();
       } else {
         curL = gWork;
         E1 = gE[2 * slot];
@@ -615,25 +731,25 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
       ++nempty;  // empty archive: the state stays (R12)
     }
     flip_streak = kind == 1 ? flip_streak + 1 : 0;
-    if (R.trace != nullptr && lane == 0) {
-      int64_t *tr = R.trace + ((size_t)row * (size_t)I_max + (size_t)(t - 1)) * 3;
+    if (trace != nullptr && leader && lane == 0) {
+      int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(t - 1)) * 3;
       tr[0] = E1;
       tr[1] = E2;
       tr[2] = kind == 1 ? (int64_t)ps : kind == 2 ? -1 - (int64_t)event_slot : INT64_MIN;
     }
-    if (fail) break;
-    __syncwarp();
   }
   // no bulk copy may be in flight when the item ends
   for (int b = 0; b < NB; ++b)
     if ((pend >> b) & 1u) wait_buf(b);
+  fail = sync_or(fail);
   if (fail) {
-    if (lane == 0) atomicExch(R.error, kErrCopyTimeout);
+    if (leader && lane == 0) atomicExch(R.error, kErrCopyTimeout);
     return false;
   }
   const uint32_t *xw = bX(cur);
-  for (int q2 = lane; q2 < W; q2 += 32) R.x_final[(size_t)row * W + q2] = xw[q2];
-  if (lane == 0) {
+  for (int q2 = 4 * c0 + lane; q2 < 4 * c1 && q2 < W; q2 += 32)
+    R.x_final[(size_t)row * W + q2] = xw[q2];
+  if (leader && lane == 0) {
     R.E_final[2 * row] = E1;
     R.E_final[2 * row + 1] = E2;
     R.arch_count[row] = acount;
@@ -647,44 +763,60 @@ __device__ bool warp_run(const WarpRun &R, const int row, unsigned char *ws, con
     st[6] = 0;
     st[7] = 0;
   }
-  __syncwarp();
+  sync();  // the team's shared memory is reused by the next item
   return true;
 }
 
 template <bool NARROW>
 __global__ void __launch_bounds__(256) warp_anneal_kernel(const WarpLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
-  unsigned char *ws = smem + (size_t)wid * L.sm.total;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L.sm.mbar);
-  if (lane == 0) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = L.team, nteams = (blockDim.x >> 5) / G;
+  const int team = wid / G;
+  Team T;
+  T.G = G;
+  T.wt = wid - team * G;
+  T.lane = lane;
+  T.bar = 1 + team;
+  T.ts = smem + (size_t)team * L.sm.total;
+  T.ws0 = T.ts + L.sm.team;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(T.ts + L.sm.mbar);
+  int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 64);
+  const bool leader = T.wt == 0;
+  if (leader && lane == 0) {
     for (int b = 0; b < L.nbuf; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
-  __syncwarp();
-  unsigned char *cache = L.cache + (size_t)(blockIdx.x * NW + wid) * L.cache_stride;
+  if (G > 1) team_sync(T.bar, 32 * G);
+  else __syncwarp();
+  unsigned char *cache =
+      L.cache + (size_t)(blockIdx.x * nteams + team) * L.cache_stride;
   uint32_t par = 0;
   for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(L.counter, 1);
-    it = __shfl_sync(kFull, it, 0);
+    if (leader && lane == 0) *sItem = atomicAdd(L.counter, 1);
+    if (G > 1) team_sync(T.bar, 32 * G);
+    else __syncwarp();
+    const int it = *sItem;
+    if (G > 1) team_sync(T.bar, 32 * G);  // read before the next item is written
     if (it >= L.nitems) break;
     const int2 item = L.items[it];
     const WarpRun &R = L.runs[item.x];
     if ((R.narrow != 0) != NARROW) {  // the host launches matching variants only
-      if (lane == 0) atomicExch(R.error, kErrVariant);
+      if (leader && lane == 0) atomicExch(R.error, kErrVariant);
       continue;
     }
-    if (!warp_run<NARROW>(R, item.y, ws, L, cache, lane, par)) break;
+    if (!team_run<NARROW>(R, item.y, T, L, cache, par)) break;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int warps,
+cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
                         cudaStream_t stream) {
-  if (warps < 1 || warps > 8 || grid < 1) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)warps * L.sm.total;
+  const int warps = teams * L.team;
+  if (L.team < 1 || L.team > 8 || teams < 1 || warps > 8 || teams > 15 || grid < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)teams * L.sm.total;
   const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
                          : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -704,12 +836,12 @@ cudaError_t warp_function(bool narrow, size_t smem, const void **func) {
   return e;
 }
 
-cudaError_t warp_occupancy(bool narrow, int warps, size_t smem, int *blocks) {
+cudaError_t warp_occupancy(bool narrow, int threads, size_t smem, int *blocks) {
   const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
                          : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, 32 * warps, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
 }
 
 }  // namespace moda

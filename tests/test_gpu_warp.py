@@ -16,26 +16,32 @@ FAST = dict(delta0=2e6, deltaf=3e3, xi=0.02)
 MODES = [(acc, arc) for acc in ("strict", "lenient") for arc in ("explore", "exploit")]
 
 
+@pytest.mark.parametrize("team", [0, 1, 3, 8])
 @pytest.mark.parametrize("cache", ["auto", "off"])
 @pytest.mark.parametrize("acc,arc", MODES)
-def test_warp_traced_small(acc, arc, cache):
+def test_warp_traced_small(acc, arc, cache, team):
     """Per-iteration traces equal the oracle's on ragged sizes: one chunk of
     128 bits and a ragged last chunk, several chunks, hot, cooling and
-    frozen phases, restarts and undecided acceptance tests."""
+    frozen phases, restarts and undecided acceptance tests; teams of 1, 3
+    and 8 warps per replica (more warps than chunks included) and the
+    automatic team size."""
     for n in (5, 7, 12, 17, 25):
         inst = inputs.uniform_instance(n, index=300 + n, workload="P8")
         kw = dict(replicas=3, I_max=1500, seed=40 + n, accept=acc, archive=arc, **FAST)
-        _, _, res, tr = gpu_run(inst, trace=True, field_cache=cache, engine="warp", **kw)
+        _, _, res, tr = gpu_run(inst, trace=True, field_cache=cache, engine="warp",
+                                block_threads=32 * team, **kw)
         _, orc = oracle_run(inst, trace=True, **kw)
         compare(res, range(3), orc, n * n, gpu_trace=tr)
 
 
+@pytest.mark.parametrize("team", [1, 4])
 @pytest.mark.parametrize("prefetch", [1, 2, 3])
-def test_warp_prefetch_distances(prefetch):
+def test_warp_prefetch_distances(prefetch, team):
     """Jump records copied 0, 1 or 2 iterations ahead give the oracle's run."""
     inst = inputs.euclid_instance(23, 0.5, False, index=3, workload="P25")
     kw = dict(replicas=5, I_max=4000, seed=8, **FAST)
-    _, _, res, tr = gpu_run(inst, trace=True, prefetch=prefetch, engine="warp", **kw)
+    _, _, res, tr = gpu_run(inst, trace=True, prefetch=prefetch, engine="warp",
+                            block_threads=32 * team, **kw)
     _, orc = oracle_run(inst, trace=True, **kw)
     compare(res, range(5), orc, 23 * 23, gpu_trace=tr)
     if prefetch > 1:  # copies started ahead: some jumps took a prefetched record
@@ -78,9 +84,10 @@ def test_warp_wide_variant(n):
     bound = [int((F + F.T).sum(1).max()) * int(D.sum(1).max()) for F in (F1, F2)]
     assert max(b + w * (2 * n + 1) for b, w in zip(bound, g.w)) >= 2 ** 31
     kw = dict(replicas=4, I_max=2500, seed=17)
-    _, _, res, tr = gpu_run(inst, trace=True, engine="warp", **kw)
     _, orc = oracle_run(inst, trace=True, **kw)
-    compare(res, range(4), orc, n * n, gpu_trace=tr)
+    for team in (1, 5):
+        _, _, res, tr = gpu_run(inst, trace=True, engine="warp", block_threads=32 * team, **kw)
+        compare(res, range(4), orc, n * n, gpu_trace=tr)
 
 
 @pytest.mark.parametrize("acc", ["strict", "lenient"])
@@ -143,6 +150,10 @@ def test_warp_large_configs_prefix(name):
     I_max = 12000
     _, _, res, _ = gpu_run(inst, replicas=run["replicas"], I_max=I_max, seed=run["seed"],
                            engine="warp")
+    _, _, one, _ = gpu_run(inst, replicas=run["replicas"], I_max=I_max, seed=run["seed"],
+                           engine="warp", block_threads=32)
+    assert np.array_equal(res.x, one.x) and np.array_equal(res.E_final, one.E_final)
+    assert np.array_equal(res.stats[:, :4], one.stats[:, :4])
     rows = [2, run["replicas"] - 3]
     _, orc = oracle_run(inst, replicas=rows, I_max=I_max, seed=run["seed"])
     compare(res, rows, orc, inst.n * inst.n)

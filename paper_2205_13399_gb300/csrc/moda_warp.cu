@@ -297,9 +297,22 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   };
 
   bool fail = false;
-  auto wait_buf = [&](int b) {
+  // Copies into buffer b complete phases of mbarrier b in turn; every warp
+  // tracks the parity of the next phase.  A copy whose data the team uses
+  // is waited for by every warp (take_buf); one that is given up only by
+  // the leader, before that buffer is filled again (retire_buf).  A warp
+  // therefore never polls a phase that the barrier may already have left
+  // twice: after a take the buffer is refilled only one barrier later.
+  auto take_buf = [&](int b) {
     const bool ok = mbar_wait(&sbar[b], (par >> b) & 1u);
     if (!__all_sync(kFull, ok)) fail = true;
+    par ^= 1u << b;
+  };
+  auto retire_buf = [&](int b) {
+    if (leader) {
+      const bool ok = mbar_wait(&sbar[b], (par >> b) & 1u);
+      if (!__all_sync(kFull, ok)) fail = true;
+    }
     par ^= 1u << b;
   };
   // the leader's lane 0 starts the copy of slot y's jump record into b
@@ -374,7 +387,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           const int b = __ffs(freeb) - 1;  // exists: LA + 1 buffers are held
           freeb &= ~(1u << b);
           if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
-            wait_buf(b);
+            retire_buf(b);
             pend &= ~(1u << b);
           }
           copy_record(b, sp);
@@ -684,7 +697,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       int nbuf;
       if (ok) {
         nbuf = pr.x;
-        wait_buf(nbuf);
+        take_buf(nbuf);
         pend &= ~(1u << nbuf);
         ++npref;
       } else {
@@ -692,12 +705,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         nbuf = __ffs(freeb) - 1;
         freeb &= ~(1u << nbuf);
         if ((pend >> nbuf) & 1u) {
-          wait_buf(nbuf);
+          retire_buf(nbuf);
           pend &= ~(1u << nbuf);
         }
         if (slot < cslots) {
           copy_record(nbuf, slot);
-          wait_buf(nbuf);
+          take_buf(nbuf);
         } else {
           // no records for this slot: rebuild from its state (the old
           // state's buffer is the scratch)
@@ -740,7 +753,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   }
   // no bulk copy may be in flight when the item ends
   for (int b = 0; b < NB; ++b)
-    if ((pend >> b) & 1u) wait_buf(b);
+    if ((pend >> b) & 1u) retire_buf(b);
   fail = sync_or(fail);
   if (fail) {
     if (leader && lane == 0) atomicExch(R.error, kErrCopyTimeout);

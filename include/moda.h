@@ -150,9 +150,10 @@ typedef struct {
                               holds min(s, 1024) slots per resident warp by
                               default (field_cache = 1: all s slots; 2:
                               none); a jump to a slot without records
-                              rebuilds its fields.  prefetch k in 1..3 copies
+                              rebuilds its fields.  prefetch k in 1..7 copies
                               a jump's target k - 1 iterations ahead (0:
-                              auto, 2 iterations).  A team of G warps (1 to
+                              auto: up to 6 iterations, as shared memory
+                              allows).  A team of G warps (1 to
                               8) runs each replica: automatically the
                               largest G that keeps every replica resident
                               at once, else 1; block_threads = 32 G
@@ -316,13 +317,14 @@ moda_status moda_qrun_read(moda_qrun run, int32_t *count, int64_t *E, uint32_t *
 moda_status moda_qrun_elapsed_ms(moda_qrun run, float *ms);
 void moda_qrun_destroy(moda_qrun run);
 
-/* Autotuner of the launch layout: times short trials of every block shape
- * the kernel has (bits per thread and threads per block) and, when the
- * escape jumps to the archive, of field-cache prefetch distances 1 and 2
- * besides the automatic choice, on `inst` with `params` (trial_iters
- * iterations at the cold end of the schedule, delta = deltaf, on at most
- * one replica per SM), and writes into *best a copy of *params with the
- * fastest block_threads and prefetch; *best_ms (if not NULL) receives the
+/* Autotuner of the launch layout: for the block engine, times short trials
+ * of every block shape the kernel has (bits per thread and threads per
+ * block) and, when the escape jumps to the archive, of field-cache
+ * prefetch distances 1 and 2 besides the automatic choice, on `inst` with
+ * `params` (trial_iters iterations at the cold end of the schedule, delta =
+ * deltaf, on at most one replica per SM); for the warp engine, prefetch
+ * distances 0, 2, 4 and 6 on the request's own replicas.  Writes into
+ * *best a copy of *params with the fastest block_threads and prefetch; *best_ms (if not NULL) receives the
  * winning trial's time.  Results of a run do not depend on these two
  * fields, so tuning never changes what an anneal computes.  Blocks the
  * calling thread while the trials run on cuda_stream. */

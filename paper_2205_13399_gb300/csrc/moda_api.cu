@@ -480,7 +480,7 @@ moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStrea
   if (p->field_cache < 0 || p->field_cache > 2)
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kWarpMaxLA + 1)
-    return fail(MODA_EINVAL, "prefetch must be in [0, 3] for the warp engine");
+    return fail(MODA_EINVAL, "prefetch must be in [0, 7] for the warp engine");
   if (p->block_threads < 0 || p->block_threads % 32 || p->block_threads > 256)
     return fail(MODA_EINVAL, "warp engine: block_threads must be 32 G, G in 1..8 (0: auto)");
   cudaSetDevice(inst->device);
@@ -1798,7 +1798,7 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
   const int m = inst->m;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   if (uses_warp(params)) {
-    // Warp engine: the prefetch distances 0, 1 and 2, each timed on the
+    // Warp engine: prefetch distances 0, 2, 4 and 6, each timed on the
     // request's own replicas at the cold end of the schedule.
     moda_params trial = *params;
     trial.I_max = trial_iters;
@@ -1807,7 +1807,7 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
     bool found = false;
     float fastest = 0.f;
     moda_params winner = *params;
-    for (int32_t pf : {1, 2, 3}) {
+    for (int32_t pf : {1, 3, 5, 7}) {
       trial.prefetch = pf;
       moda_run r = nullptr;
       if (moda_anneal(inst, &trial, stream, &r) != MODA_OK) continue;

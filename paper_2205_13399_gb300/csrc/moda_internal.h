@@ -236,7 +236,7 @@ cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t sm
 // L_k (int32 pairs) live in global memory and are read only by flips.
 
 constexpr int kWarpRing = 64;   // draw / schedule ring entries (iterations)
-constexpr int kWarpMaxLA = 2;   // prefetch distance (iterations ahead)
+constexpr int kWarpMaxLA = 6;   // prefetch distance (iterations ahead)
 
 // Records of one archive slot for a run of n, m (the field cache of the
 // warp annealer):
@@ -294,7 +294,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
   L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
-  L.pf = (uint32_t)o;        o = align_up(o + 16 * 4 + 4 * 4, 16);
+  L.pf = (uint32_t)o;        o = align_up(o + 16 * 8 + 4 * 8, 16);
   L.warp = (uint32_t)o;
   L.total = L.team + (uint32_t)G * L.warp;
   return L;

@@ -145,11 +145,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   int32_t *sCnt = reinterpret_cast<int32_t *>(ts + SL.cnt);
   int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 80);  // [G][2] rebuild sums
   unsigned char *ws = T.ws0 + (size_t)wt * SL.warp;
-  // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 3]
+  // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 7]
   // = {buffer or -1, slot, issuing iteration} of the copy for target
-  // iteration tt; sWr[x & 3] = the slot iteration x wrote (-1: none)
+  // iteration tt; sWr[x & 7] = the slot iteration x wrote (-1: none)
   int4 *sPf = reinterpret_cast<int4 *>(ws + SL.pf);
-  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 64);
+  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 128);
   uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
   int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
   int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
@@ -342,7 +342,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         x0[4 * c + w] = v;
       }
     }
-    if (lane < 4) {
+    if (lane < 8) {
       sPf[lane] = make_int4(-1, 0, 0, 0);
       sWr[lane] = -1;
     }
@@ -368,7 +368,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
 
   for (uint32_t t = 1; t <= I_max; ++t) {
     if (leader && (t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
-    if (lane == 0) sWr[t & 3u] = -1;
+    if (lane == 0) sWr[t & 7u] = -1;
     __syncwarp();
     const WRing e = ring[t % kWarpRing];
 
@@ -383,7 +383,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         // a slot written in the previous iteration is left alone: warps
         // still writing it are ordered before the copy only by the next
         // barrier
-        if (sp < cslots && sWr[(t - 1u) & 3u] != sp) {
+        if (sp < cslots && sWr[(t - 1u) & 7u] != sp) {
           const int b = __ffs(freeb) - 1;  // exists: LA + 1 buffers are held
           freeb &= ~(1u << b);
           if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
@@ -395,7 +395,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           rec_pf = make_int4(b, sp, (int)t, 0);
         }
       }
-      if (lane == 0) sPf[tt & 3u] = rec_pf;
+      if (lane == 0) sPf[tt & 7u] = rec_pf;
     }
 
     // ---- the parallel trial of every bit (Eq. pacceptms / pacceptml) -----
@@ -473,7 +473,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     for (int w = 0; w < G; ++w) total += cntp[w];
 
     // the copy for this iteration: taken by a jump below, else given back
-    const int4 pr = LA > 0 ? sPf[t & 3u] : make_int4(-1, 0, 0, 0);
+    const int4 pr = LA > 0 ? sPf[t & 7u] : make_int4(-1, 0, 0, 0);
     int kind = 0;  // 1 flip, 2 jump, 0 neither
     int event_slot = 0, ps = 0;
     if (total > 0) {
@@ -508,11 +508,30 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       jj = __shfl_sync(kFull, jj, owner);
       ps = c * 128 + owner * 4 + jj;
 
+      const int j = divn(ps), v = ps - j * n;
+      // the flip's global reads, issued together: L(ps), flow row j,
+      // distance row v and this warp's first chunk of fields
+      const int2 Lp = curL[ps];
+      int32_t rf1[4], rf2[4], rdd[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = lane + 32 * k;
+        rf1[k] = rf2[k] = rdd[k] = 0;
+        if (i < n) {
+          rf1[k] = __ldg(&Fs1[j * n + i]);  // Fs symmetric: row j = column j
+          rf2[k] = __ldg(&Fs2[j * n + i]);
+          rdd[k] = __ldg(&Dm[v * n + i]);
+        }
+      }
+      int4 nx01 = make_int4(0, 0, 0, 0), nx23 = nx01;
+      if (c0 < c1) {
+        const int4 *src = reinterpret_cast<const int4 *>(curL + c0 * 128 + lane * 4);
+        nx01 = src[0];
+        nx23 = src[1];
+      }
       uint32_t *xw = bX(cur);
       const int xps = (int)((xw[ps >> 5] >> (ps & 31)) & 1u);
       const int sgn = 1 - 2 * xps;  // +1: the bit turns on
-      const int j = divn(ps), v = ps - j * n;
-      const int2 Lp = curL[ps];
       const int64_t hps = (int64_t)rcp[j] + (int64_t)rcp[n + v] - 1 - 2 * xps;
       const int64_t nE1 = E1 + (int64_t)sgn * ((int64_t)Lp.x + w1l * hps);
       const int64_t nE2 = E2 + (int64_t)sgn * ((int64_t)Lp.y + w2l * hps);
@@ -579,7 +598,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // every warp has read the archive and the accepted lists: they may
       // change now
       sync();
-      if (lane == 0) sWr[t & 3u] = target;
+      if (lane == 0) sWr[t & 7u] = target;
       if (target >= 0 && leader && lane == 0) {
         gE[2 * target] = nE1;
         gE[2 * target + 1] = nE2;
@@ -589,10 +608,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // ---- apply the flip to this warp's chunks: outer product of flow
       // row j and distance row v; the counts read are the old ones, so
       // bits of row j or column v add the change
-      for (int i = lane; i < n; i += 32) {
-        sRow[i] = __ldg(&Fs1[j * n + i]);  // Fs symmetric: row j = column j
-        sRow[kMaxN + i] = __ldg(&Fs2[j * n + i]);
-        sRow[2 * kMaxN + i] = __ldg(&Dm[v * n + i]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = lane + 32 * k;
+        if (i < n) {
+          sRow[i] = rf1[k];
+          sRow[kMaxN + i] = rf2[k];
+          sRow[2 * kMaxN + i] = rdd[k];
+        }
       }
       __syncwarp();
       const bool cached = target >= 0 && target < cslots;
@@ -601,12 +624,6 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       uint4 *dA = reinterpret_cast<uint4 *>(jrec);
       uint4 *sa4 = reinterpret_cast<uint4 *>(bA(cur));
       int c_next = c0;
-      int4 nx01 = make_int4(0, 0, 0, 0), nx23 = nx01;
-      if (c0 < c1) {
-        const int4 *src = reinterpret_cast<const int4 *>(curL + c0 * 128 + lane * 4);
-        nx01 = src[0];
-        nx23 = src[1];
-      }
       for (int cc = c0; cc < c1; ++cc) {
         const int p0 = cc * 128 + lane * 4;
         const int4 l01 = nx01, l23 = nx23;
@@ -693,7 +710,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       bool ok = pr.x >= 0 && pr.y == slot;
       if (ok)
         for (uint32_t xi = (uint32_t)pr.z; xi < t; ++xi)
-          if (sWr[xi & 3u] == slot) ok = false;  // rewritten after the copy began
+          if (sWr[xi & 7u] == slot) ok = false;  // rewritten after the copy began
       int nbuf;
       if (ok) {
         nbuf = pr.x;

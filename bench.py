@@ -344,7 +344,7 @@ def batch_measure(args, steps: int, warmup: int, seq_instances: int):
         r = moda.anneal(insts[i], params[i], stream=stream).wait()
         seq_ms += r.elapsed_ms()
         r.close()
-    sub_ms = statistics.mean(ms) if k == len(insts) else batch(params, subset=k)
+    sub_ms = statistics.mean(ms) if k in (0, len(insts)) else batch(params, subset=k)
     # end to end: instance upload, the batch, merged fronts read back
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -379,10 +379,11 @@ def batch_measure(args, steps: int, warmup: int, seq_instances: int):
                    "l2": "flushed between timed steps (512 MiB write)",
                    **({"autotuned": tuned} if tuned else {})},
         "bit_trials_per_s": value * statistics.mean(n * n for n in ns),
-        "vs_sequential": {"instances": k, "batched_ms": sub_ms, "sequential_ms": seq_ms,
-                          "speedup": seq_ms / sub_ms,
-                          "what": "the same instances as plain moda_anneal launches one after "
-                                  "another (sum of their kernel times) against the batch"},
+        "vs_sequential": None if k == 0 else {
+            "instances": k, "batched_ms": sub_ms, "sequential_ms": seq_ms,
+            "speedup": seq_ms / sub_ms,
+            "what": "the same instances as plain moda_anneal launches one after another "
+                    "(sum of their kernel times) against the batch"},
         "e2e": {"value": rep_steps / e2e_s, "unit": "replica-steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": 1},
         "gpu_launches": None, "roofline": roofline, "clocks": clk,

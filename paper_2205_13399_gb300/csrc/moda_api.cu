@@ -889,7 +889,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
     const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, la_try + 2, G);
     *blocks = 0;
     if ((int64_t)L.total > optin) return false;
-    if (moda::warp_occupancy(narrow, 32 * G, L.total, blocks) != cudaSuccess || *blocks < 1)
+    if (moda::warp_occupancy(narrow, G, L.total, blocks) != cudaSuccess || *blocks < 1)
       return false;
     *out = L;
     return true;
@@ -1411,7 +1411,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     }
     const void *func = nullptr;
     const size_t smem = (size_t)G.warps * G.L.sm.total;
-    if (e == cudaSuccess) e = moda::warp_function(G.narrow, smem, &func);
+    if (e == cudaSuccess) e = moda::warp_function(G.narrow, G.L.team, smem, &func);
     cudaGraphNode_t kn;
     if (e == cudaSuccess) {
       void *kargs[1] = {const_cast<moda::WarpLaunch *>(&G.L)};

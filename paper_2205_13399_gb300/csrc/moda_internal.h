@@ -352,11 +352,12 @@ inline size_t warp_cache_bytes(int n, int m, int cslots) {
 // Launches the warp annealer: `grid` blocks of `teams` teams of L.team warps.
 cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
                         cudaStream_t stream);
-// The warp annealer's kernel (one WarpLaunch argument) for a CUDA graph
-// node, with `smem` bytes of dynamic shared memory allowed.
-cudaError_t warp_function(bool narrow, size_t smem, const void **func);
-// Resident blocks per SM of the warp annealer for blocks of `threads`.
-cudaError_t warp_occupancy(bool narrow, int threads, size_t smem, int *blocks);
+// The warp annealer's kernel (one WarpLaunch argument) for teams of `team`
+// warps, for a CUDA graph node, with `smem` bytes of dynamic shared memory
+// allowed.
+cudaError_t warp_function(bool narrow, int team, size_t smem, const void **func);
+// Resident blocks (one team of `team` warps each) per SM.
+cudaError_t warp_occupancy(bool narrow, int team, size_t smem, int *blocks);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);

@@ -797,8 +797,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   return true;
 }
 
-template <bool NARROW>
-__global__ void __launch_bounds__(256) warp_anneal_kernel(const WarpLaunch L) {
+// MINB: blocks per SM the register allocation is sized for -- 1 for teams
+// of several warps (no register spills; one replica's iteration is a
+// latency chain), 2 for single-warp teams (twice the resident warps).
+template <bool NARROW, int MINB>
+__global__ void __launch_bounds__(256, MINB) warp_anneal_kernel(const WarpLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = L.team, nteams = (blockDim.x >> 5) / G;
@@ -841,37 +844,45 @@ __global__ void __launch_bounds__(256) warp_anneal_kernel(const WarpLaunch L) {
 
 }  // namespace
 
+namespace {
+// The kernel variant of a launch: narrow or not, and the register budget
+// (teams of several warps take the unspilled one).
+const void *warp_kernel(bool narrow, int team) {
+  if (team > 1)
+    return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, 1>)
+                  : reinterpret_cast<const void *>(warp_anneal_kernel<false, 1>);
+  return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, 2>)
+                : reinterpret_cast<const void *>(warp_anneal_kernel<false, 2>);
+}
+}  // namespace
+
 cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
                         cudaStream_t stream) {
   const int warps = teams * L.team;
   if (L.team < 1 || L.team > 8 || teams < 1 || warps > 8 || teams > 15 || grid < 1)
     return cudaErrorInvalidValue;
   const size_t smem = (size_t)teams * L.sm.total;
-  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
-                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+  const void *f = warp_kernel(narrow, L.team);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (narrow)
-    warp_anneal_kernel<true><<<grid, 32 * warps, smem, stream>>>(L);
-  else
-    warp_anneal_kernel<false><<<grid, 32 * warps, smem, stream>>>(L);
+  void *args[1] = {const_cast<WarpLaunch *>(&L)};
+  e = cudaLaunchKernel(f, dim3((unsigned)grid), dim3((unsigned)(32 * warps)), args, smem, stream);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-cudaError_t warp_function(bool narrow, size_t smem, const void **func) {
-  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
-                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+cudaError_t warp_function(bool narrow, int team, size_t smem, const void **func) {
+  const void *f = warp_kernel(narrow, team);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) *func = f;
   return e;
 }
 
-cudaError_t warp_occupancy(bool narrow, int threads, size_t smem, int *blocks) {
-  const void *f = narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
-                         : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+cudaError_t warp_occupancy(bool narrow, int team, size_t smem, int *blocks) {
+  const void *f = warp_kernel(narrow, team);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, 32 * team, smem);
 }
 
 }  // namespace moda

@@ -285,12 +285,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
 
   // Exact penalty of bit p of the state in buffer b with fields gL (only
   // for a saturated a(p) in the int64 variant).
-  auto exact_penalty = [&](int b, const int2 *gL, int p) -> int64_t {
+  auto exact_penalty = [&](int b, const int2 *gL, const unsigned char *rcq, int p) -> int64_t {
     const int2 L = gL[p];
     const int i = divn(p), u = p - i * n;
     const uint32_t *xw = bX(b);
     const int xv = (int)((xw[p >> 5] >> (p & 31)) & 1u);
-    const int64_t g = 1 - 2 * xv, h = (int64_t)rcp[i] + rcp[n + u] - 1 - 2 * xv;
+    const int64_t g = 1 - 2 * xv, h = (int64_t)rcq[i] + rcq[n + u] - 1 - 2 * xv;
     const int64_t e1 = g * ((int64_t)L.x + w1l * h), e2 = g * ((int64_t)L.y + w2l * h);
     const int64_t u1 = e1 > 0 ? e1 : 0, u2 = e2 > 0 ? e2 : 0;
     return lenient ? (u1 < u2 ? u1 : u2) : u1 + u2;
@@ -347,6 +347,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       sWr[lane] = -1;
     }
     if (leader) {
+      if (lane < 16) sCnt[lane] = 0;  // counts of warps beyond G stay 0
       fill(1);
       fill(33);
     }
@@ -365,6 +366,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   uint32_t freeb = ((1u << NB) - 1u) & ~1u, pend = 0u;
   int flip_streak = 0;
   uint32_t nflip = 0, njump = 0, nempty = 0, npref = 0, ndirect = 0;
+  // the last iteration that wrote an archive slot; after a jump to a
+  // cached slot this warp's counts are refreshed from the buffer only when
+  // needed (rc_stale)
+  uint32_t last_wr_t = 0;
+  bool rc_stale = false;
 
   for (uint32_t t = 1; t <= I_max; ++t) {
     if (leader && (t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
@@ -430,8 +436,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
                 need[j] = true;
               ad[j] = (double)av[j];
             } else {
-              const int64_t ax =
-                  av[j] == 0xFFFFFFFFu ? exact_penalty(cur, curL, p0 + j) : (int64_t)av[j];
+              const int64_t ax = av[j] == 0xFFFFFFFFu
+                                     ? exact_penalty(cur, curL, rc_stale ? bRC(cur) : rcp, p0 + j)
+                                     : (int64_t)av[j];
               if (ax <= lo)
                 acc[j] = true;
               else if (ax <= hi)
@@ -469,8 +476,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       fail = true;
       break;
     }
-    int total = 0;
-    for (int w = 0; w < G; ++w) total += cntp[w];
+    const int4 ca = reinterpret_cast<const int4 *>(cntp)[0],
+               cb = reinterpret_cast<const int4 *>(cntp)[1];
+    const int total = ca.x + ca.y + ca.z + ca.w + cb.x + cb.y + cb.z + cb.w;
 
     // the copy for this iteration: taken by a jump below, else given back
     const int4 pr = LA > 0 ? sPf[t & 7u] : make_int4(-1, 0, 0, 0);
@@ -508,6 +516,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       jj = __shfl_sync(kFull, jj, owner);
       ps = c * 128 + owner * 4 + jj;
 
+      if (rc_stale) {  // this warp's counts of the state the jump reached
+        const unsigned char *rc = bRC(cur);
+        for (int q2 = lane; q2 < 2 * n; q2 += 32) rcp[q2] = rc[q2];
+        __syncwarp();
+        rc_stale = false;
+      }
       const int j = divn(ps), v = ps - j * n;
       // the flip's global reads, issued together: L(ps), flow row j,
       // distance row v and this warp's first chunk of fields
@@ -599,6 +613,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // change now
       sync();
       if (lane == 0) sWr[t & 7u] = target;
+      if (target >= 0) last_wr_t = t;
       if (target >= 0 && leader && lane == 0) {
         gE[2 * target] = nE1;
         gE[2 * target + 1] = nE2;
@@ -708,7 +723,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const int slot = pick(e.rst, acount);
       event_slot = slot;
       bool ok = pr.x >= 0 && pr.y == slot;
-      if (ok)
+      if (ok && last_wr_t >= (uint32_t)pr.z)  // some slot was written after the copy began
         for (uint32_t xi = (uint32_t)pr.z; xi < t; ++xi)
           if (sWr[xi & 7u] == slot) ok = false;  // rewritten after the copy began
       int nbuf;
@@ -736,7 +751,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
           sync();
           int64_t t1, t2, gp;
-          rebuild(nbuf, cur, gWork, t1, t2, gp);
+          rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
         }
         ++ndirect;
       }
@@ -747,13 +762,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const int64_t *be = bE(cur);
         E1 = be[0];
         E2 = be[1];
-        const unsigned char *rc = bRC(cur);
-        for (int q2 = lane; q2 < 2 * n; q2 += 32) rcp[q2] = rc[q2];
-        __syncwarp();
+        rc_stale = true;
       } else {
         curL = gWork;
         E1 = gE[2 * slot];
         E2 = gE[2 * slot + 1];
+        rc_stale = false;
       }
       ++njump;
     } else {

@@ -543,6 +543,17 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         nx01 = src[0];
         nx23 = src[1];
       }
+      // the rows into this warp's shared memory now: no registers held
+      // across the archive scan
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = lane + 32 * k;
+        if (i < n) {
+          sRow[i] = rf1[k];
+          sRow[kMaxN + i] = rf2[k];
+          sRow[2 * kMaxN + i] = rdd[k];
+        }
+      }
       uint32_t *xw = bX(cur);
       const int xps = (int)((xw[ps >> 5] >> (ps & 31)) & 1u);
       const int sgn = 1 - 2 * xps;  // +1: the bit turns on
@@ -623,15 +634,6 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // ---- apply the flip to this warp's chunks: outer product of flow
       // row j and distance row v; the counts read are the old ones, so
       // bits of row j or column v add the change
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int i = lane + 32 * k;
-        if (i < n) {
-          sRow[i] = rf1[k];
-          sRow[kMaxN + i] = rf2[k];
-          sRow[2 * kMaxN + i] = rdd[k];
-        }
-      }
       __syncwarp();
       const bool cached = target >= 0 && target < cslots;
       int2 *dstL = cached ? gLR + (size_t)target * rec.mp : gWork;

@@ -813,11 +813,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   return true;
 }
 
-// MINB: blocks per SM the register allocation is sized for -- 1 for teams
-// of several warps (no register spills; one replica's iteration is a
-// latency chain), 2 for single-warp teams (twice the resident warps).
-template <bool NARROW, int MINB>
-__global__ void __launch_bounds__(256, MINB) warp_anneal_kernel(const WarpLaunch L) {
+// The register allocation is sized for one block per SM: no register
+// spills (their local-memory reads missed L1 and sat on every iteration's
+// chain), at the cost of resident warps.
+template <bool NARROW>
+__global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = L.team, nteams = (blockDim.x >> 5) / G;
@@ -861,14 +861,10 @@ __global__ void __launch_bounds__(256, MINB) warp_anneal_kernel(const WarpLaunch
 }  // namespace
 
 namespace {
-// The kernel variant of a launch: narrow or not, and the register budget
-// (teams of several warps take the unspilled one).
-const void *warp_kernel(bool narrow, int team) {
-  if (team > 1)
-    return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, 1>)
-                  : reinterpret_cast<const void *>(warp_anneal_kernel<false, 1>);
-  return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, 2>)
-                : reinterpret_cast<const void *>(warp_anneal_kernel<false, 2>);
+// The kernel variant of a launch: narrow or not.
+const void *warp_kernel(bool narrow, int) {
+  return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
+                : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
 }
 }  // namespace
 

@@ -159,7 +159,9 @@ typedef struct {
                               at once, else 1; block_threads = 32 G
                               prescribes it.
                             0 auto: warp when the options allow it and
-                              block_threads is 0, else block. */
+                              block_threads is 0, else block; a plain
+                              moda_anneal whose replicas fit one per SM
+                              takes block. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */

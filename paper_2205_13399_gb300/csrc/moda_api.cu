@@ -297,6 +297,21 @@ bool uses_warp(const moda_params *p) {
   return p->engine == 2 || (p->engine == 0 && warp_options(p) && p->block_threads == 0);
 }
 
+// A plain anneal with the automatic engine: whose replicas fit one per SM
+// runs on the block engine (a whole block per replica: the shortest
+// iteration), more replicas on the warp engine.  Batches and the server
+// keep the warp engine, whose work list packs many runs.
+moda_params resolve_plain(moda_instance inst, const moda_params *p) {
+  moda_params q = *p;
+  if (q.engine == 0 && q.block_threads == 0 && warp_options(p)) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inst->device) == cudaSuccess &&
+        q.replicas <= sms)
+      q.engine = 1;
+  }
+  return q;
+}
+
 // Archive slots with field-cache records per resident warp by default.
 constexpr int kWarpCacheSlots = 1024;
 // Archive energies kept in shared memory per warp, at most.
@@ -1052,7 +1067,9 @@ moda_status moda_anneal(moda_instance inst, const moda_params *p,
   *out = nullptr;
   Prepared pl{};
   moda_run r = nullptr;
-  moda_status st = prepare_run(inst, p, static_cast<cudaStream_t>(cuda_stream), &r, &pl);
+  if (!inst || !p) return fail(MODA_EINVAL, "NULL instance or params");
+  const moda_params q = resolve_plain(inst, p);
+  moda_status st = prepare_run(inst, &q, static_cast<cudaStream_t>(cuda_stream), &r, &pl);
   if (st != MODA_OK) return st;
   if (r->warp) {
     size_t free_b = 0;
@@ -1797,6 +1814,8 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
   if (trial_iters < 1) return fail(MODA_EINVAL, "trial_iters must be >= 1");
   const int m = inst->m;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const moda_params resolved = resolve_plain(inst, params);
+  params = &resolved;
   if (uses_warp(params)) {
     // Warp engine: prefetch distances 0, 2, 4 and 6, each timed on the
     // request's own replicas at the cold end of the schedule.

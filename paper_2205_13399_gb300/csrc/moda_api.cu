@@ -901,7 +901,8 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   const int la_max = la;
   moda::WarpSmem sm{};
   auto resident = [&](int G, int la_try, int se_try, int *blocks, moda::WarpSmem *out) {
-    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, la_try + 2, G);
+    // la_try + 1 iterations tried together, 2 la_try + 2 buffers
+    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, 2 * la_try + 2, G);
     *blocks = 0;
     if ((int64_t)L.total > optin) return false;
     if (moda::warp_occupancy(narrow, G, L.total, blocks) != cudaSuccess || *blocks < 1)
@@ -1013,7 +1014,8 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.items = reinterpret_cast<const int2 *>(base + d_bytes);
   L.nitems = (int32_t)items.size();
   L.lookahead = la;
-  L.nbuf = la + 2;
+  L.window = la + 1;
+  L.nbuf = la + L.window + 1;
   L.team = best_w;
   L.counter = reinterpret_cast<int32_t *>(base + d_bytes + i_bytes);
   L.cache = static_cast<unsigned char *>(scratch->cache);

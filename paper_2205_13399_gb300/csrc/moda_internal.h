@@ -235,7 +235,7 @@ cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t sm
 // lenient: min_k max(0, dE_k)) saturated to uint32; the integer cost fields
 // L_k (int32 pairs) live in global memory and are read only by flips.
 
-constexpr int kWarpRing = 64;   // draw / schedule ring entries (iterations)
+constexpr int kWarpRing = 128;  // draw / schedule ring entries (iterations)
 constexpr int kWarpMaxLA = 6;   // prefetch distance (iterations ahead)
 
 // Records of one archive slot for a run of n, m (the field cache of the
@@ -286,15 +286,15 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nbuf, 16);
   L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
   L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
-  // accepted counts of the warps by iteration parity [2][8], the work
-  // item, the warps' partial sums of a rebuild [8][2]
-  L.cnt = (uint32_t)o;       o = align_up(o + 64 + 16 + 128, 16);
+  // accepted counts of the warps by round parity [2][8 positions + 2][8],
+  // the work item, the warps' partial sums of a rebuild [8][2]
+  L.cnt = (uint32_t)o;       o = align_up(o + 640 + 16 + 128, 16);
   L.team = (uint32_t)o;
   o = 0;
   L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
   L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
-  L.pf = (uint32_t)o;        o = align_up(o + 16 * 8 + 4 * 8, 16);
+  L.pf = (uint32_t)o;        o = align_up(o + 16 * 16 + 4 * 16, 16);
   L.warp = (uint32_t)o;
   L.total = L.team + (uint32_t)G * L.warp;
   return L;
@@ -333,9 +333,11 @@ struct WarpLaunch {
   const WarpRun *runs;
   const int2 *items;         // (run, replica row), largest runs first
   int32_t nitems;
-  int32_t nbuf;              // jump-record buffers per team: lookahead + 2
+  int32_t nbuf;              // jump-record buffers per team: lookahead + window + 1
   int32_t lookahead;         // prefetch distance, 0 .. kWarpMaxLA
   int32_t team;              // G: warps per replica (1 .. 8)
+  int32_t window;            // iterations tried together, 1 .. lookahead + 1
+  int32_t pad2;
   int32_t *counter;          // next item; zero before the launch
   unsigned char *cache;      // field-cache region of each resident team
   size_t cache_stride;       // bytes per team

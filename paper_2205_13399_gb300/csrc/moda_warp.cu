@@ -140,16 +140,17 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   uint64_t *sbar = reinterpret_cast<uint64_t *>(ts + SL.mbar);
   WRing *ring = reinterpret_cast<WRing *>(ts + SL.ring);
   longlong2 *sAE = reinterpret_cast<longlong2 *>(ts + SL.aE);
-  // accepted counts of the warps, [iteration parity][warp]: a warp may
-  // write its next count while another still reads this iteration's
+  // accepted counts of the warps by round parity: [window position][warp],
+  // then [warp] its first window position with an accepted bit (a warp may
+  // write the next round's while another still reads this round's)
   int32_t *sCnt = reinterpret_cast<int32_t *>(ts + SL.cnt);
-  int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 80);  // [G][2] rebuild sums
+  int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 656);  // [G][2] rebuild sums
   unsigned char *ws = T.ws0 + (size_t)wt * SL.warp;
-  // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 7]
+  // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 15]
   // = {buffer or -1, slot, issuing iteration} of the copy for target
-  // iteration tt; sWr[x & 7] = the slot iteration x wrote (-1: none)
+  // iteration tt; sWr[x & 15] = the slot iteration x wrote (-1: none)
   int4 *sPf = reinterpret_cast<int4 *>(ws + SL.pf);
-  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 128);
+  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 256);
   uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
   int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
   int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
@@ -342,12 +343,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         x0[4 * c + w] = v;
       }
     }
-    if (lane < 8) {
+    if (lane < 16) {
       sPf[lane] = make_int4(-1, 0, 0, 0);
       sWr[lane] = -1;
     }
     if (leader) {
-      if (lane < 16) sCnt[lane] = 0;  // counts of warps beyond G stay 0
+      for (int q2 = lane; q2 < 160; q2 += 32) sCnt[q2] = 0;  // counts of warps beyond G stay 0
       fill(1);
       fill(33);
     }
@@ -372,123 +373,284 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   uint32_t last_wr_t = 0;
   bool rc_stale = false;
 
-  for (uint32_t t = 1; t <= I_max; ++t) {
-    if (leader && (t & 31u) == 1u && t > 1u) fill(t + 32u);  // iterations t + 32 .. t + 63
-    if (lane == 0) sWr[t & 7u] = -1;
-    __syncwarp();
-    const WRing e = ring[t % kWarpRing];
+  // Rounds of up to KW iterations.  While the replica only jumps, the
+  // states of the next iterations are known in advance -- iteration tau
+  // jumps to the member its restart draw picks among |A| -- and their jump
+  // records are prefetched, so the trials of a window of iterations t ..
+  // t + K - 1 run together, iteration t + k on the member iteration
+  // t + k - 1 would land on.  Every bit of every iteration is tested.  The
+  // first iteration of the window that accepts a bit flips (the window's
+  // earlier iterations were jumps, as assumed), and the trials after it
+  // are discarded; a window without an accepted bit commits K jumps.
+  const int KW = Lc.window;
+  uint32_t filled = 64;  // the ring holds the iterations up to `filled`
+  // Every target iteration tau gets one record sPf[tau & 15], a copy or
+  // none, written once, in the round that first reaches it; records up to
+  // issued_to are written (none for 1 .. LA).
+  uint32_t issued_to = (uint32_t)LA;
+  uint32_t t = 1, rnd = 0;
+  while (t <= I_max) {
+    if (leader)
+      while (filled < t + 48u) {
+        fill(filled + 1u);
+        filled += 32u;
+      }
+    const int K = (KW > 1 && acount > 0 && flip_streak == 0)
+                      ? (int)min((uint32_t)KW, I_max - t + 1u)
+                      : 1;
 
-    // ---- prefetch: the jump record of the member a jump at t + LA would
-    // land on (its draw and |A| are known), unless the replica is in a run
-    // of flips
+    // ---- prefetch: the jump records of the members jumps up to t + K - 1
+    // + LA would land on (their draws and |A| are known), unless the
+    // replica is in a run of flips.  At most LA + K + 1 buffers are held:
+    // the state's and those of targets t .. t + K - 1 + LA.
     if (LA > 0) {
-      const uint32_t tt = t + (uint32_t)LA;
-      int4 rec_pf = make_int4(-1, 0, 0, 0);
-      if (acount > 0 && flip_streak < 3 && tt <= I_max) {
-        const int sp = pick(ring[tt % kWarpRing].rst, acount);
-        // a slot written in the previous iteration is left alone: warps
-        // still writing it are ordered before the copy only by the next
-        // barrier
-        if (sp < cslots && sWr[(t - 1u) & 7u] != sp) {
-          const int b = __ffs(freeb) - 1;  // exists: LA + 1 buffers are held
-          freeb &= ~(1u << b);
-          if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
-            retire_buf(b);
-            pend &= ~(1u << b);
+      for (uint32_t tt = issued_to + 1u; tt <= t + (uint32_t)(K - 1 + LA); ++tt) {
+        int4 rec_pf = make_int4(-1, 0, 0, 0);
+        if (acount > 0 && flip_streak < 3 && tt <= I_max) {
+          const int sp = pick(ring[tt % kWarpRing].rst, acount);
+          // a slot written in the previous iteration is left alone: warps
+          // still writing it are ordered before the copy only by the next
+          // barrier
+          if (sp < cslots && sWr[(t - 1u) & 15u] != sp) {
+            const int b = __ffs(freeb) - 1;
+            freeb &= ~(1u << b);
+            if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
+              retire_buf(b);
+              pend &= ~(1u << b);
+            }
+            copy_record(b, sp);
+            pend |= 1u << b;
+            rec_pf = make_int4(b, sp, (int)t, 0);
           }
-          copy_record(b, sp);
-          pend |= 1u << b;
-          rec_pf = make_int4(b, sp, (int)t, 0);
         }
+        sPf[tt & 15u] = rec_pf;  // every lane: no lane reads another's write
       }
-      if (lane == 0) sPf[tt & 7u] = rec_pf;
+      issued_to = t + (uint32_t)(K - 1 + LA);
+    }
+    // The copy for target iteration tau is usable if it began for the slot
+    // tau's draw picks now and no iteration before `lim` rewrote that slot
+    // since (the iterations of this window write nothing before a flip).
+    auto usable = [&](uint32_t tau, int slot, uint32_t lim) {
+      const int4 pr = sPf[tau & 15u];
+      bool ok = pr.x >= 0 && pr.y == slot;
+      if (ok && last_wr_t >= (uint32_t)pr.z)
+        for (uint32_t xi = (uint32_t)pr.z; xi < lim; ++xi)
+          if (sWr[xi & 15u] == slot) ok = false;
+      return ok;
+    };
+    // the window: iteration t + k (k >= 1) tries the member iteration
+    // t + k - 1 would jump to, if its record is here
+    int Keff = 1;
+    for (int k = 1; k < K; ++k) {
+      const uint32_t tau = t + (uint32_t)(k - 1);
+      if (!usable(tau, pick(ring[tau % kWarpRing].rst, acount), t)) break;
+      Keff = k + 1;
+    }
+    for (int k = 1; k < Keff; ++k) {  // those records, for every warp
+      const int b = sPf[(t + (uint32_t)(k - 1)) & 15u].x;
+      take_buf(b);
+      pend &= ~(1u << b);
     }
 
-    // ---- the parallel trial of every bit (Eq. pacceptms / pacceptml) -----
-    const double delta = e.delta;
-    const int64_t lo = e.lo, hi = e.hi;
-    const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
-    const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
-    const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(cur));
-    int cnt_w = 0, nl = 0;
+    // ---- the parallel trials (Eq. pacceptms / pacceptml) of the window,
+    // this warp's chunks, up to its first accepted bit
+    int32_t *cntr = sCnt + 80 * (int)(rnd & 1u);  // [k][warp] counts, then [warp] first k
+    int first_w = Keff, nl = 0;
+    for (int k = 0; k < Keff; ++k) {
+      const uint32_t tk = t + (uint32_t)k;
+      const WRing e = ring[tk % kWarpRing];
+      const double delta = e.delta;
+      const int64_t lo = e.lo, hi = e.hi;
+      const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
+      const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
+      int sb = cur;
+      const int2 *Lk = curL;
+      const unsigned char *rck = rc_stale ? bRC(cur) : rcp;
+      if (k > 0) {
+        const int4 pr = sPf[(tk - 1u) & 15u];
+        sb = pr.x;
+        Lk = gLR + (size_t)pr.y * rec.mp;
+        rck = bRC(sb);
+      }
+      const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(sb));
+      int cnt_w = 0;
 #pragma unroll 4
-    for (int c = c0; c < c1; ++c) {
-      const uint4 a4 = a4p[c * 32 + lane];
-      const uint32_t amin = min(min(a4.x, a4.y), min(a4.z, a4.w));
-      if (__any_sync(kFull, amin <= hi32)) {
-        // some bit of the chunk may be accepted: exact decisions
-        const int p0 = c * 128 + lane * 4;
-        const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
-        bool acc[4], need[4];
-        double ad[4];
-        bool anyneed = false;
+      for (int c = c0; c < c1; ++c) {
+        const uint4 a4 = a4p[c * 32 + lane];
+        const uint32_t amin = min(min(a4.x, a4.y), min(a4.z, a4.w));
+        if (__any_sync(kFull, amin <= hi32)) {
+          // some bit of the chunk may be accepted: exact decisions
+          const int p0 = c * 128 + lane * 4;
+          const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+          bool acc[4], need[4];
+          double ad[4];
+          bool anyneed = false;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[j] = false;
-          need[j] = false;
-          ad[j] = 0.0;
-          if (p0 + j < m && av[j] <= hi32) {
-            if (NARROW) {
-              // a < 2^32 - 1: the clamped thresholds decide exactly
-              if (av[j] <= lo32)
-                acc[j] = true;
-              else
-                need[j] = true;
-              ad[j] = (double)av[j];
-            } else {
-              const int64_t ax = av[j] == 0xFFFFFFFFu
-                                     ? exact_penalty(cur, curL, rc_stale ? bRC(cur) : rcp, p0 + j)
-                                     : (int64_t)av[j];
-              if (ax <= lo)
-                acc[j] = true;
-              else if (ax <= hi)
-                need[j] = true;
-              ad[j] = (double)ax;
+          for (int j = 0; j < 4; ++j) {
+            acc[j] = false;
+            need[j] = false;
+            ad[j] = 0.0;
+            if (p0 + j < m && av[j] <= hi32) {
+              if (NARROW) {
+                // a < 2^32 - 1: the clamped thresholds decide exactly
+                if (av[j] <= lo32)
+                  acc[j] = true;
+                else
+                  need[j] = true;
+                ad[j] = (double)av[j];
+              } else {
+                const int64_t ax =
+                    av[j] == 0xFFFFFFFFu ? exact_penalty(sb, Lk, rck, p0 + j) : (int64_t)av[j];
+                if (ax <= lo)
+                  acc[j] = true;
+                else if (ax <= hi)
+                  need[j] = true;
+                ad[j] = (double)ax;
+              }
             }
+            anyneed |= need[j];
           }
-          anyneed |= need[j];
-        }
-        if (__any_sync(kFull, anyneed)) {
-          // a in (lo, hi]: the draw decides (R7, R21); group 32c + lane
-          uint32_t d[4] = {(uint32_t)(c * 32 + lane), t, rep, kTagAccept};
-          philox10(d, k0, k1);
+          if (__any_sync(kFull, anyneed)) {
+            // a in (lo, hi]: the draw decides (R7, R21); group 32c + lane
+            uint32_t d[4] = {(uint32_t)(c * 32 + lane), tk, rep, kTagAccept};
+            philox10(d, k0, k1);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
-        }
-        const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
-                       b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
-        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
-        if (cnt > 0) {
-          if (lane == 0) {
-            sAccW[nl] = make_uint4(b0, b1, b2, b3);
-            sAccC[nl] = c;
+            for (int j = 0; j < 4; ++j)
+              if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
           }
-          ++nl;
-          cnt_w += cnt;
+          const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
+                         b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
+          const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+          if (cnt > 0) {
+            if (lane == 0) {
+              sAccW[nl] = make_uint4(b0, b1, b2, b3);
+              sAccC[nl] = c;
+            }
+            ++nl;
+            cnt_w += cnt;
+          }
         }
       }
+      if (lane == 0) cntr[8 * k + wt] = cnt_w;
+      if (cnt_w > 0) {
+        first_w = k;
+        break;
+      }
     }
-    int32_t *cntp = sCnt + 8 * (int)(t & 1u);
-    if (lane == 0) cntp[wt] = cnt_w;
-    // every warp's count, and whether any warp gave up a wait
+    if (lane == 0) cntr[64 + wt] = first_w;
+    // every warp's counts, and whether any warp gave up a wait
     if (sync_or(fail)) {
       fail = true;
       break;
     }
-    const int4 ca = reinterpret_cast<const int4 *>(cntp)[0],
-               cb = reinterpret_cast<const int4 *>(cntp)[1];
-    const int total = ca.x + ca.y + ca.z + ca.w + cb.x + cb.y + cb.z + cb.w;
+    int kstar = Keff;  // the window's first iteration with an accepted bit
+    for (int w = 0; w < G; ++w) kstar = min(kstar, (int)cntr[64 + w]);
+    ++rnd;
 
-    // the copy for this iteration: taken by a jump below, else given back
-    const int4 pr = LA > 0 ? sPf[t & 7u] : make_int4(-1, 0, 0, 0);
-    int kind = 0;  // 1 flip, 2 jump, 0 neither
-    int event_slot = 0, ps = 0;
-    if (total > 0) {
+    // ---- iterations t .. t + kstar - 1 jump (Alg. 3), or escape with an
+    // empty archive (R12)
+    for (int k = 0; k < kstar; ++k) {
+      const uint32_t tk = t + (uint32_t)k;
+      sWr[tk & 15u] = -1;
+      if (acount == 0) {
+        const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
+        if (pr.x >= 0) freeb |= 1u << pr.x;
+        ++nempty;
+        if (trace != nullptr && leader && lane == 0) {
+          int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tk - 1)) * 3;
+          tr[0] = E1;
+          tr[1] = E2;
+          tr[2] = INT64_MIN;
+        }
+        continue;
+      }
+      const int slot = pick(ring[tk % kWarpRing].rst, acount);
+      int nbuf;
+      if (k + 1 < Keff) {
+        nbuf = sPf[tk & 15u].x;  // tried by iteration tk + 1: taken above
+        ++npref;
+      } else {
+        const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
+        if (LA > 0 && usable(tk, slot, tk)) {
+          nbuf = pr.x;
+          take_buf(nbuf);
+          pend &= ~(1u << nbuf);
+          ++npref;
+        } else {
+          if (pr.x >= 0) freeb |= 1u << pr.x;
+          nbuf = __ffs(freeb) - 1;
+          freeb &= ~(1u << nbuf);
+          if ((pend >> nbuf) & 1u) {
+            retire_buf(nbuf);
+            pend &= ~(1u << nbuf);
+          }
+          if (slot < cslots) {
+            copy_record(nbuf, slot);
+            take_buf(nbuf);
+          } else {
+            // no records for this slot: rebuild from its state (the old
+            // state's buffer is the scratch)
+            uint32_t *xn = bX(nbuf);
+            for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
+              xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
+            sync();
+            int64_t t1, t2, gp;
+            rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
+          }
+          ++ndirect;
+        }
+      }
+      freeb |= 1u << cur;
+      cur = nbuf;
+      if (slot < cslots) {
+        curL = gLR + (size_t)slot * rec.mp;
+        const int64_t *be = bE(cur);
+        E1 = be[0];
+        E2 = be[1];
+        rc_stale = true;
+      } else {
+        curL = gWork;
+        E1 = gE[2 * slot];
+        E2 = gE[2 * slot + 1];
+        rc_stale = false;
+      }
+      ++njump;
+      if (trace != nullptr && leader && lane == 0) {
+        int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tk - 1)) * 3;
+        tr[0] = E1;
+        tr[1] = E2;
+        tr[2] = -1 - (int64_t)slot;
+      }
+    }
+    if (kstar == Keff) {  // no bit accepted in the window
+      t += (uint32_t)Keff;
+      flip_streak = 0;
+      __syncwarp();
+      continue;
+    }
+
+    // ---- iteration tf = t + kstar flips.  Every record of targets tf
+    // onwards is given up (the flip may change |A| or rewrite their slots):
+    // a copy taken by the window has landed, one still in flight is waited
+    // for before its buffer is filled again.  The next round copies again
+    // from target tf + 1.
+    const uint32_t tf = t + (uint32_t)kstar;
+    if (LA > 0) {
+      for (uint32_t tau = tf; tau <= issued_to; ++tau) {
+        const int b = sPf[tau & 15u].x;
+        if (b >= 0) freeb |= 1u << b;
+        sPf[tau & 15u].x = -1;
+      }
+      issued_to = tf;
+    }
+    const WRing ef = ring[tf % kWarpRing];
+    const int32_t *cntp = cntr + 8 * kstar;  // [warp] counts of iteration tf
+    {
+      const int4 ca = reinterpret_cast<const int4 *>(cntp)[0],
+                 cb = reinterpret_cast<const int4 *>(cntp)[1];
+      const int total = ca.x + ca.y + ca.z + ca.w + cb.x + cb.y + cb.z + cb.w;
       // ---- one accepted flip at random (R11): rank r in ascending bit order
-      if (pr.x >= 0) freeb |= 1u << pr.x;
-      kind = 1;
-      int r = pick(e.sel, total);
+      int r = pick(ef.sel, total);
       int ow = 0;
       while (r >= cntp[ow]) r -= cntp[ow++];  // the warp holding rank r
       const unsigned char *ows = T.ws0 + (size_t)ow * SL.warp;
@@ -514,7 +676,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const int owner = __ffs(who) - 1;
       int jj = mine ? nth_set_bit(nib, rr - (incl - cl)) : 0;
       jj = __shfl_sync(kFull, jj, owner);
-      ps = c * 128 + owner * 4 + jj;
+      const int ps = c * 128 + owner * 4 + jj;
 
       if (rc_stale) {  // this warp's counts of the state the jump reached
         const unsigned char *rc = bRC(cur);
@@ -598,7 +760,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         }
         if (!anyd) {
           if (nb > 0) {
-            int want = pick(e.exp, nb);
+            int want = pick(ef.exp, nb);
             for (int base = 0; base < acount; base += 32) {
               const int y = base + lane;
               bool dom = false;
@@ -623,8 +785,8 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // every warp has read the archive and the accepted lists: they may
       // change now
       sync();
-      if (lane == 0) sWr[t & 7u] = target;
-      if (target >= 0) last_wr_t = t;
+      sWr[tf & 15u] = target;
+      if (target >= 0) last_wr_t = tf;
       if (target >= 0 && leader && lane == 0) {
         gE[2 * target] = nE1;
         gE[2 * target + 1] = nE2;
@@ -717,72 +879,17 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       curL = dstL;
       E1 = nE1;
       E2 = nE2;
-      event_slot = target;
       ++nflip;
-    } else if (acount > 0) {
-      // ---- no bit accepted: jump to a random archive member (Alg. 3)
-      kind = 2;
-      const int slot = pick(e.rst, acount);
-      event_slot = slot;
-      bool ok = pr.x >= 0 && pr.y == slot;
-      if (ok && last_wr_t >= (uint32_t)pr.z)  // some slot was written after the copy began
-        for (uint32_t xi = (uint32_t)pr.z; xi < t; ++xi)
-          if (sWr[xi & 7u] == slot) ok = false;  // rewritten after the copy began
-      int nbuf;
-      if (ok) {
-        nbuf = pr.x;
-        take_buf(nbuf);
-        pend &= ~(1u << nbuf);
-        ++npref;
-      } else {
-        if (pr.x >= 0) freeb |= 1u << pr.x;
-        nbuf = __ffs(freeb) - 1;
-        freeb &= ~(1u << nbuf);
-        if ((pend >> nbuf) & 1u) {
-          retire_buf(nbuf);
-          pend &= ~(1u << nbuf);
-        }
-        if (slot < cslots) {
-          copy_record(nbuf, slot);
-          take_buf(nbuf);
-        } else {
-          // no records for this slot: rebuild from its state (the old
-          // state's buffer is the scratch)
-          uint32_t *xn = bX(nbuf);
-          for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
-            xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
-          sync();
-          int64_t t1, t2, gp;
-          rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
-        }
-        ++ndirect;
+      if (trace != nullptr && leader && lane == 0) {
+        int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tf - 1)) * 3;
+        tr[0] = E1;
+        tr[1] = E2;
+        tr[2] = (int64_t)ps;
       }
-      freeb |= 1u << cur;
-      cur = nbuf;
-      if (slot < cslots) {
-        curL = gLR + (size_t)slot * rec.mp;
-        const int64_t *be = bE(cur);
-        E1 = be[0];
-        E2 = be[1];
-        rc_stale = true;
-      } else {
-        curL = gWork;
-        E1 = gE[2 * slot];
-        E2 = gE[2 * slot + 1];
-        rc_stale = false;
-      }
-      ++njump;
-    } else {
-      if (pr.x >= 0) freeb |= 1u << pr.x;
-      ++nempty;  // empty archive: the state stays (R12)
     }
-    flip_streak = kind == 1 ? flip_streak + 1 : 0;
-    if (trace != nullptr && leader && lane == 0) {
-      int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(t - 1)) * 3;
-      tr[0] = E1;
-      tr[1] = E2;
-      tr[2] = kind == 1 ? (int64_t)ps : kind == 2 ? -1 - (int64_t)event_slot : INT64_MIN;
-    }
+    flip_streak = kstar == 0 ? flip_streak + 1 : 1;
+    t = tf + 1u;
+    __syncwarp();
   }
   // no bulk copy may be in flight when the item ends
   for (int b = 0; b < NB; ++b)
@@ -830,7 +937,7 @@ __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L)
   T.ts = smem + (size_t)team * L.sm.total;
   T.ws0 = T.ts + L.sm.team;
   uint64_t *bar = reinterpret_cast<uint64_t *>(T.ts + L.sm.mbar);
-  int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 64);
+  int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 640);
   const bool leader = T.wt == 0;
   if (leader && lane == 0) {
     for (int b = 0; b < L.nbuf; ++b) mbar_init(&bar[b], 1);

@@ -402,30 +402,53 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // ---- prefetch: the jump records of the members jumps up to t + K - 1
     // + LA would land on (their draws and |A| are known), unless the
     // replica is in a run of flips.  At most LA + K + 1 buffers are held:
-    // the state's and those of targets t .. t + K - 1 + LA.
+    // the state's and those of targets t .. t + K - 1 + LA.  Lane k
+    // handles target issued_to + 1 + k; every warp keeps the same books,
+    // the leader warp's lanes start the copies.
     if (LA > 0) {
-      for (uint32_t tt = issued_to + 1u; tt <= t + (uint32_t)(K - 1 + LA); ++tt) {
-        int4 rec_pf = make_int4(-1, 0, 0, 0);
-        if (acount > 0 && flip_streak < 3 && tt <= I_max) {
-          const int sp = pick(ring[tt % kWarpRing].rst, acount);
-          // a slot written in the previous iteration is left alone: warps
-          // still writing it are ordered before the copy only by the next
-          // barrier
-          if (sp < cslots && sWr[(t - 1u) & 15u] != sp) {
-            const int b = __ffs(freeb) - 1;
-            freeb &= ~(1u << b);
-            if ((pend >> b) & 1u) {  // an unused earlier copy still lands here
-              retire_buf(b);
-              pend &= ~(1u << b);
-            }
-            copy_record(b, sp);
-            pend |= 1u << b;
-            rec_pf = make_int4(b, sp, (int)t, 0);
-          }
-        }
-        sPf[tt & 15u] = rec_pf;  // every lane: no lane reads another's write
+      // targets not yet given a record (none when an earlier, longer
+      // window already reached t + K - 1 + LA)
+      const int nI = (int)(t + (uint32_t)(K - 1 + LA)) - (int)issued_to;
+      const uint32_t tt = issued_to + 1u + (uint32_t)lane;
+      int sp = 0;
+      bool want = false;
+      if (lane < nI && acount > 0 && flip_streak < 3 && tt <= I_max) {
+        sp = pick(ring[tt % kWarpRing].rst, acount);
+        // a slot written in the previous iteration is left alone: warps
+        // still writing it are ordered before the copy only by the next
+        // barrier
+        want = sp < cslots && sWr[(t - 1u) & 15u] != sp;
       }
-      issued_to = t + (uint32_t)(K - 1 + LA);
+      const uint32_t wm = __ballot_sync(kFull, want);
+      // the r-th copy takes the r-th free buffer (there are enough: at
+      // most NB - 1 - (issued_to - t + 1) >= nI are held)
+      const int rank = __popc(wm & ((1u << lane) - 1u));
+      int b = want ? nth_set_bit(freeb, rank) : -1;
+      if (b >= NB || (b >= 0 && !((freeb >> b) & 1u))) {  // never: the books are kept so
+        fail = true;
+        b = -1;
+      }
+      const uint32_t bm = __reduce_or_sync(kFull, b >= 0 ? 1u << b : 0u);  // buffers taken now
+      freeb &= ~bm;
+      const uint32_t stale = pend & bm;  // unused earlier copies still land there
+      if (stale) {
+        if (leader) {
+          bool ok = true;
+          if (b >= 0 && ((stale >> b) & 1u)) ok = mbar_wait(&sbar[b], (par >> b) & 1u);
+          if (!__all_sync(kFull, ok)) fail = true;
+        }
+        par ^= stale;
+        pend &= ~stale;
+      }
+      if (leader && b >= 0) {
+        fence_proxy_async_shared();
+        mbar_expect_tx(&sbar[b], rec.jr);
+        bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
+      }
+      pend |= bm;
+      if (lane < nI) sPf[tt & 15u] = make_int4(b, b >= 0 ? sp : 0, (int)t, 0);
+      if (nI > 0) issued_to += (uint32_t)nI;
+      __syncwarp();
     }
     // The copy for target iteration tau is usable if it began for the slot
     // tau's draw picks now and no iteration before `lim` rewrote that slot
@@ -439,23 +462,51 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       return ok;
     };
     // the window: iteration t + k (k >= 1) tries the member iteration
-    // t + k - 1 would jump to, if its record is here
+    // t + k - 1 would jump to, if its record is here (lane k - 1 checks)
     int Keff = 1;
-    for (int k = 1; k < K; ++k) {
-      const uint32_t tau = t + (uint32_t)(k - 1);
-      if (!usable(tau, pick(ring[tau % kWarpRing].rst, acount), t)) break;
-      Keff = k + 1;
-    }
-    for (int k = 1; k < Keff; ++k) {  // those records, for every warp
-      const int b = sPf[(t + (uint32_t)(k - 1)) & 15u].x;
-      take_buf(b);
-      pend &= ~(1u << b);
+    if (K > 1) {
+      bool u = false;
+      if (lane < K - 1) {
+        const uint32_t tau = t + (uint32_t)lane;
+        u = usable(tau, pick(ring[tau % kWarpRing].rst, acount), t);
+      }
+      const uint32_t um = __ballot_sync(kFull, u);
+      Keff = 1 + __ffs(~um) - 1;  // leading usable targets
+      if (Keff > K) Keff = K;
+      // those records, for every warp: lane k waits for target t + k
+      bool ok = true;
+      int tb = -1;
+      if (lane < Keff - 1) {
+        tb = sPf[(t + (uint32_t)lane) & 15u].x;
+        ok = mbar_wait(&sbar[tb], (par >> tb) & 1u);
+      }
+      if (!__all_sync(kFull, ok)) fail = true;
+      const uint32_t tm = __reduce_or_sync(kFull, tb >= 0 ? 1u << tb : 0u);
+      par ^= tm;
+      pend &= ~tm;
     }
 
     // ---- the parallel trials (Eq. pacceptms / pacceptml) of the window,
     // this warp's chunks, up to its first accepted bit
     int32_t *cntr = sCnt + 80 * (int)(rnd & 1u);  // [k][warp] counts, then [warp] first k
     int first_w = Keff, nl = 0;
+    // first every bit of the window against its hi_t: usually none can be
+    // accepted, and the window's trials end here
+    bool cand = false;
+    for (int k = 0; k < Keff; ++k) {
+      const int64_t hk = ring[(t + (uint32_t)k) % kWarpRing].hi;
+      const uint32_t h32 = hk < 0xFFFFFFFFll ? (uint32_t)hk : 0xFFFFFFFFu;
+      const int sbk = k == 0 ? cur : sPf[(t + (uint32_t)(k - 1)) & 15u].x;
+      const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
+#pragma unroll 4
+      for (int c = c0; c < c1; ++c) {
+        const uint4 a4 = ap[c * 32 + lane];
+        cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+      }
+    }
+    if (!__any_sync(kFull, cand)) {
+      if (lane < Keff) cntr[8 * lane + wt] = 0;
+    } else
     for (int k = 0; k < Keff; ++k) {
       const uint32_t tk = t + (uint32_t)k;
       const WRing e = ring[tk % kWarpRing];
@@ -549,77 +600,101 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
 
     // ---- iterations t .. t + kstar - 1 jump (Alg. 3), or escape with an
     // empty archive (R12)
-    for (int k = 0; k < kstar; ++k) {
-      const uint32_t tk = t + (uint32_t)k;
-      sWr[tk & 15u] = -1;
-      if (acount == 0) {
-        const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
+    if (kstar > 0) {
+      if (lane < kstar) sWr[(t + (uint32_t)lane) & 15u] = -1;
+      __syncwarp();
+      if (acount == 0) {  // K = 1: one iteration
+        const int4 pr = LA > 0 ? sPf[t & 15u] : make_int4(-1, 0, 0, 0);
         if (pr.x >= 0) freeb |= 1u << pr.x;
         ++nempty;
         if (trace != nullptr && leader && lane == 0) {
-          int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tk - 1)) * 3;
+          int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(t - 1)) * 3;
           tr[0] = E1;
           tr[1] = E2;
           tr[2] = INT64_MIN;
         }
-        continue;
-      }
-      const int slot = pick(ring[tk % kWarpRing].rst, acount);
-      int nbuf;
-      if (k + 1 < Keff) {
-        nbuf = sPf[tk & 15u].x;  // tried by iteration tk + 1: taken above
-        ++npref;
       } else {
-        const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
-        if (LA > 0 && usable(tk, slot, tk)) {
-          nbuf = pr.x;
-          take_buf(nbuf);
-          pend &= ~(1u << nbuf);
-          ++npref;
-        } else {
-          if (pr.x >= 0) freeb |= 1u << pr.x;
-          nbuf = __ffs(freeb) - 1;
-          freeb &= ~(1u << nbuf);
-          if ((pend >> nbuf) & 1u) {
-            retire_buf(nbuf);
-            pend &= ~(1u << nbuf);
+        // jumps to targets t .. t + ns - 1 land on records the window
+        // took: the state passes through them and keeps the last
+        const int ns = min(kstar, Keff - 1);
+        if (trace != nullptr && leader && lane == 0)
+          for (int k = 0; k < ns; ++k) {
+            const int4 pr = sPf[(t + (uint32_t)k) & 15u];
+            const int64_t *be = bE(pr.x);
+            int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(t + k - 1)) * 3;
+            tr[0] = be[0];
+            tr[1] = be[1];
+            tr[2] = -1 - (int64_t)pr.y;
           }
-          if (slot < cslots) {
-            copy_record(nbuf, slot);
-            take_buf(nbuf);
-          } else {
-            // no records for this slot: rebuild from its state (the old
-            // state's buffer is the scratch)
-            uint32_t *xn = bX(nbuf);
-            for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
-              xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
-            sync();
-            int64_t t1, t2, gp;
-            rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
-          }
-          ++ndirect;
+        if (ns > 0) {
+          for (int k = 0; k + 1 < ns; ++k) freeb |= 1u << sPf[(t + (uint32_t)k) & 15u].x;
+          freeb |= 1u << cur;
+          const int4 pr = sPf[(t + (uint32_t)(ns - 1)) & 15u];
+          cur = pr.x;
+          curL = gLR + (size_t)pr.y * rec.mp;
+          const int64_t *be = bE(cur);
+          E1 = be[0];
+          E2 = be[1];
+          rc_stale = true;
+          npref += (uint32_t)ns;
+          njump += (uint32_t)ns;
         }
-      }
-      freeb |= 1u << cur;
-      cur = nbuf;
-      if (slot < cslots) {
-        curL = gLR + (size_t)slot * rec.mp;
-        const int64_t *be = bE(cur);
-        E1 = be[0];
-        E2 = be[1];
-        rc_stale = true;
-      } else {
-        curL = gWork;
-        E1 = gE[2 * slot];
-        E2 = gE[2 * slot + 1];
-        rc_stale = false;
-      }
-      ++njump;
-      if (trace != nullptr && leader && lane == 0) {
-        int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tk - 1)) * 3;
-        tr[0] = E1;
-        tr[1] = E2;
-        tr[2] = -1 - (int64_t)slot;
+        if (kstar > ns) {
+          // the window's last iteration jumps to a member no trial holds
+          const uint32_t tk = t + (uint32_t)(kstar - 1);
+          const int slot = pick(ring[tk % kWarpRing].rst, acount);
+          const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
+          int nbuf;
+          if (LA > 0 && usable(tk, slot, tk)) {
+            nbuf = pr.x;
+            take_buf(nbuf);
+            pend &= ~(1u << nbuf);
+            ++npref;
+          } else {
+            if (pr.x >= 0) freeb |= 1u << pr.x;
+            nbuf = __ffs(freeb) - 1;
+            freeb &= ~(1u << nbuf);
+            if ((pend >> nbuf) & 1u) {
+              retire_buf(nbuf);
+              pend &= ~(1u << nbuf);
+            }
+            if (slot < cslots) {
+              copy_record(nbuf, slot);
+              take_buf(nbuf);
+            } else {
+              // no records for this slot: rebuild from its state (the old
+              // state's buffer is the scratch)
+              uint32_t *xn = bX(nbuf);
+              for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
+                xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
+              sync();
+              int64_t t1, t2, gp;
+              rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
+            }
+            ++ndirect;
+          }
+          freeb |= 1u << cur;
+          cur = nbuf;
+          if (slot < cslots) {
+            curL = gLR + (size_t)slot * rec.mp;
+            const int64_t *be = bE(cur);
+            E1 = be[0];
+            E2 = be[1];
+            rc_stale = true;
+          } else {
+            curL = gWork;
+            E1 = gE[2 * slot];
+            E2 = gE[2 * slot + 1];
+            rc_stale = false;
+          }
+          ++njump;
+          if (trace != nullptr && leader && lane == 0) {
+            int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(tk - 1)) * 3;
+            tr[0] = E1;
+            tr[1] = E2;
+            tr[2] = -1 - (int64_t)slot;
+          }
+        }
       }
     }
     if (kstar == Keff) {  // no bit accepted in the window

@@ -158,10 +158,14 @@ typedef struct {
                               largest G that keeps every replica resident
                               at once, else 1; block_threads = 32 G
                               prescribes it.
+                              While a replica only jumps, the trials of up
+                              to prefetch iterations run together on the
+                              members the earlier ones jump to (every bit of
+                              every iteration is still tested; the first
+                              iteration that accepts a bit flips and later
+                              trials are discarded).
                             0 auto: warp when the options allow it and
-                              block_threads is 0, else block; a plain
-                              moda_anneal whose replicas fit one per SM
-                              takes block. */
+                              block_threads is 0, else block. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */

@@ -297,20 +297,9 @@ bool uses_warp(const moda_params *p) {
   return p->engine == 2 || (p->engine == 0 && warp_options(p) && p->block_threads == 0);
 }
 
-// A plain anneal with the automatic engine: whose replicas fit one per SM
-// runs on the block engine (a whole block per replica: the shortest
-// iteration), more replicas on the warp engine.  Batches and the server
-// keep the warp engine, whose work list packs many runs.
-moda_params resolve_plain(moda_instance inst, const moda_params *p) {
-  moda_params q = *p;
-  if (q.engine == 0 && q.block_threads == 0 && warp_options(p)) {
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inst->device) == cudaSuccess &&
-        q.replicas <= sms)
-      q.engine = 1;
-  }
-  return q;
-}
+// The engine of a plain anneal with the automatic choice: the same rule as
+// batches and the server (the warp engine whenever the options allow it).
+moda_params resolve_plain(moda_instance, const moda_params *p) { return *p; }
 
 // Archive slots with field-cache records per resident warp by default.
 constexpr int kWarpCacheSlots = 1024;
@@ -900,9 +889,13 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   const int nc_max = (m_max + 127) / 128;
   const int la_max = la;
   moda::WarpSmem sm{};
-  auto resident = [&](int G, int la_try, int se_try, int *blocks, moda::WarpSmem *out) {
-    // la_try + 1 iterations tried together, 2 la_try + 2 buffers
-    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, 2 * la_try + 2, G);
+  // (lookahead, window) pairs, preferred first; la + window + 1 buffers
+  static const int kOpts[][2] = {{6, 7}, {5, 6}, {4, 5}, {3, 4}, {2, 3}, {1, 2},
+                                 {2, 1}, {1, 1}, {0, 1}};
+  int kw = 1;
+  auto resident = [&](int G, int la_try, int kw_try, int se_try, int *blocks,
+                      moda::WarpSmem *out) {
+    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G);
     *blocks = 0;
     if ((int64_t)L.total > optin) return false;
     if (moda::warp_occupancy(narrow, G, L.total, blocks) != cudaSuccess || *blocks < 1)
@@ -913,26 +906,30 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   // params.block_threads = 32 G prescribes the team size
   const int forced = r0->prm.block_threads / 32;
   for (int gsz = forced > 0 ? forced : std::min(8, nc_max); gsz >= 1 && best_w == 0; --gsz)
-    for (int la_try = la_max; la_try >= 0 && best_w == 0; --la_try) {
+    for (const auto &o : kOpts) {
+      if (o[0] > la_max || best_w != 0) continue;
       int blocks = 0;
       moda::WarpSmem L{};
-      if (resident(gsz, la_try, se_max, &blocks, &L) &&
+      if (resident(gsz, o[0], o[1], se_max, &blocks, &L) &&
           ((int64_t)blocks * sms >= items_total || forced > 0)) {
         best_w = gsz;
         best_blocks = blocks;
-        la = la_try;
+        la = o[0];
+        kw = o[1];
         sm = L;
       }
     }
   for (int attempt = 0; attempt < 2 && best_w == 0; ++attempt) {
-    // throughput: single warps, the most resident
-    for (int la_try = la_max; la_try >= 0; --la_try) {
+    // throughput: single warps, the most resident (then the larger window)
+    for (const auto &o : kOpts) {
+      if (o[0] > la_max) continue;
       int blocks = 0;
       moda::WarpSmem L{};
-      if (resident(1, la_try, se_max, &blocks, &L) && blocks > best_blocks) {
+      if (resident(1, o[0], o[1], se_max, &blocks, &L) && blocks > best_blocks) {
         best_w = 1;
         best_blocks = blocks;
-        la = la_try;
+        la = o[0];
+        kw = o[1];
         sm = L;
       }
     }
@@ -1014,8 +1011,8 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.items = reinterpret_cast<const int2 *>(base + d_bytes);
   L.nitems = (int32_t)items.size();
   L.lookahead = la;
-  L.window = la + 1;
-  L.nbuf = la + L.window + 1;
+  L.window = kw;
+  L.nbuf = la + kw + 1;
   L.team = best_w;
   L.counter = reinterpret_cast<int32_t *>(base + d_bytes + i_bytes);
   L.cache = static_cast<unsigned char *>(scratch->cache);

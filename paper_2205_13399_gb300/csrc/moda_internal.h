@@ -287,8 +287,9 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
   L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
   // accepted counts of the warps by round parity [2][8 positions + 2][8],
-  // the work item, the warps' partial sums of a rebuild [8][2]
-  L.cnt = (uint32_t)o;       o = align_up(o + 640 + 16 + 128, 16);
+  // the work item, the warps' partial sums of a rebuild [8][2], the warps'
+  // first dominated archive slots by round parity [2][8]
+  L.cnt = (uint32_t)o;       o = align_up(o + 640 + 16 + 128 + 64, 16);
   L.team = (uint32_t)o;
   o = 0;
   L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);

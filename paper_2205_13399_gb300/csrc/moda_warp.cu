@@ -145,6 +145,8 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // write the next round's while another still reads this round's)
   int32_t *sCnt = reinterpret_cast<int32_t *>(ts + SL.cnt);
   int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 656);  // [G][2] rebuild sums
+  // explore: each warp's first dominated slot, [round parity][warp]
+  int32_t *sScan = reinterpret_cast<int32_t *>(ts + SL.cnt + 784);
   unsigned char *ws = T.ws0 + (size_t)wt * SL.warp;
   // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 15]
   // = {buffer or -1, slot, issuing iteration} of the copy for target
@@ -372,6 +374,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // needed (rc_stale)
   uint32_t last_wr_t = 0;
   bool rc_stale = false;
+  // this thread wrote records that later bulk copies (async proxy) read and
+  // has not yet ordered them by fence.proxy.async: it does so at the start
+  // of the next round, before any copy of the round is issued (a slot
+  // written in the previous iteration is not copied until a barrier later)
+  bool unfenced = false;
 
   // Rounds of up to KW iterations.  While the replica only jumps, the
   // states of the next iterations are known in advance -- iteration tau
@@ -395,6 +402,10 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         fill(filled + 1u);
         filled += 32u;
       }
+    if (unfenced) {
+      fence_proxy_async_global();
+      unfenced = false;
+    }
     const int K = (KW > 1 && acount > 0 && flip_streak == 0)
                       ? (int)min((uint32_t)KW, I_max - t + 1u)
                       : 1;
@@ -801,9 +812,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // ---- archive update: Alg. 4 (explore) or Alg. 5 (exploit), decided
       // the same way by every warp of the team
       int target = -1;
+      int first_dom = -1;  // explore: this warp's first dominated slot of its stripes
       if (!exploit) {
-        // the first member x dominates is replaced; else x is appended
-        for (int base = 0; base < acount; base += 32) {
+        // the first member x dominates is replaced; else x is appended.
+        // Warp w scans the stripes of 32 slots w, w + G, ...; the team's
+        // first is the least of the warps' (after the barrier below).
+        for (int base = 32 * wt; base < acount; base += 32 * G) {
           const int y = base + lane;
           bool dom = false;
           if (y < acount) {
@@ -812,11 +826,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           }
           const unsigned bal = __ballot_sync(kFull, dom);
           if (bal) {
-            target = base + __ffs(bal) - 1;
+            first_dom = base + __ffs(bal) - 1;
             break;
           }
         }
-        if (target < 0 && acount < s) target = acount++;
+        if (lane == 0) sScan[8 * (int)(rnd & 1u) + wt] = first_dom;
       } else {
         // no member may dominate x; then a random dominated member is
         // replaced (tag 3 draw, slot order), else x is appended
@@ -860,6 +874,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // every warp has read the archive and the accepted lists: they may
       // change now
       sync();
+      if (!exploit) {
+        for (int w = 0; w < G; ++w) {
+          const int f = sScan[8 * (int)(rnd & 1u) + w];
+          if (f >= 0 && (target < 0 || f < target)) target = f;
+        }
+        if (target < 0 && acount < s) target = acount++;
+      }
       sWr[tf & 15u] = target;
       if (target >= 0) last_wr_t = tf;
       if (target >= 0 && leader && lane == 0) {
@@ -950,7 +971,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           }
         }
       }
-      if (cached) fence_proxy_async_global();  // later bulk copies read these records
+      if (cached) unfenced = true;  // fenced before the next bulk copy
       curL = dstL;
       E1 = nE1;
       E2 = nE2;

@@ -272,7 +272,7 @@ __host__ __device__ inline WarpRec warp_rec(int n, int m) {
 struct WarpSmem {
   uint32_t jr;     // buffer stride
   uint32_t buf, mbar, ring, aE, cnt, team;        // team part (bytes: team)
-  uint32_t acc, rows, rc, pf, warp;               // warp part (bytes: warp)
+  uint32_t acc, rows, rc, pf, tbl, warp;          // warp part (bytes: warp)
   int32_t nc_max;
   uint32_t total;  // team + G warps
 };
@@ -296,6 +296,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
   L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
   L.pf = (uint32_t)o;        o = align_up(o + 16 * 16 + 4 * 16, 16);
+  L.tbl = (uint32_t)o;       o = align_up(o + 8 * 4 * 32 * 2, 16);  // staged -ln(u), 2 chunks
   L.warp = (uint32_t)o;
   L.total = L.team + (uint32_t)G * L.warp;
   return L;

@@ -157,6 +157,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
   int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
   unsigned char *rcp = ws + SL.rc;  // this warp's row and column counts of the state
+  // -ln(u) of the acceptance draws of iteration `staged` for this warp's
+  // (at most two) chunks, [chunk][word][lane], copied during the flip
+  // before it: the draws do not depend on the state
+  double *sTbl = reinterpret_cast<double *>(ws + SL.tbl);
+  const bool can_stage = c1 - c0 <= 2;
+  uint32_t staged = 0;
 
   int64_t *gE = R.arch_E + (size_t)row * s * 2;
   uint32_t *gB = R.arch_bits + (size_t)row * s * W;
@@ -416,7 +422,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // the state's and those of targets t .. t + K - 1 + LA.  Lane k
     // handles target issued_to + 1 + k; every warp keeps the same books,
     // the leader warp's lanes start the copies.
-    if (LA > 0) {
+    if (LA > 0 && !(acount > 0 && flip_streak < 3)) {
+      // no copies now: the targets get empty records
+      const int nI = (int)(t + (uint32_t)(K - 1 + LA)) - (int)issued_to;
+      if (lane < nI) sPf[(issued_to + 1u + (uint32_t)lane) & 15u] = make_int4(-1, 0, (int)t, 0);
+      if (nI > 0) issued_to += (uint32_t)nI;
+      __syncwarp();
+    } else if (LA > 0) {
       // targets not yet given a record (none when an earlier, longer
       // window already reached t + K - 1 + LA)
       const int nI = (int)(t + (uint32_t)(K - 1 + LA)) - (int)issued_to;
@@ -504,15 +516,25 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // first every bit of the window against its hi_t: usually none can be
     // accepted, and the window's trials end here
     bool cand = false;
-    for (int k = 0; k < Keff; ++k) {
-      const int64_t hk = ring[(t + (uint32_t)k) % kWarpRing].hi;
-      const uint32_t h32 = hk < 0xFFFFFFFFll ? (uint32_t)hk : 0xFFFFFFFFu;
-      const int sbk = k == 0 ? cur : sPf[(t + (uint32_t)(k - 1)) & 15u].x;
-      const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
-#pragma unroll 4
+    {
+      // lane k holds the buffer and threshold of window position k
+      int sbl = cur;
+      uint32_t hl = 0u;
+      if (lane < Keff) {
+        if (lane > 0) sbl = sPf[(t + (uint32_t)(lane - 1)) & 15u].x;
+        const int64_t hk = ring[(t + (uint32_t)lane) % kWarpRing].hi;
+        hl = hk < 0xFFFFFFFFll ? (uint32_t)hk : 0xFFFFFFFFu;
+      }
       for (int c = c0; c < c1; ++c) {
-        const uint4 a4 = ap[c * 32 + lane];
-        cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+#pragma unroll
+        for (int k = 0; k < kWarpMaxLA + 1; ++k) {
+          const int sbk = __shfl_sync(kFull, sbl, k);
+          const uint32_t h32 = __shfl_sync(kFull, hl, k);
+          if (k < Keff) {
+            const uint4 a4 = reinterpret_cast<const uint4 *>(bA(sbk))[c * 32 + lane];
+            cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+          }
+        }
       }
     }
     if (!__any_sync(kFull, cand)) {
@@ -574,11 +596,20 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           }
           if (__any_sync(kFull, anyneed)) {
             // a in (lo, hi]: the draw decides (R7, R21); group 32c + lane
-            uint32_t d[4] = {(uint32_t)(c * 32 + lane), tk, rep, kTagAccept};
-            philox10(d, k0, k1);
+            if (staged == tk) {
+              cp_async_wait_all();
+              __syncwarp();
+              const double *tv = sTbl + (size_t)(c - c0) * 128;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
+              for (int j = 0; j < 4; ++j)
+                if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, tv[32 * j + lane]);
+            } else {
+              uint32_t d[4] = {(uint32_t)(c * 32 + lane), tk, rep, kTagAccept};
+              philox10(d, k0, k1);
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
+            }
           }
           const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
                          b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
@@ -638,7 +669,8 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             tr[2] = -1 - (int64_t)pr.y;
           }
         if (ns > 0) {
-          for (int k = 0; k + 1 < ns; ++k) freeb |= 1u << sPf[(t + (uint32_t)k) & 15u].x;
+          const int pb = lane + 1 < ns ? sPf[(t + (uint32_t)lane) & 15u].x : -1;
+          freeb |= __reduce_or_sync(kFull, pb >= 0 ? 1u << pb : 0u);  // passed through
           freeb |= 1u << cur;
           const int4 pr = sPf[(t + (uint32_t)(ns - 1)) & 15u];
           cur = pr.x;
@@ -790,6 +822,21 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const int4 *src = reinterpret_cast<const int4 *>(curL + c0 * 128 + lane * 4);
         nx01 = src[0];
         nx23 = src[1];
+      }
+      // the next iteration, tried alone after a flip, will likely need
+      // draws: its -ln(u) values start coming now
+      if (can_stage && tf < I_max) {
+        cp_async_wait_all();  // no earlier copy may still be writing
+        __syncwarp();
+        for (int c = c0; c < c1; ++c) {
+          uint32_t d[4] = {(uint32_t)(c * 32 + lane), tf + 1u, rep, kTagAccept};
+          philox10(d, k0, k1);
+          double *tv = sTbl + (size_t)(c - c0) * 128;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cp_async8(&tv[32 * j + lane], &table[d[j] >> 16]);
+        }
+        cp_async_commit();
+        staged = tf + 1u;
       }
       // the rows into this warp's shared memory now: no registers held
       // across the archive scan
@@ -987,7 +1034,8 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     t = tf + 1u;
     __syncwarp();
   }
-  // no bulk copy may be in flight when the item ends
+  // no copy may be in flight when the item ends
+  cp_async_wait_all();
   for (int b = 0; b < NB; ++b)
     if ((pend >> b) & 1u) retire_buf(b);
   fail = sync_or(fail);

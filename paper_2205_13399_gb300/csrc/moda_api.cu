@@ -1011,6 +1011,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.items = reinterpret_cast<const int2 *>(base + d_bytes);
   L.nitems = (int32_t)items.size();
   L.lookahead = la;
+  L.stage = moda::warp_stage(m_max, best_w) ? 1 : 0;
   L.window = kw;
   L.nbuf = la + kw + 1;
   L.team = best_w;

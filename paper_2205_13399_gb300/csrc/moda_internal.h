@@ -276,6 +276,11 @@ struct WarpSmem {
   int32_t nc_max;
   uint32_t total;  // team + G warps
 };
+// stage: each warp owns at most two chunks of the largest run (then the
+// -ln(u) values of the draws after a flip are staged on chip).
+__host__ __device__ inline bool warp_stage(int m_max, int G) {
+  return (m_max + 127) / 128 <= 2 * G;
+}
 __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G) {
   const WarpRec r = warp_rec(n_max, m_max);
   WarpSmem L;
@@ -296,7 +301,8 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
   L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
   L.pf = (uint32_t)o;        o = align_up(o + 16 * 16 + 4 * 16, 16);
-  L.tbl = (uint32_t)o;       o = align_up(o + 8 * 4 * 32 * 2, 16);  // staged -ln(u), 2 chunks
+  L.tbl = (uint32_t)o;       // staged -ln(u), 2 chunks
+  if (warp_stage(m_max, G)) o = align_up(o + 8 * 4 * 32 * 2, 16);
   L.warp = (uint32_t)o;
   L.total = L.team + (uint32_t)G * L.warp;
   return L;
@@ -339,7 +345,7 @@ struct WarpLaunch {
   int32_t lookahead;         // prefetch distance, 0 .. kWarpMaxLA
   int32_t team;              // G: warps per replica (1 .. 8)
   int32_t window;            // iterations tried together, 1 .. lookahead + 1
-  int32_t pad2;
+  int32_t stage;             // warp_stage() of the launch's largest run
   int32_t *counter;          // next item; zero before the launch
   unsigned char *cache;      // field-cache region of each resident team
   size_t cache_stride;       // bytes per team

@@ -525,16 +525,31 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const int64_t hk = ring[(t + (uint32_t)lane) % kWarpRing].hi;
         hl = hk < 0xFFFFFFFFll ? (uint32_t)hk : 0xFFFFFFFFu;
       }
+      if (c1 - c0 <= 2) {
+        // few chunks: every position's loads of a chunk issue together
+        for (int c = c0; c < c1; ++c) {
 #pragma unroll
-      for (int k = 0; k < kWarpMaxLA + 1; ++k) {
-        const int sbk = __shfl_sync(kFull, sbl, k);
-        const uint32_t h32 = __shfl_sync(kFull, hl, k);
-        if (k < Keff) {
-          const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
+          for (int k = 0; k < kWarpMaxLA + 1; ++k) {
+            const int sbk = __shfl_sync(kFull, sbl, k);
+            const uint32_t h32 = __shfl_sync(kFull, hl, k);
+            if (k < Keff) {
+              const uint4 a4 = reinterpret_cast<const uint4 *>(bA(sbk))[c * 32 + lane];
+              cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kWarpMaxLA + 1; ++k) {
+          const int sbk = __shfl_sync(kFull, sbl, k);
+          const uint32_t h32 = __shfl_sync(kFull, hl, k);
+          if (k < Keff) {
+            const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
 #pragma unroll 4
-          for (int c = c0; c < c1; ++c) {
-            const uint4 a4 = ap[c * 32 + lane];
-            cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+            for (int c = c0; c < c1; ++c) {
+              const uint4 a4 = ap[c * 32 + lane];
+              cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+            }
           }
         }
       }

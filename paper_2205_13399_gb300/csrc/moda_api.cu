@@ -905,20 +905,24 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   };
   // params.block_threads = 32 G prescribes the team size
   const int forced = r0->prm.block_threads / 32;
+  // (a shorter on-chip archive-energy list is traded for buffers)
+  const int se_opts[2] = {se_max, std::min(se_max, 128)};
   for (int gsz = forced > 0 ? forced : std::min(8, nc_max); gsz >= 1 && best_w == 0; --gsz)
-    for (const auto &o : kOpts) {
-      if (o[0] > la_max || best_w != 0) continue;
-      int blocks = 0;
-      moda::WarpSmem L{};
-      if (resident(gsz, o[0], o[1], se_max, &blocks, &L) &&
-          ((int64_t)blocks * sms >= items_total || forced > 0)) {
-        best_w = gsz;
-        best_blocks = blocks;
-        la = o[0];
-        kw = o[1];
-        sm = L;
+    for (const auto &o : kOpts)
+      for (int se_try : se_opts) {
+        if (o[0] > la_max || best_w != 0) continue;
+        int blocks = 0;
+        moda::WarpSmem L{};
+        if (resident(gsz, o[0], o[1], se_try, &blocks, &L) &&
+            ((int64_t)blocks * sms >= items_total || forced > 0)) {
+          best_w = gsz;
+          best_blocks = blocks;
+          la = o[0];
+          kw = o[1];
+          sm = L;
+          se_max = se_try;
+        }
       }
-    }
   for (int attempt = 0; attempt < 2 && best_w == 0; ++attempt) {
     // throughput: single warps, the most resident (then the larger window)
     for (const auto &o : kOpts) {

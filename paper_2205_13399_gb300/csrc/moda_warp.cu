@@ -513,10 +513,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // this warp's chunks, up to its first accepted bit
     int32_t *cntr = sCnt + 80 * (int)(rnd & 1u);  // [k][warp] counts, then [warp] first k
     int first_w = Keff, nl = 0;
-    // first every bit of the window against its hi_t: usually none can be
-    // accepted, and the window's trials end here
-    bool cand = false;
-    {
+    // A run of flips (one iteration, not staged): nearly every chunk
+    // needs draws, so the draws and -ln(u) loads of two chunks are in
+    // flight together, with no branch on the chunk's candidates.
+    const bool hot = Keff == 1 && flip_streak > 0 && staged != t;
+    // Otherwise first every bit of the window against its hi_t: usually
+    // none can be accepted, and the window's trials end here.
+    bool cand = hot;
+    if (!hot) {
       // lane k holds the buffer and threshold of window position k
       int sbl = cur;
       uint32_t hl = 0u;
@@ -554,7 +558,55 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         }
       }
     }
-    if (!__any_sync(kFull, cand)) {
+    if (hot) {
+      const WRing e = ring[t % kWarpRing];
+      const double delta = e.delta;
+      const int64_t lo = e.lo, hi = e.hi;
+      const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
+      const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
+      const unsigned char *rck = rc_stale ? bRC(cur) : rcp;
+      const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(cur));
+      int cnt_w = 0;
+#pragma unroll 2
+      for (int c = c0; c < c1; ++c) {
+        const uint4 a4 = a4p[c * 32 + lane];
+        uint32_t d[4] = {(uint32_t)(c * 32 + lane), t, rep, kTagAccept};
+        philox10(d, k0, k1);
+        double tv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tv[j] = __ldg(&table[d[j] >> 16]);
+        const int p0 = c * 128 + lane * 4;
+        const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+        bool acc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[j] = false;
+          if (p0 + j < m && av[j] <= hi32) {
+            if (NARROW) {
+              // a < 2^32 - 1: the clamped thresholds decide exactly
+              acc[j] = av[j] <= lo32 || (double)av[j] <= __dmul_rn(delta, tv[j]);
+            } else {
+              const int64_t ax =
+                  av[j] == 0xFFFFFFFFu ? exact_penalty(cur, curL, rck, p0 + j) : (int64_t)av[j];
+              acc[j] = ax <= lo || (ax <= hi && (double)ax <= __dmul_rn(delta, tv[j]));
+            }
+          }
+        }
+        const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
+                       b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
+        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+        if (cnt > 0) {
+          if (lane == 0) {
+            sAccW[nl] = make_uint4(b0, b1, b2, b3);
+            sAccC[nl] = c;
+          }
+          ++nl;
+          cnt_w += cnt;
+        }
+      }
+      if (lane == 0) cntr[wt] = cnt_w;
+      if (cnt_w > 0) first_w = 0;
+    } else if (!__any_sync(kFull, cand)) {
       if (lane < Keff) cntr[8 * lane + wt] = 0;
     } else
     for (int k = 0; k < Keff; ++k) {

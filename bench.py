@@ -41,29 +41,38 @@ OPS_PER_BIT_TRIAL = 20
 INT_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM bytes (read + write) of one annealing launch, from one ncu capture
-# of the default workload, valid only for the kernel sources it was taken
-# on (their SHA-256 below).
-KERNEL_TRAFFIC = {"workload": "P25", "sha256": "8b43fbf52741c0322d1dd50fad8f5df8188cfd697740eb69e7b43a41c55d39e3",
-                  "bytes": 10926261248 + 889593344}
+# DRAM bytes (read + write) of one annealing launch of the default workload,
+# from one ncu capture per kernel, valid only for the kernel sources it was
+# taken on (their SHA-256 below).
+KERNEL_FILES = {
+    "anneal_kernel": ("moda_kernel_body.cuh", "moda_kernel.cu", "moda_kernel_special.cu",
+                      "moda_internal.h"),
+    "warp_anneal_kernel": ("moda_warp.cu", "moda_device.cuh", "moda_internal.h"),
+}
+KERNEL_TRAFFIC = {
+    "anneal_kernel": {"workload": "P25", "bytes": None, "sha256": None},
+    "warp_anneal_kernel": {"workload": "P25", "bytes": 670029056 + 1872576768,
+                           "sha256": "e019a21aa55f6135265526b302e976c1109173d01b7bd342f0559b85eeac7adf"},
+}
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("moda_kernel_body.cuh", "moda_kernel.cu", "moda_kernel_special.cu", "moda_internal.h"):
+    for f in KERNEL_FILES[kernel]:
         with open(os.path.join(ROOT, "paper_2205_13399_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def kernel_traffic(workload: str, I_max: int, default_I_max: int):
-    """DRAM bytes per launch when the stored capture matches this kernel and
-    workload, else None."""
-    if (KERNEL_TRAFFIC["bytes"] is None or workload != KERNEL_TRAFFIC["workload"]
-            or I_max != default_I_max or kernel_sources_sha256() != KERNEL_TRAFFIC["sha256"]):
+def kernel_traffic(kernel: str, workload: str, I_max: int, default_I_max: int):
+    """DRAM bytes per launch when the stored capture matches this kernel,
+    its sources and the workload, else None."""
+    rec = KERNEL_TRAFFIC.get(kernel)
+    if (rec is None or rec["bytes"] is None or workload != rec["workload"]
+            or I_max != default_I_max or kernel_sources_sha256(kernel) != rec["sha256"]):
         return None
-    return KERNEL_TRAFFIC["bytes"]
+    return rec["bytes"]
 
 
 def parse_args(argv=None):
@@ -825,8 +834,9 @@ def main(argv=None):
     roofline = roofline_line(ops_per_launch, statistics.mean(kernel_ms) / 1e3,
                              props.multi_processor_count, sm_max_mhz,
                              f"{OPS_PER_BIT_TRIAL} int32 lane-ops per bit-trial")
+    roofline["kernel"] = "anneal_kernel" if args.engine == "block" else "warp_anneal_kernel"
     roofline["traffic"] = kernel_traffic(
-        args.workload, I_max, inputs.WORKLOAD_RUN[args.workload]["I_max"])
+        roofline["kernel"], args.workload, I_max, inputs.WORKLOAD_RUN[args.workload]["I_max"])
     if roofline["traffic"] is not None:
         roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read + write)"
 

@@ -531,17 +531,21 @@ def hv_norm(points, lo, hi):
 
 def run_sbda(args):
     """SB-DA (Alg. 2: eleven scalarised DA runs, one batch launch) against
-    MDA (Alg. 3) on the P25 instance, same replicas and I_max per run: the
-    paper's comparison of the two (Table 3), with both fronts' normalised
-    hypervolume over the union's cost range."""
+    MDA (Alg. 3) on the P25 instance in the paper's setting (Sec. 4.2, 5.1:
+    normalised QUBOs, I_max = 0.25 m^2, delta0 = 1e9, delta_f = 1e4,
+    xi = 0.001, beta = delta0 / I_max), same replicas per run: the paper's
+    comparison of the two (Table 3), with both fronts' normalised
+    hypervolume over the union's cost range.  The same comparison on the
+    integer QUBOs is reported beside it."""
     import torch
     from paper_2205_13399_gb300 import inputs, moda
     dev = torch.device("cuda", torch.cuda.current_device())
     qi = inputs.workload_instance("P25")
     run = dict(inputs.WORKLOAD_RUN["P25"])
-    if args.I_max is not None:
-        run["I_max"] = args.I_max
-    R, I_max = run["replicas"], run["I_max"]
+    m = qi.n * qi.n
+    I_max = args.I_max if args.I_max is not None else m * m // 4
+    R = run["replicas"]
+    sched = dict(delta0=1e9, deltaf=1e4, xi=1e-3)
     inst = moda.Instance(qi.F1, qi.F2, qi.D)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -556,49 +560,60 @@ def run_sbda(args):
         b.synchronize()
         return a.elapsed_time(b), out
 
-    def sbda():
-        return moda.sbda(inst, replicas=R, I_max=I_max, seed=run["seed"], stream=stream)
+    def compare(normalize, steps, warmup):
+        def sbda():
+            return moda.sbda(inst, replicas=R, I_max=I_max, seed=run["seed"],
+                             normalize=normalize, stream=stream, **sched)
 
-    def mda():
-        r = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"], stream=stream)
-        r.wait()
-        return r
+        def mda():
+            r = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"],
+                            normalize=normalize, stream=stream, **sched)
+            r.wait()
+            return r
 
-    for _ in range(args.warmup):
-        sbda()
-        mda().close()
+        for _ in range(warmup):
+            for x in sbda()[0]:
+                x.close()
+            mda().close()
+        s_ms, m_ms = [], []
+        for _ in range(steps):
+            ms, (runs, front_s) = timed(sbda)
+            s_ms.append(ms)
+            ms, r = timed(mda)
+            m_ms.append(ms)
+            front_m = [(p["c1"], p["c2"]) for p in r.read_archive(-1) if p["feasible"]]
+            r.close()
+            for x in runs:
+                x.close()
+        fs = [(p["c1"], p["c2"]) for p in front_s]
+        allp = fs + front_m
+        lo = (min(p[0] for p in allp), min(p[1] for p in allp))
+        hi = (max(p[0] for p in allp), max(p[1] for p in allp))
+        sb, md = statistics.mean(s_ms), statistics.mean(m_ms)
+        return {"normalised": normalize, "sbda_ms": sb, "mda_ms": md,
+                "sbda_over_mda_time": sb / md, "mda_engine": "block" if normalize else "warp",
+                "sbda_front_points": len(fs), "mda_front_points": len(front_m),
+                "hv_sbda": hv_norm(fs, lo, hi), "hv_mda": hv_norm(front_m, lo, hi)}
+
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    s_ms, m_ms = [], []
-    for _ in range(args.steps):
-        ms, (runs, front_s) = timed(sbda)
-        s_ms.append(ms)
-        ms, r = timed(mda)
-        m_ms.append(ms)
-        front_m = [(p["c1"], p["c2"]) for p in r.read_archive(-1) if p["feasible"]]
-        r.close()
-        for x in runs:
-            x.close()
+    main = compare(True, args.steps, args.warmup)
+    integer = compare(False, 1, 1)
     clk = clocks.stop()
-    fs = [(p["c1"], p["c2"]) for p in front_s]
-    allp = fs + front_m
-    lo = (min(p[0] for p in allp), min(p[1] for p in allp))
-    hi = (max(p[0] for p in allp), max(p[1] for p in allp))
-    sb = statistics.mean(s_ms)
+    sb = main["sbda_ms"]
     value = 11 * R * I_max / (sb / 1e3)
     line = {
         "metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sb,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
         "data": "synthetic",
         "config": {"workload": f"SBDA: SB-DA (11 weights, Alg. 2) vs MDA (Alg. 3) on P25, "
-                               f"{R} replicas, I_max={I_max} per run",
-                   "weights": 11, "replicas": R, "I_max": I_max,
+                               f"normalised QUBOs, {R} replicas, I_max={I_max} per run",
+                   "weights": 11, "replicas": R, "I_max": I_max, **sched,
+                   "beta": "delta0 / I_max",
                    "l2": "flushed before each timed solve (512 MiB write)"},
-        "vs_mda": {"sbda_ms": sb, "mda_ms": statistics.mean(m_ms),
-                   "sbda_over_mda_time": sb / statistics.mean(m_ms),
-                   "sbda_front_points": len(fs), "mda_front_points": len(front_m),
-                   "hv_sbda": hv_norm(fs, lo, hi), "hv_mda": hv_norm(front_m, lo, hi)},
+        "vs_mda": main,
+        "integer_qubos": integer,
         "e2e": {"value": value, "unit": "replica-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": None, "note": "front read-back inside the timed call"},
         "gpu_launches": 12 * args.steps, "clocks": clk,

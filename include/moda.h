@@ -147,10 +147,10 @@ typedef struct {
                               archive escape only, without normalize,
                               snapshot_every or fast_forward;
                               MODA_EUNSUPPORTED otherwise).  Its field cache
-                              holds min(s, 1024) slots per resident warp by
-                              default (field_cache = 1: all s slots; 2:
-                              none); a jump to a slot without records
-                              rebuilds its fields.  prefetch k in 1..7 copies
+                              holds the records of the first cache_slots
+                              archive slots per resident team (field_cache
+                              = 1: all s slots; 2: none); a jump to a slot
+                              without records rebuilds its fields.  prefetch k in 1..7 copies
                               a jump's target k - 1 iterations ahead (0:
                               auto: up to 6 iterations, as shared memory
                               allows).  A team of G warps (1 to
@@ -166,6 +166,14 @@ typedef struct {
                               trials are discarded).
                             0 auto: warp when the options allow it and
                               block_threads is 0, else block. */
+  int32_t cache_slots;   /* warp engine, field_cache = 0: archive slots with
+                            field-cache records per team; 0: min(s, 1024),
+                            k > 0: min(s, k), fewer where the launch's caches
+                            would not fit the memory budget.  A jump to a
+                            slot beyond it rebuilds the member's fields (as
+                            slow as hundreds of jumps), so the cache should
+                            cover the archive sizes runs reach.  Results are
+                            identical for every value. */
 } moda_params;
 
 /* One archive member as returned by moda_read_archive. */
@@ -229,7 +237,8 @@ moda_status moda_wait(moda_run run, int64_t timeout_ms);
  *                       jumps served by a prefetched field-cache record,
  *                       jumps that read the record directly, iterations
  *                       settled without being executed (params.fast_forward),
- *                       and 0
+ *                       and jumps that rebuilt the fields of a slot without
+ *                       records (warp engine; 0 in the block engine)
  * Any pointer may be NULL.  MODA_EBUSY while the run executes. */
 moda_status moda_read_replica(moda_run run, int32_t r, int32_t *count,
                               int64_t *E, uint32_t *bits, uint32_t *x,

@@ -82,6 +82,7 @@ class _DAParams(ctypes.Structure):
         ("xi", ctypes.c_double),
         ("beta", ctypes.c_int64),
         ("seed", ctypes.c_uint64),
+        ("normalize", ctypes.c_int),
     ]
 
 
@@ -130,6 +131,8 @@ def _load():
         lib.oracle_squbo_free.argtypes = [P]
         lib.oracle_squbo_w.restype = i64
         lib.oracle_squbo_w.argtypes = [P]
+        lib.oracle_squbo_scale.restype = ctypes.c_double
+        lib.oracle_squbo_scale.argtypes = [P]
         lib.oracle_squbo_energy.restype = i64
         lib.oracle_squbo_energy.argtypes = [P, P]
         lib.oracle_da_run_many.restype = ctypes.c_int
@@ -344,14 +347,20 @@ def run(inst: Instance, *, I_max: int, replicas, seed: int = 0, accept: str = "s
 
 def da_run(inst: Instance, gnum: int, gden: int, *, I_max: int, replicas, seed: int = 0,
            delta0: float = 1e9, deltaf: float = 1e4, xi: float = 1e-3,
-           beta: int | None = None, threads: int | None = None) -> dict:
+           beta: int | None = None, threads: int | None = None,
+           normalize: bool = False) -> dict:
     """Alg. 1 (DA) on the scalarised QUBO of Alg. 2 for gamma = gnum / gden,
     in integers scaled by gden: Q = gnum R + (gden - gnum) S + alpha G with
     alpha from Eq. vermap on that cost, temperatures delta0 * gden and
     deltaf * gden, offset rate beta * gden (beta defaults to delta0 / I_max).
-    Returns ``w`` and per replica ``best_x`` [R, m], ``best_E`` [R],
-    ``x`` [R, m], ``E_final`` [R] and ``stats`` [R, 2] (flips, offset
-    raises)."""
+    ``normalize``: the QUBO normalised as in Sec. 4.2 (its cost part's
+    largest coefficient set to 2^23, ``scale`` = 2^23 / that coefficient):
+    the acceptance test sees scale * Delta E - E_off in IEEE double, and the
+    temperatures and offset rate are taken as given, in the normalised
+    QUBO's units (the gden factor cancels in the scale).
+    Returns ``w``, ``scale`` and per replica ``best_x`` [R, m], ``best_E``
+    [R], ``x`` [R, m], ``E_final`` [R] and ``stats`` [R, 2] (flips, offset
+    raises); energies are the unnormalised integers."""
     lib = _load()
     if isinstance(replicas, (int, np.integer)):
         replicas = range(int(replicas))
@@ -363,9 +372,10 @@ def da_run(inst: Instance, gnum: int, gden: int, *, I_max: int, replicas, seed: 
     if not q:
         raise ValueError("bad scalarisation weight")
     try:
-        prm = _DAParams(int(I_max), float(delta0) * gden, float(deltaf) * gden, float(xi),
-                        int(beta) * gden, int(seed) & 0xFFFFFFFFFFFFFFFF)
-        out = {"w": int(lib.oracle_squbo_w(q)),
+        f = 1 if normalize else gden
+        prm = _DAParams(int(I_max), float(delta0) * f, float(deltaf) * f, float(xi),
+                        int(beta) * f, int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(normalize)))
+        out = {"w": int(lib.oracle_squbo_w(q)), "scale": float(lib.oracle_squbo_scale(q)),
                "best_x": np.zeros((R, m), dtype=np.uint8),
                "best_E": np.zeros(R, dtype=np.int64),
                "x": np.zeros((R, m), dtype=np.uint8),

@@ -721,6 +721,7 @@ typedef struct oracle_squbo {
   int n;
   int64_t m;
   int64_t w;
+  int64_t cmax;    /* largest coefficient of C, p <= q (Sec. 4.2) */
   int64_t offset;  /* alpha p_g */
   int64_t *Q;      /* upper triangular */
   int64_t *P;      /* symmetric, diagonal = Q_pp (Eq. cale) */
@@ -751,6 +752,10 @@ oracle_squbo *oracle_sbda_qubo(const oracle_instance *inst, int64_t gnum,
   }
   for (int64_t e = 0; e < m * m; ++e)
     C[e] = gnum * inst->C[0][e] + (gden - gnum) * inst->C[1][e];
+  q->cmax = 0;
+  for (int64_t p = 0; p < m; ++p)
+    for (int64_t r = p; r < m; ++r)
+      if (C[p * m + r] > q->cmax) q->cmax = C[p * m + r];
   q->w = oracle_penalty_w(m, C);
   for (int64_t e = 0; e < m * m; ++e) q->Q[e] = C[e] + q->w * (inst->G[e] / 2);
   q->offset = q->w * (inst->pg / 2);
@@ -763,6 +768,12 @@ oracle_squbo *oracle_sbda_qubo(const oracle_instance *inst, int64_t gnum,
 
 int64_t oracle_squbo_w(const oracle_squbo *q) { return q->w; }
 
+/* Sec. 4.2 for the scalarised QUBO: s = 2^23 / (largest coefficient of its
+ * cost part C), 1 if that is 0.  The gden factor of C cancels in s C. */
+double oracle_squbo_scale(const oracle_squbo *q) {
+  return q->cmax > 0 ? 8388608.0 / (double)q->cmax : 1.0;
+}
+
 /* E(x) = x^T Q x + alpha p_g */
 int64_t oracle_squbo_energy(const oracle_squbo *q, const uint8_t *x) {
   return oracle_quadratic(q->m, q->Q, x) + q->offset;
@@ -770,9 +781,13 @@ int64_t oracle_squbo_energy(const oracle_squbo *q, const uint8_t *x) {
 
 typedef struct oracle_da_params {
   int64_t I_max;
-  double delta0, deltaf, xi;  /* already scaled by gden */
-  int64_t beta;               /* already scaled by gden */
+  double delta0, deltaf, xi;  /* scaled by gden unless normalize */
+  int64_t beta;               /* scaled by gden unless normalize */
   uint64_t seed;
+  int normalize;              /* 1: the acceptance test sees s Delta E - E_off
+                                 in IEEE double (s = oracle_squbo_scale), the
+                                 temperatures and the offset in the units of
+                                 the normalised QUBO */
 } oracle_da_params;
 
 /* Alg. 1 for one replica with the draws of Alg. 3 (same Philox counters).
@@ -814,6 +829,7 @@ int oracle_da_run(const oracle_squbo *q, const oracle_da_params *prm,
   int have_best = 0;
   double delta = prm->delta0;
   const double factor = 1.0 - prm->xi;
+  const double scale = oracle_squbo_scale(q);
   int64_t Eoff = 0;
   for (int64_t it = 1; it <= prm->I_max; ++it) {
     const uint32_t step = (uint32_t)it;
@@ -824,11 +840,19 @@ int oracle_da_run(const oracle_squbo *q, const oracle_da_params *prm,
     /* propose every flip with Delta E_i - E_offset (Eq. paccepts) */
     int64_t count = 0;
     for (int64_t p = 0; p < m; ++p) {
-      int64_t e = dE[p] - Eoff;
-      int64_t a = e > 0 ? e : 0;
       uint32_t w = draw_word(prm->seed, (uint32_t)(p >> 2), step, replica, TAG_ACCEPT,
                              (int)(p & 3));
-      if ((double)a <= delta * T[w >> 16]) accepted[count++] = p;
+      if (!prm->normalize) {
+        int64_t e = dE[p] - Eoff;
+        int64_t a = e > 0 ? e : 0;
+        if ((double)a <= delta * T[w >> 16]) accepted[count++] = p;
+      } else {
+        /* normalised QUBO: s Delta E_i - E_offset, in doubles */
+        double e = scale * (double)dE[p];
+        e = e - (double)Eoff;
+        double a = e > 0 ? e : 0.0;
+        if (a <= delta * T[w >> 16]) accepted[count++] = p;
+      }
     }
     if (count > 0) {
       uint32_t u = draw_word(prm->seed, 0, step, replica, TAG_SELECT, 0);

@@ -301,8 +301,24 @@ bool uses_warp(const moda_params *p) {
 // batches and the server (the warp engine whenever the options allow it).
 moda_params resolve_plain(moda_instance, const moda_params *p) { return *p; }
 
-// Archive slots with field-cache records per resident warp by default.
+// Archive slots with field-cache records per resident team by default.
+// A jump to a slot without records rebuilds its fields (O(n^3) by the
+// team), which costs as much as hundreds of jumps: on the n = 75 workload
+// (archives of up to 528 members) 512 slots took 695 ms and 256 slots
+// 7.3 s against 353 ms with 1,024, so the default covers the archives that
+// runs reach rather than a byte budget.
 constexpr int kWarpCacheSlots = 1024;
+
+// Field-cache slots per team of a warp-engine run before the launch's
+// memory budget is applied: all s (field_cache = 1), none (2), min(s,
+// cache_slots) when given, else min(s, kWarpCacheSlots).
+int warp_slots(moda_instance inst, const moda_params &p) {
+  const int s = p.archive_size > 0 ? p.archive_size : inst->m;
+  if (p.field_cache == 2) return 0;
+  if (p.field_cache == 1) return s;
+  if (p.cache_slots > 0) return std::min(s, p.cache_slots);
+  return std::min(s, kWarpCacheSlots);
+}
 // Archive energies kept in shared memory per warp, at most.
 constexpr int kWarpSmemEnergies = 512;
 
@@ -485,6 +501,7 @@ moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStrea
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kWarpMaxLA + 1)
     return fail(MODA_EINVAL, "prefetch must be in [0, 7] for the warp engine");
+  if (p->cache_slots < 0) return fail(MODA_EINVAL, "cache_slots must be >= 0");
   if (p->block_threads < 0 || p->block_threads % 32 || p->block_threads > 256)
     return fail(MODA_EINVAL, "warp engine: block_threads must be 32 G, G in 1..8 (0: auto)");
   cudaSetDevice(inst->device);
@@ -827,10 +844,8 @@ size_t run_bytes(moda_instance inst, const moda_params &p, bool cache) {
              R * sizeof(int32_t) + R * W * sizeof(uint32_t) + R * 2 * sizeof(int64_t) +
              R * moda::kStats * sizeof(int64_t) + sizeof(int32_t);
   if (cache && uses_warp(&p)) {
-    // the field caches of up to R resident warps
-    const int cs = p.field_cache == 2 ? 0 : p.field_cache == 1 ? (int)s
-                                                                : std::min((int)s, kWarpCacheSlots);
-    b += R * moda::align_up(moda::warp_cache_bytes(inst->n, (int)m, cs), 256);
+    // the field caches of up to R resident teams
+    b += R * moda::align_up(moda::warp_cache_bytes(inst->n, (int)m, warp_slots(inst, p)), 256);
   } else if (cache && p.escape == MODA_ESC_ARCHIVE && p.field_cache != 2) {
     b += R * s * moda::slot_layout((int)m, narrow).bytes;
   }
@@ -943,8 +958,8 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   const int64_t resident_teams = (int64_t)best_blocks * sms;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_teams, items_total));
   const size_t warps = (size_t)grid;  // teams, one per block
-  // Field-cache slots per run: all (field_cache = 1), none (2), or up to
-  // kWarpCacheSlots, fewer if the launch's caches would exceed the budget.
+  // Field-cache slots per run (warp_slots), fewer where field_cache = 0 and
+  // the launch's caches would exceed the budget.
   std::vector<int> cs(idx.size());
   auto stride_of = [&]() {
     size_t st = 0;
@@ -956,8 +971,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   };
   for (size_t k = 0; k < idx.size(); ++k) {
     const moda_run r = runs[idx[k]];
-    const int fc = r->prm.field_cache;
-    cs[k] = fc == 2 ? 0 : fc == 1 ? r->s : std::min(r->s, kWarpCacheSlots);
+    cs[k] = warp_slots(r->inst, r->prm);
   }
   size_t stride = stride_of();
   while (warps * stride > cache_budget) {

@@ -374,7 +374,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // free buffers (bit b), copies in flight (bit b)
   uint32_t freeb = ((1u << NB) - 1u) & ~1u, pend = 0u;
   int flip_streak = 0;
-  uint32_t nflip = 0, njump = 0, nempty = 0, npref = 0, ndirect = 0;
+  uint32_t nflip = 0, njump = 0, nempty = 0, npref = 0, ndirect = 0, nrebuild = 0;
   // the last iteration that wrote an archive slot; after a jump to a
   // cached slot this warp's counts are refreshed from the buffer only when
   // needed (rc_stale)
@@ -782,6 +782,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
               sync();
               int64_t t1, t2, gp;
               rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
+              ++nrebuild;
             }
             ++ndirect;
           }
@@ -1127,7 +1128,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     st[4] = npref;
     st[5] = ndirect;
     st[6] = 0;
-    st[7] = 0;
+    st[7] = nrebuild;
   }
   sync();  // the team's shared memory is reused by the next item
   return true;

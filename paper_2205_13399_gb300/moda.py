@@ -73,6 +73,7 @@ class Params(ctypes.Structure):
         ("snapshot_every", ctypes.c_int32),
         ("fast_forward", ctypes.c_int32),
         ("engine", ctypes.c_int32),
+        ("cache_slots", ctypes.c_int32),
     ]
 
 
@@ -353,14 +354,16 @@ def make_params(*, replicas: int, I_max: int, seed: int = 0, accept: str = "stri
                 archive_size: int = 0, replica_base: int = 0, block_threads: int = 0,
                 trace: bool = False, field_cache: str = "auto", prefetch: int = 0,
                 normalize: bool = False, snapshot_every: int = 0,
-                fast_forward: bool = False, engine: str = "auto") -> Params:
+                fast_forward: bool = False, engine: str = "auto",
+                cache_slots: int = 0) -> Params:
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
     return Params(int(replicas), int(replica_base), int(I_max), float(delta0), float(deltaf),
                   float(xi), int(beta), int(archive_size), ACCEPT[accept], ARCHIVE[archive],
                   ESCAPE[escape], int(seed) & 0xFFFFFFFFFFFFFFFF, int(block_threads),
                   int(bool(trace)), FIELD_CACHE[field_cache], int(prefetch), int(bool(normalize)),
-                  int(snapshot_every), int(bool(fast_forward)), ENGINE[engine])
+                  int(snapshot_every), int(bool(fast_forward)), ENGINE[engine],
+                  int(cache_slots))
 
 
 def anneal_noalloc(F1, F2, D, outputs: dict, params: Params | None = None, stream=None,
@@ -490,20 +493,28 @@ def probe_smem_peak(iters: int = 20000, stream=None) -> tuple[float, float]:
 
 def sbda(inst: Instance, *, replicas: int, I_max: int, seed: int = 0, gamma_den: int = 10,
          gammas=None, delta0: float = 1e9, deltaf: float = 1e4, xi: float = 1e-3,
-         beta: int | None = None, block_threads: int = 0, stream=None):
+         beta: int | None = None, block_threads: int = 0, normalize: bool = False,
+         stream=None):
     """SB-DA (Alg. 2): one DA run (Alg. 1) per weight gamma = g / gamma_den,
     g in ``gammas`` (default 0..gamma_den), all enqueued as one
     ``moda_anneal_batch`` launch, then the merged non-dominated feasible
-    front (``moda_sbda_front``).  Returns (runs, front); front points are
-    dicts with c1, c2, weight (index into gammas), replica and perm."""
+    front (``moda_sbda_front``).  The scalarised instances are integers
+    scaled by gamma_den, so the temperatures and the offset rate are scaled
+    by it too; with ``normalize`` each scalarised QUBO is normalised as in
+    Sec. 4.2 (params.normalize: the acceptance test sees s Delta E in IEEE
+    double, s = 2^23 / its largest cost coefficient, in which gamma_den
+    cancels) and they are taken as given.  Returns (runs, front); front
+    points are dicts with c1, c2, weight (index into gammas), replica and
+    perm."""
     gammas = list(range(gamma_den + 1)) if gammas is None else list(gammas)
     if beta is None:
         beta = int(round(delta0 / I_max)) if I_max > 0 else 0
+    f = 1 if normalize else gamma_den
     insts = [inst.scalarize(g, gamma_den) for g in gammas]
     params = [make_params(replicas=replicas, I_max=I_max, seed=seed, escape="offset",
-                          archive_size=1, delta0=delta0 * gamma_den,
-                          deltaf=deltaf * gamma_den, xi=xi, beta=beta * gamma_den,
-                          block_threads=block_threads) for _ in gammas]
+                          archive_size=1, delta0=delta0 * f, deltaf=deltaf * f, xi=xi,
+                          beta=beta * f, block_threads=block_threads,
+                          normalize=normalize) for _ in gammas]
     runs = anneal_batch(insts, params, stream=stream)
     for r in runs:
         r.wait()

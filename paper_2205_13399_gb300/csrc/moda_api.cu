@@ -44,6 +44,7 @@ moda_status cuda_fail(cudaError_t e, const char *what) {
 // Per-device constant data: the -ln(u) table and schedules.
 struct DeviceData {
   double *table = nullptr;
+  float *tablef = nullptr;  // the same entries rounded to float (warp engine)
   double tmin = 0, tmax = 0;
   struct Sched {
     double *delta = nullptr;
@@ -77,7 +78,19 @@ moda_status device_table(int dev, DeviceData **out) {
       cudaFree(d);
       return cuda_fail(e, "upload -ln(u) table");
     }
+    std::vector<float> Tf(T.size());
+    for (size_t i = 0; i < T.size(); ++i) Tf[i] = static_cast<float>(T[i]);
+    float *f = nullptr;
+    e = cudaMalloc(&f, sizeof(float) * Tf.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(f, Tf.data(), sizeof(float) * Tf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      if (f) cudaFree(f);
+      return cuda_fail(e, "upload -ln(u) table");
+    }
     dd.table = d;
+    dd.tablef = f;
     dd.tmax = T.front();
     dd.tmin = T.back();
   }
@@ -570,6 +583,7 @@ moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStrea
   w.sch_lo = sch.lo;
   w.sch_hi = sch.hi;
   w.table = dd->table;
+  w.tablef = dd->tablef;
   w.Fs1 = inst->dFs1;
   w.Fs2 = inst->dFs2;
   w.D = inst->dD;
@@ -955,6 +969,20 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
     if (best_w == 0) se_max = std::min(se_max, 64);
   }
   if (best_w == 0) return fail(MODA_EUNSUPPORTED, "warp engine: shared memory need exceeds the device");
+  // The fields of a flip's state on chip too, where that keeps the
+  // residency (as many teams, or still every replica, per launch).
+  bool sfields = false;
+  {
+    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true);
+    int blocks = 0;
+    if ((int64_t)L.total <= optin &&
+        moda::warp_occupancy(narrow, best_w, L.total, &blocks) == cudaSuccess &&
+        (blocks >= best_blocks || (int64_t)blocks * sms >= items_total)) {
+      sfields = true;
+      best_blocks = blocks;
+      sm = L;
+    }
+  }
   const int64_t resident_teams = (int64_t)best_blocks * sms;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_teams, items_total));
   const size_t warps = (size_t)grid;  // teams, one per block
@@ -1030,6 +1058,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.nitems = (int32_t)items.size();
   L.lookahead = la;
   L.stage = moda::warp_stage(m_max, best_w) ? 1 : 0;
+  L.sfields = sfields ? 1 : 0;
   L.window = kw;
   L.nbuf = la + kw + 1;
   L.team = best_w;

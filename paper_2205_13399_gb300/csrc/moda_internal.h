@@ -271,7 +271,7 @@ __host__ __device__ inline WarpRec warp_rec(int n, int m) {
 // flip and its copy of the row and column counts.
 struct WarpSmem {
   uint32_t jr;     // buffer stride
-  uint32_t buf, mbar, ring, aE, cnt, team;        // team part (bytes: team)
+  uint32_t buf, mbar, ring, aE, cnt, fld, team;   // team part (bytes: team)
   uint32_t acc, rows, rc, pf, tbl, warp;          // warp part (bytes: warp)
   int32_t nc_max;
   uint32_t total;  // team + G warps
@@ -281,7 +281,10 @@ struct WarpSmem {
 __host__ __device__ inline bool warp_stage(int m_max, int G) {
   return (m_max + 127) / 128 <= 2 * G;
 }
-__host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G) {
+// sfields: the team part also holds the fields of the state a flip
+// reached (8 bytes per bit), so that flips following flips read them on chip.
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G,
+                                              bool sfields = false) {
   const WarpRec r = warp_rec(n_max, m_max);
   WarpSmem L;
   size_t o = 0;
@@ -295,6 +298,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, 
   // the work item, the warps' partial sums of a rebuild [8][2], the warps'
   // first dominated archive slots by round parity [2][8]
   L.cnt = (uint32_t)o;       o = align_up(o + 640 + 16 + 128 + 64, 16);
+  L.fld = (uint32_t)o;       if (sfields) o = align_up(o + 8 * (size_t)r.mp, 16);
   L.team = (uint32_t)o;
   o = 0;
   L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);
@@ -325,6 +329,7 @@ struct WarpRun {
   const double *sch_delta;
   const int64_t *sch_lo, *sch_hi;
   const double *table;
+  const float *tablef;       // table rounded to float: the FP32 prefilter
   const int32_t *Fs1, *Fs2, *D;
   int64_t *arch_E;
   uint32_t *arch_bits;
@@ -346,6 +351,7 @@ struct WarpLaunch {
   int32_t team;              // G: warps per replica (1 .. 8)
   int32_t window;            // iterations tried together, 1 .. lookahead + 1
   int32_t stage;             // warp_stage() of the launch's largest run
+  int32_t sfields;           // fields of a flip's state in shared memory (sm.fld)
   int32_t *counter;          // next item; zero before the launch
   unsigned char *cache;      // field-cache region of each resident team
   size_t cache_stride;       // bytes per team

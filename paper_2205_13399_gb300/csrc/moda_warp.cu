@@ -49,9 +49,26 @@ namespace {
 struct WRing {
   double delta;
   int64_t lo, hi;
-  uint32_t sel, rst, exp, pad;
+  uint32_t sel, rst, exp;
+  float deltaf;  // fl32(delta), for the FP32 prefilter of accept_draw
 };
 static_assert(sizeof(WRing) == 40, "ring entry layout");
+
+// The acceptance test of a bit whose penalty a (an integer >= 0) lies in
+// (lo_t, hi_t] is a <= fl(delta T) (R7).  This part's FP64 rate is low, so
+// it is first decided in FP32 where that is exact: with df = fl32(delta),
+// Tf = fl32(T) and pf = fl32(df Tf), pf lies within (1 +- 2^-24)^3 of
+// delta T, fl(delta T) within 2^-53 of it, and af = fl32(a) within 2^-24 of
+// a.  Hence af <= fl32(pf (1 - 2^-20)) implies a <= (1 - 11 2^-24)
+// fl(delta T) (accept, 1), and af >= fl32(pf (1 + 2^-20)) implies
+// a >= (1 + 11 2^-24) fl(delta T) (reject, 0).  Otherwise (-1, a within
+// about 2^-20 of the product, rare) the caller takes the double test.
+__device__ __forceinline__ int prefilter(float af, float df, float Tf) {
+  const float pf = __fmul_rn(df, Tf);
+  if (af <= __fmul_rn(pf, 1.0f - 0x1p-20f)) return 1;
+  if (af >= __fmul_rn(pf, 1.0f + 0x1p-20f)) return 0;
+  return -1;
+}
 
 // Named barrier `id` (1 .. 15) of `threads` threads; returns whether `v`
 // held in any of them.
@@ -124,6 +141,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   const int LA = Lc.lookahead, NB = Lc.nbuf;
   const WarpSmem &SL = Lc.sm;
   const double *const table = R.table;
+  const float *const tablef = R.tablef;
   int64_t *const trace = R.trace;
   const int team_threads = 32 * G;
   auto sync = [&]() {
@@ -147,6 +165,10 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 656);  // [G][2] rebuild sums
   // explore: each warp's first dominated slot, [round parity][warp]
   int32_t *sScan = reinterpret_cast<int32_t *>(ts + SL.cnt + 784);
+  // the fields of the state the last flip reached, while Lc.sfields: flips
+  // that follow flips read them here rather than from global memory
+  int2 *const sF = reinterpret_cast<int2 *>(ts + SL.fld);
+  const bool use_sf = Lc.sfields != 0;
   unsigned char *ws = T.ws0 + (size_t)wt * SL.warp;
   // this warp's prefetch bookkeeping (the same in every warp): sPf[tt & 15]
   // = {buffer or -1, slot, issuing iteration} of the copy for target
@@ -157,10 +179,10 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
   int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
   unsigned char *rcp = ws + SL.rc;  // this warp's row and column counts of the state
-  // -ln(u) of the acceptance draws of iteration `staged` for this warp's
-  // (at most two) chunks, [chunk][word][lane], copied during the flip
+  // fl32(-ln u) of the acceptance draws of iteration `staged` for this
+  // warp's (at most two) chunks, [chunk][lane][word], copied during the flip
   // before it: the draws do not depend on the state
-  double *sTbl = reinterpret_cast<double *>(ws + SL.tbl);
+  float *sTbl = reinterpret_cast<float *>(ws + SL.tbl);
   const bool can_stage = Lc.stage != 0 && c1 - c0 <= 2;
   uint32_t staged = 0;
 
@@ -190,6 +212,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     const uint32_t sn = (q <= nsched ? q : nsched) - 1u;
     WRing e;
     e.delta = R.sch_delta[sn];
+    e.deltaf = __double2float_rn(e.delta);
     e.lo = R.sch_lo[sn];
     e.hi = R.sch_hi[sn];
     uint32_t c[4] = {0u, q, rep, kTagSelect};
@@ -204,7 +227,6 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       philox10(x, k0, k1);
       e.exp = x[0];
     }
-    e.pad = 0u;
     ring[q % kWarpRing] = e;
   };
 
@@ -517,10 +539,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // needs draws, so the draws and -ln(u) loads of two chunks are in
     // flight together, with no branch on the chunk's candidates.
     const bool hot = Keff == 1 && flip_streak > 0 && staged != t;
+    // The iteration after a flip whose -ln(u) values were staged (it is
+    // tried alone): the same, from the staged values.
+    const bool hot_st = staged == t;
     // Otherwise first every bit of the window against its hi_t: usually
     // none can be accepted, and the window's trials end here.
-    bool cand = hot;
-    if (!hot) {
+    bool cand = hot || hot_st;
+    if (!cand) {
       // lane k holds the buffer and threshold of window position k
       int sbl = cur;
       uint32_t hl = 0u;
@@ -561,6 +586,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     if (hot) {
       const WRing e = ring[t % kWarpRing];
       const double delta = e.delta;
+      const float df = e.deltaf;
       const int64_t lo = e.lo, hi = e.hi;
       const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
       const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
@@ -572,9 +598,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const uint4 a4 = a4p[c * 32 + lane];
         uint32_t d[4] = {(uint32_t)(c * 32 + lane), t, rep, kTagAccept};
         philox10(d, k0, k1);
-        double tv[4];
+        float tv[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) tv[j] = __ldg(&table[d[j] >> 16]);
+        for (int j = 0; j < 4; ++j) tv[j] = __ldg(&tablef[d[j] >> 16]);
         const int p0 = c * 128 + lane * 4;
         const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
         bool acc[4];
@@ -584,13 +610,78 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           if (p0 + j < m && av[j] <= hi32) {
             if (NARROW) {
               // a < 2^32 - 1: the clamped thresholds decide exactly
-              acc[j] = av[j] <= lo32 || (double)av[j] <= __dmul_rn(delta, tv[j]);
+              const int r = av[j] <= lo32 ? 1 : prefilter(__uint2float_rn(av[j]), df, tv[j]);
+              acc[j] = r > 0 ||
+                       (r < 0 && (double)av[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16])));
             } else {
               const int64_t ax =
                   av[j] == 0xFFFFFFFFu ? exact_penalty(cur, curL, rck, p0 + j) : (int64_t)av[j];
-              acc[j] = ax <= lo || (ax <= hi && (double)ax <= __dmul_rn(delta, tv[j]));
+              const int r = ax <= lo ? 1 : ax > hi ? 0 : prefilter(__ll2float_rn(ax), df, tv[j]);
+              acc[j] = r > 0 || (r < 0 && (double)ax <= __dmul_rn(delta, __ldg(&table[d[j] >> 16])));
             }
           }
+        }
+        const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
+                       b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
+        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+        if (cnt > 0) {
+          if (lane == 0) {
+            sAccW[nl] = make_uint4(b0, b1, b2, b3);
+            sAccC[nl] = c;
+          }
+          ++nl;
+          cnt_w += cnt;
+        }
+      }
+      if (lane == 0) cntr[wt] = cnt_w;
+      if (cnt_w > 0) first_w = 0;
+    } else if (hot_st) {
+      const WRing e = ring[t % kWarpRing];
+      const double delta = e.delta;
+      const float df = e.deltaf;
+      const int64_t lo = e.lo, hi = e.hi;
+      const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
+      const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
+      const unsigned char *rck = rc_stale ? bRC(cur) : rcp;
+      const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(cur));
+      const float4 *t4p = reinterpret_cast<const float4 *>(sTbl);
+      cp_async_wait_all();  // the staged values (copied during the flip)
+      __syncwarp();
+      int cnt_w = 0;
+      for (int c = c0; c < c1; ++c) {
+        const uint4 a4 = a4p[c * 32 + lane];
+        const float4 t4 = t4p[(c - c0) * 32 + lane];
+        const int p0 = c * 128 + lane * 4;
+        const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+        bool acc[4], amb[4];
+        int64_t ai[4];
+        bool anyamb = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[j] = false;
+          amb[j] = false;
+          ai[j] = (int64_t)av[j];
+          if (p0 + j < m && av[j] <= hi32) {
+            int r;
+            if (NARROW) {
+              // a < 2^32 - 1: the clamped thresholds decide exactly
+              r = av[j] <= lo32 ? 1 : prefilter(__uint2float_rn(av[j]), df, tv[j]);
+            } else {
+              if (av[j] == 0xFFFFFFFFu) ai[j] = exact_penalty(cur, curL, rck, p0 + j);
+              r = ai[j] <= lo ? 1 : ai[j] > hi ? 0 : prefilter(__ll2float_rn(ai[j]), df, tv[j]);
+            }
+            acc[j] = r > 0;
+            amb[j] = r < 0;
+            anyamb |= amb[j];
+          }
+        }
+        if (__any_sync(kFull, anyamb)) {  // the double test near the boundary
+          uint32_t d[4] = {(uint32_t)(c * 32 + lane), t, rep, kTagAccept};
+          philox10(d, k0, k1);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (amb[j]) acc[j] = (double)ai[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
         }
         const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
                        b2 = __ballot_sync(kFull, acc[2]), b3 = __ballot_sync(kFull, acc[3]);
@@ -613,6 +704,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const uint32_t tk = t + (uint32_t)k;
       const WRing e = ring[tk % kWarpRing];
       const double delta = e.delta;
+      const float df = e.deltaf;
       const int64_t lo = e.lo, hi = e.hi;
       const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
       const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
@@ -636,13 +728,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           const int p0 = c * 128 + lane * 4;
           const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
           bool acc[4], need[4];
-          double ad[4];
+          int64_t ai[4];
           bool anyneed = false;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             acc[j] = false;
             need[j] = false;
-            ad[j] = 0.0;
+            ai[j] = 0;
             if (p0 + j < m && av[j] <= hi32) {
               if (NARROW) {
                 // a < 2^32 - 1: the clamped thresholds decide exactly
@@ -650,7 +742,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
                   acc[j] = true;
                 else
                   need[j] = true;
-                ad[j] = (double)av[j];
+                ai[j] = (int64_t)av[j];
               } else {
                 const int64_t ax =
                     av[j] == 0xFFFFFFFFu ? exact_penalty(sb, Lk, rck, p0 + j) : (int64_t)av[j];
@@ -658,26 +750,34 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
                   acc[j] = true;
                 else if (ax <= hi)
                   need[j] = true;
-                ad[j] = (double)ax;
+                ai[j] = ax;
               }
             }
             anyneed |= need[j];
           }
           if (__any_sync(kFull, anyneed)) {
             // a in (lo, hi]: the draw decides (R7, R21); group 32c + lane
-            if (staged == tk) {
-              cp_async_wait_all();
-              __syncwarp();
-              const double *tv = sTbl + (size_t)(c - c0) * 128;
+            bool amb[4];
+            bool anyamb = false;
+            uint32_t d[4] = {(uint32_t)(c * 32 + lane), tk, rep, kTagAccept};
+            philox10(d, k0, k1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              amb[j] = false;
+              if (need[j]) {
+                const float tf = __ldg(&tablef[d[j] >> 16]);
+                const float af =
+                    NARROW ? __uint2float_rn((uint32_t)ai[j]) : __ll2float_rn(ai[j]);
+                const int r = prefilter(af, df, tf);
+                acc[j] = r > 0;
+                amb[j] = r < 0;
+                anyamb |= amb[j];
+              }
+            }
+            if (__any_sync(kFull, anyamb)) {  // the double test near the boundary
 #pragma unroll
               for (int j = 0; j < 4; ++j)
-                if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, tv[32 * j + lane]);
-            } else {
-              uint32_t d[4] = {(uint32_t)(c * 32 + lane), tk, rep, kTagAccept};
-              philox10(d, k0, k1);
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (need[j]) acc[j] = ad[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
+                if (amb[j]) acc[j] = (double)ai[j] <= __dmul_rn(delta, __ldg(&table[d[j] >> 16]));
             }
           }
           const uint32_t b0 = __ballot_sync(kFull, acc[0]), b1 = __ballot_sync(kFull, acc[1]),
@@ -823,12 +923,30 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // for before its buffer is filled again.  The next round copies again
     // from target tf + 1.
     const uint32_t tf = t + (uint32_t)kstar;
-    if (LA > 0) {
-      for (uint32_t tau = tf; tau <= issued_to; ++tau) {
-        const int b = sPf[tau & 15u].x;
-        if (b >= 0) freeb |= 1u << b;
-        sPf[tau & 15u].x = -1;
+    // the next iteration, tried alone after a flip, will likely need
+    // draws: their Philox blocks overlap the selection below, and their
+    // -ln(u) values start coming now
+    if (can_stage && tf < I_max) {
+      cp_async_wait_all();  // no earlier copy may still be writing
+      __syncwarp();
+      for (int c = c0; c < c1; ++c) {
+        uint32_t d[4] = {(uint32_t)(c * 32 + lane), tf + 1u, rep, kTagAccept};
+        philox10(d, k0, k1);
+        float *tv = sTbl + (size_t)(c - c0) * 128;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cp_async4(&tv[4 * lane + j], &tablef[d[j] >> 16]);
       }
+      cp_async_commit();
+      staged = tf + 1u;
+    }
+    if (LA > 0) {
+      // lane k gives up target tf + k (at most K + LA <= 13 of them)
+      const int nd = (int)issued_to - (int)tf + 1;
+      const uint32_t tau = tf + (uint32_t)lane;
+      const int b = lane < nd ? sPf[tau & 15u].x : -1;
+      freeb |= __reduce_or_sync(kFull, b >= 0 ? 1u << b : 0u);
+      if (lane < nd) sPf[tau & 15u].x = -1;
+      __syncwarp();
       issued_to = tf;
     }
     const WRing ef = ring[tf % kWarpRing];
@@ -892,21 +1010,6 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const int4 *src = reinterpret_cast<const int4 *>(curL + c0 * 128 + lane * 4);
         nx01 = src[0];
         nx23 = src[1];
-      }
-      // the next iteration, tried alone after a flip, will likely need
-      // draws: its -ln(u) values start coming now
-      if (can_stage && tf < I_max) {
-        cp_async_wait_all();  // no earlier copy may still be writing
-        __syncwarp();
-        for (int c = c0; c < c1; ++c) {
-          uint32_t d[4] = {(uint32_t)(c * 32 + lane), tf + 1u, rep, kTagAccept};
-          philox10(d, k0, k1);
-          double *tv = sTbl + (size_t)(c - c0) * 128;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) cp_async8(&tv[32 * j + lane], &table[d[j] >> 16]);
-        }
-        cp_async_commit();
-        staged = tf + 1u;
       }
       // the rows into this warp's shared memory now: no registers held
       // across the archive scan
@@ -1011,7 +1114,8 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       // bits of row j or column v add the change
       __syncwarp();
       const bool cached = target >= 0 && target < cslots;
-      int2 *dstL = cached ? gLR + (size_t)target * rec.mp : gWork;
+      int2 *const slotL = cached ? gLR + (size_t)target * rec.mp : nullptr;
+      int2 *dstL = use_sf ? sF : cached ? slotL : gWork;
       unsigned char *jrec = cached ? gJR + (size_t)target * rec.jr : nullptr;
       uint4 *dA = reinterpret_cast<uint4 *>(jrec);
       uint4 *sa4 = reinterpret_cast<uint4 *>(bA(cur));
@@ -1050,9 +1154,16 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             ++i;
           }
         }
+        const int4 f01 = make_int4(Lx[0], Ly[0], Lx[1], Ly[1]);
+        const int4 f23 = make_int4(Lx[2], Ly[2], Lx[3], Ly[3]);
         int4 *dst = reinterpret_cast<int4 *>(dstL + p0);
-        dst[0] = make_int4(Lx[0], Ly[0], Lx[1], Ly[1]);
-        dst[1] = make_int4(Lx[2], Ly[2], Lx[3], Ly[3]);
+        dst[0] = f01;
+        dst[1] = f23;
+        if (use_sf && cached) {  // and the slot's field record
+          int4 *dg = reinterpret_cast<int4 *>(slotL + p0);
+          dg[0] = f01;
+          dg[1] = f23;
+        }
         const uint4 a4n = make_uint4(an[0], an[1], an[2], an[3]);
         sa4[cc * 32 + lane] = a4n;
         if (cached) dA[cc * 32 + lane] = a4n;

@@ -954,11 +954,21 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     {
       const int4 ca = reinterpret_cast<const int4 *>(cntp)[0],
                  cb = reinterpret_cast<const int4 *>(cntp)[1];
-      const int total = ca.x + ca.y + ca.z + ca.w + cb.x + cb.y + cb.z + cb.w;
+      // prefix sums of the warps' counts, in registers
+      const int s0 = ca.x, s1 = s0 + ca.y, s2 = s1 + ca.z, s3 = s2 + ca.w, s4 = s3 + cb.x,
+                s5 = s4 + cb.y, s6 = s5 + cb.z, total = s6 + cb.w;
       // ---- one accepted flip at random (R11): rank r in ascending bit order
       int r = pick(ef.sel, total);
-      int ow = 0;
-      while (r >= cntp[ow]) r -= cntp[ow++];  // the warp holding rank r
+      // the warp holding rank r: the number of warps whose counts end at or
+      // before it (warps past the team's G count 0 and end at `total`)
+      const int ow = (r >= s0) + (r >= s1) + (r >= s2) + (r >= s3) + (r >= s4) + (r >= s5) +
+                     (r >= s6);
+      const int sw[8] = {0, s0, s1, s2, s3, s4, s5, s6};
+      int before_w = 0;
+#pragma unroll
+      for (int w = 1; w < 8; ++w)
+        if (ow == w) before_w = sw[w];
+      r -= before_w;
       const unsigned char *ows = T.ws0 + (size_t)ow * SL.warp;
       const uint4 *oAccW = reinterpret_cast<const uint4 *>(ows + SL.acc);
       const int32_t *oAccC = reinterpret_cast<const int32_t *>(ows + SL.acc + 16 * (size_t)SL.nc_max);
@@ -971,11 +981,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         bw = oAccW[++q];
       }
       const int c = oAccC[q];
-      // lane l's accepted bits (4l .. 4l + 3 of the chunk) as a nibble
+      // lane l's accepted bits (4l .. 4l + 3 of the chunk) as a nibble, and
+      // the accepted bits of lanes 0 .. l (from the ballots, no shuffles)
       const uint32_t nib = ((bw.x >> lane) & 1u) | (((bw.y >> lane) & 1u) << 1) |
                            (((bw.z >> lane) & 1u) << 2) | (((bw.w >> lane) & 1u) << 3);
       const int cl = __popc(nib);
-      const int incl = warp_incl_scan(cl, lane);
+      const uint32_t upto = lane == 31 ? kFull : (2u << lane) - 1u;
+      const int incl = __popc(bw.x & upto) + __popc(bw.y & upto) + __popc(bw.z & upto) +
+                       __popc(bw.w & upto);
       const int rr = r - before;
       const bool mine = rr >= incl - cl && rr < incl;
       const unsigned who = __ballot_sync(kFull, mine);
@@ -1133,25 +1146,30 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         int Lx[4] = {l01.x, l01.z, l23.x, l23.z};
         int Ly[4] = {l01.y, l01.w, l23.y, l23.w};
         uint32_t an[4];
-        int i = divn(p0), u = p0 - i * n;
+        // the four bits' (i, u), independent of one another, so that their
+        // shared-memory reads issue together; a padding bit (p >= m) has
+        // i <= 128, whose reads stay inside the rows and counts arrays
+        int iq[4], uq[4];
 #pragma unroll
         for (int q2 = 0; q2 < 4; ++q2) {
-          const int p = p0 + q2;
+          iq[q2] = divn(p0 + q2);
+          uq[q2] = p0 + q2 - iq[q2] * n;
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int p = p0 + q2, i = iq[q2], u = uq[q2];
+          const int32_t dd = sRow[2 * kMaxN + u];
+          const int32_t f1 = sRow[i], f2 = sRow[kMaxN + i];
+          const int hc = (int)rcp[i] + (int)rcp[n + u];
           if (p < m) {
-            const int32_t dd = sRow[2 * kMaxN + u];
-            Lx[q2] += sgn * sRow[i] * dd;
-            Ly[q2] += sgn * sRow[kMaxN + i] * dd;
+            Lx[q2] += sgn * f1 * dd;
+            Ly[q2] += sgn * f2 * dd;
             const int xq = (int)((nibx >> q2) & 1u) ^ (p == ps ? 1 : 0);
             const dE_t g = (dE_t)(1 - 2 * xq);
-            const dE_t h = (dE_t)rcp[i] + (dE_t)rcp[n + u] +
-                           (dE_t)(sgn * ((i == j ? 1 : 0) + (u == v ? 1 : 0))) - 1 - 2 * xq;
+            const dE_t h = (dE_t)(hc + sgn * ((i == j ? 1 : 0) + (u == v ? 1 : 0)) - 1 - 2 * xq);
             an[q2] = WA::penalty(g * ((dE_t)Lx[q2] + w1 * h), g * ((dE_t)Ly[q2] + w2 * h), lenient);
           } else {
             an[q2] = 0xFFFFFFFFu;
-          }
-          if (++u == n) {
-            u = 0;
-            ++i;
           }
         }
         const int4 f01 = make_int4(Lx[0], Ly[0], Lx[1], Ly[1]);

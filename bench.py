@@ -51,8 +51,8 @@ KERNEL_FILES = {
 }
 KERNEL_TRAFFIC = {
     "anneal_kernel": {"workload": "P25", "bytes": None, "sha256": None},
-    "warp_anneal_kernel": {"workload": "P25", "bytes": 670029056 + 1872576768,
-                           "sha256": "e019a21aa55f6135265526b302e976c1109173d01b7bd342f0559b85eeac7adf"},
+    "warp_anneal_kernel": {"workload": "P25", "bytes": 700750848 + 1878468096,
+                           "sha256": "63cd3b4f789f8aa422d26300cb500dc7a837b2ad9038e4b708c07222d4361352"},
 }
 
 

@@ -150,9 +150,9 @@ typedef struct {
                               holds the records of the first cache_slots
                               archive slots per resident team (field_cache
                               = 1: all s slots; 2: none); a jump to a slot
-                              without records rebuilds its fields.  prefetch k in 1..7 copies
+                              without records rebuilds its fields.  prefetch k in 1..15 copies
                               a jump's target k - 1 iterations ahead (0:
-                              auto: up to 6 iterations, as shared memory
+                              auto: up to 14 iterations, as shared memory
                               allows).  A team of G warps (1 to
                               8) runs each replica: automatically the
                               largest G that keeps every replica resident
@@ -338,7 +338,7 @@ void moda_qrun_destroy(moda_qrun run);
  * prefetch distances 1 and 2 besides the automatic choice, on `inst` with
  * `params` (trial_iters iterations at the cold end of the schedule, delta =
  * deltaf, on at most one replica per SM); for the warp engine, prefetch
- * distances 0, 2, 4 and 6 on the request's own replicas.  Writes into
+ * distances 0, 2, 6, 10 and 14 on the request's own replicas.  Writes into
  * *best a copy of *params with the fastest block_threads and prefetch; *best_ms (if not NULL) receives the
  * winning trial's time.  Results of a run do not depend on these two
  * fields, so tuning never changes what an anneal computes.  Blocks the

@@ -513,7 +513,7 @@ moda_status prepare_warp_run(moda_instance inst, const moda_params *p, cudaStrea
   if (p->field_cache < 0 || p->field_cache > 2)
     return fail(MODA_EINVAL, "field_cache must be 0 (auto), 1 (on) or 2 (off)");
   if (p->prefetch < 0 || p->prefetch > moda::kWarpMaxLA + 1)
-    return fail(MODA_EINVAL, "prefetch must be in [0, 7] for the warp engine");
+    return fail(MODA_EINVAL, "prefetch must be in [0, 15] for the warp engine");
   if (p->cache_slots < 0) return fail(MODA_EINVAL, "cache_slots must be >= 0");
   if (p->block_threads < 0 || p->block_threads % 32 || p->block_threads > 256)
     return fail(MODA_EINVAL, "warp engine: block_threads must be 32 G, G in 1..8 (0: auto)");
@@ -919,12 +919,13 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   const int la_max = la;
   moda::WarpSmem sm{};
   // (lookahead, window) pairs, preferred first; la + window + 1 buffers
-  static const int kOpts[][2] = {{6, 7}, {5, 6}, {4, 5}, {3, 4}, {2, 3}, {1, 2},
-                                 {2, 1}, {1, 1}, {0, 1}};
+  static const int kOpts[][2] = {{14, 15}, {10, 11}, {8, 9}, {6, 7}, {5, 6}, {4, 5},
+                                 {3, 4}, {2, 3}, {1, 2}, {2, 1}, {1, 1}, {0, 1}};
   int kw = 1;
   auto resident = [&](int G, int la_try, int kw_try, int se_try, int *blocks,
                       moda::WarpSmem *out) {
-    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G);
+    const moda::WarpSmem L =
+        moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G, false, kw_try);
     *blocks = 0;
     if ((int64_t)L.total > optin) return false;
     if (moda::warp_occupancy(narrow, G, L.total, blocks) != cudaSuccess || *blocks < 1)
@@ -973,7 +974,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   // residency (as many teams, or still every replica, per launch).
   bool sfields = false;
   {
-    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true);
+    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true, kw);
     int blocks = 0;
     if ((int64_t)L.total <= optin &&
         moda::warp_occupancy(narrow, best_w, L.total, &blocks) == cudaSuccess &&
@@ -1873,7 +1874,7 @@ moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t
     bool found = false;
     float fastest = 0.f;
     moda_params winner = *params;
-    for (int32_t pf : {1, 3, 5, 7}) {
+    for (int32_t pf : {1, 3, 7, 11, 15}) {
       trial.prefetch = pf;
       moda_run r = nullptr;
       if (moda_anneal(inst, &trial, stream, &r) != MODA_OK) continue;

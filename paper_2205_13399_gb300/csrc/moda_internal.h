@@ -236,7 +236,7 @@ cudaError_t anneal_function_special(int rounds, bool narrow, int mode, size_t sm
 // L_k (int32 pairs) live in global memory and are read only by flips.
 
 constexpr int kWarpRing = 128;  // draw / schedule ring entries (iterations)
-constexpr int kWarpMaxLA = 6;   // prefetch distance (iterations ahead)
+constexpr int kWarpMaxLA = 14;  // prefetch distance (iterations ahead)
 
 // Records of one archive slot for a run of n, m (the field cache of the
 // warp annealer):
@@ -274,6 +274,8 @@ struct WarpSmem {
   uint32_t buf, mbar, ring, aE, cnt, fld, team;   // team part (bytes: team)
   uint32_t acc, rows, rc, pf, tbl, warp;          // warp part (bytes: warp)
   int32_t nc_max;
+  int32_t pfr;     // per-target record ring entries: 16, or 32 past 16 buffers
+  int32_t cst;     // ints per round parity of the counts: 8 (window + 1)
   uint32_t total;  // team + G warps
 };
 // stage: each warp owns at most two chunks of the largest run (then the
@@ -284,27 +286,29 @@ __host__ __device__ inline bool warp_stage(int m_max, int G) {
 // sfields: the team part also holds the fields of the state a flip
 // reached (8 bytes per bit), so that flips following flips read them on chip.
 __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G,
-                                              bool sfields = false) {
+                                              bool sfields, int window) {
   const WarpRec r = warp_rec(n_max, m_max);
   WarpSmem L;
   size_t o = 0;
   L.jr = r.jr;
   L.nc_max = r.nc;
+  L.pfr = nbuf <= 16 ? 16 : 32;  // holds targets t .. t + window - 1 + lookahead
+  L.cst = 8 * (window + 1);
   L.buf = 0;                 o = align_up(o + (size_t)nbuf * r.jr, 16);
   L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nbuf, 16);
   L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
   L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
-  // accepted counts of the warps by round parity [2][8 positions + 2][8],
-  // the work item, the warps' partial sums of a rebuild [8][2], the warps'
-  // first dominated archive slots by round parity [2][8]
-  L.cnt = (uint32_t)o;       o = align_up(o + 640 + 16 + 128 + 64, 16);
+  // accepted counts of the warps by round parity [2][window positions +
+  // 1][8], the work item, the warps' partial sums of a rebuild [8][2], the
+  // warps' first dominated archive slots by round parity [2][8]
+  L.cnt = (uint32_t)o;       o = align_up(o + 8 * (size_t)L.cst + 16 + 128 + 64, 16);
   L.fld = (uint32_t)o;       if (sfields) o = align_up(o + 8 * (size_t)r.mp, 16);
   L.team = (uint32_t)o;
   o = 0;
   L.acc = 0;                 o = align_up(o + 20 * (size_t)r.nc, 16);
   L.rows = (uint32_t)o;      o = align_up(o + 3 * 4 * (size_t)kMaxN, 16);
   L.rc = (uint32_t)o;        o = align_up(o + 2 * (size_t)kMaxN, 16);
-  L.pf = (uint32_t)o;        o = align_up(o + 16 * 16 + 4 * 16, 16);
+  L.pf = (uint32_t)o;        o = align_up(o + 20 * (size_t)L.pfr, 16);
   L.tbl = (uint32_t)o;       // staged -ln(u), 2 chunks
   if (warp_stage(m_max, G)) o = align_up(o + 8 * 4 * 32 * 2, 16);
   L.warp = (uint32_t)o;

@@ -63,6 +63,12 @@ static_assert(sizeof(WRing) == 40, "ring entry layout");
 // fl(delta T) (accept, 1), and af >= fl32(pf (1 + 2^-20)) implies
 // a >= (1 + 11 2^-24) fl(delta T) (reject, 0).  Otherwise (-1, a within
 // about 2^-20 of the product, rare) the caller takes the double test.
+// fl32(a) of a penalty a >= 0: the 32-bit conversion whenever a fits it
+// (the 64-bit one is slow here), both rounding to nearest.
+__device__ __forceinline__ float penalty_f32(int64_t a) {
+  return a < 0x100000000ll ? __uint2float_rn((uint32_t)a) : __ll2float_rn(a);
+}
+
 __device__ __forceinline__ int prefilter(float af, float df, float Tf) {
   const float pf = __fmul_rn(df, Tf);
   if (af <= __fmul_rn(pf, 1.0f - 0x1p-20f)) return 1;
@@ -162,9 +168,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // then [warp] its first window position with an accepted bit (a warp may
   // write the next round's while another still reads this round's)
   int32_t *sCnt = reinterpret_cast<int32_t *>(ts + SL.cnt);
-  int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 656);  // [G][2] rebuild sums
+  // counts: [2 parities][window positions + 1][8 warps], SL.cst ints a parity
+  const int cst = SL.cst;
+  int64_t *sSum = reinterpret_cast<int64_t *>(ts + SL.cnt + 8 * cst + 16);  // [G][2] rebuild sums
   // explore: each warp's first dominated slot, [round parity][warp]
-  int32_t *sScan = reinterpret_cast<int32_t *>(ts + SL.cnt + 784);
+  int32_t *sScan = reinterpret_cast<int32_t *>(ts + SL.cnt + 8 * cst + 144);
   // the fields of the state the last flip reached, while Lc.sfields: flips
   // that follow flips read them here rather than from global memory
   int2 *const sF = reinterpret_cast<int2 *>(ts + SL.fld);
@@ -174,7 +182,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // = {buffer or -1, slot, issuing iteration} of the copy for target
   // iteration tt; sWr[x & 15] = the slot iteration x wrote (-1: none)
   int4 *sPf = reinterpret_cast<int4 *>(ws + SL.pf);
-  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 256);
+  // per-target records and writes, a ring of SL.pfr iterations
+  const uint32_t pfm = (uint32_t)SL.pfr - 1u;
+  int32_t *sWr = reinterpret_cast<int32_t *>(ws + SL.pf + 16 * SL.pfr);
   uint4 *sAccW = reinterpret_cast<uint4 *>(ws + SL.acc);
   int32_t *sAccC = reinterpret_cast<int32_t *>(ws + SL.acc + 16 * (size_t)SL.nc_max);
   int32_t *sRow = reinterpret_cast<int32_t *>(ws + SL.rows);  // Fs1 row, Fs2 row, D row
@@ -373,12 +383,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         x0[4 * c + w] = v;
       }
     }
-    if (lane < 16) {
+    if (lane < SL.pfr) {
       sPf[lane] = make_int4(-1, 0, 0, 0);
       sWr[lane] = -1;
     }
     if (leader) {
-      for (int q2 = lane; q2 < 160; q2 += 32) sCnt[q2] = 0;  // counts of warps beyond G stay 0
+      for (int q2 = lane; q2 < 2 * cst; q2 += 32)
+        sCnt[q2] = 0;  // counts of warps beyond G stay 0
       fill(1);
       fill(33);
     }
@@ -447,7 +458,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     if (LA > 0 && !(acount > 0 && flip_streak < 3)) {
       // no copies now: the targets get empty records
       const int nI = (int)(t + (uint32_t)(K - 1 + LA)) - (int)issued_to;
-      if (lane < nI) sPf[(issued_to + 1u + (uint32_t)lane) & 15u] = make_int4(-1, 0, (int)t, 0);
+      if (lane < nI) sPf[(issued_to + 1u + (uint32_t)lane) & pfm] = make_int4(-1, 0, (int)t, 0);
       if (nI > 0) issued_to += (uint32_t)nI;
       __syncwarp();
     } else if (LA > 0) {
@@ -462,7 +473,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         // a slot written in the previous iteration is left alone: warps
         // still writing it are ordered before the copy only by the next
         // barrier
-        want = sp < cslots && sWr[(t - 1u) & 15u] != sp;
+        want = sp < cslots && sWr[(t - 1u) & pfm] != sp;
       }
       const uint32_t wm = __ballot_sync(kFull, want);
       // the r-th copy takes the r-th free buffer (there are enough: at
@@ -491,7 +502,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
       }
       pend |= bm;
-      if (lane < nI) sPf[tt & 15u] = make_int4(b, b >= 0 ? sp : 0, (int)t, 0);
+      if (lane < nI) sPf[tt & pfm] = make_int4(b, b >= 0 ? sp : 0, (int)t, 0);
       if (nI > 0) issued_to += (uint32_t)nI;
       __syncwarp();
     }
@@ -499,11 +510,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // tau's draw picks now and no iteration before `lim` rewrote that slot
     // since (the iterations of this window write nothing before a flip).
     auto usable = [&](uint32_t tau, int slot, uint32_t lim) {
-      const int4 pr = sPf[tau & 15u];
+      const int4 pr = sPf[tau & pfm];
       bool ok = pr.x >= 0 && pr.y == slot;
       if (ok && last_wr_t >= (uint32_t)pr.z)
         for (uint32_t xi = (uint32_t)pr.z; xi < lim; ++xi)
-          if (sWr[xi & 15u] == slot) ok = false;
+          if (sWr[xi & pfm] == slot) ok = false;
       return ok;
     };
     // the window: iteration t + k (k >= 1) tries the member iteration
@@ -522,7 +533,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       bool ok = true;
       int tb = -1;
       if (lane < Keff - 1) {
-        tb = sPf[(t + (uint32_t)lane) & 15u].x;
+        tb = sPf[(t + (uint32_t)lane) & pfm].x;
         ok = mbar_wait(&sbar[tb], (par >> tb) & 1u);
       }
       if (!__all_sync(kFull, ok)) fail = true;
@@ -533,7 +544,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
 
     // ---- the parallel trials (Eq. pacceptms / pacceptml) of the window,
     // this warp's chunks, up to its first accepted bit
-    int32_t *cntr = sCnt + 80 * (int)(rnd & 1u);  // [k][warp] counts, then [warp] first k
+    int32_t *cntr = sCnt + cst * (int)(rnd & 1u);  // [k][warp] counts, then [warp] first k
     int first_w = Keff, nl = 0;
     // A run of flips (one iteration, not staged): nearly every chunk
     // needs draws, so the draws and -ln(u) loads of two chunks are in
@@ -550,12 +561,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       int sbl = cur;
       uint32_t hl = 0u;
       if (lane < Keff) {
-        if (lane > 0) sbl = sPf[(t + (uint32_t)(lane - 1)) & 15u].x;
+        if (lane > 0) sbl = sPf[(t + (uint32_t)(lane - 1)) & pfm].x;
         const int64_t hk = ring[(t + (uint32_t)lane) % kWarpRing].hi;
         hl = hk < 0xFFFFFFFFll ? (uint32_t)hk : 0xFFFFFFFFu;
       }
       if (c1 - c0 <= 2) {
         // few chunks: every position's loads of a chunk issue together
+        // (fully unrolled and predicated)
         for (int c = c0; c < c1; ++c) {
 #pragma unroll
           for (int k = 0; k < kWarpMaxLA + 1; ++k) {
@@ -570,15 +582,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       } else {
 #pragma unroll
         for (int k = 0; k < kWarpMaxLA + 1; ++k) {
+          if (k >= Keff) break;  // Keff is the same in every lane
           const int sbk = __shfl_sync(kFull, sbl, k);
           const uint32_t h32 = __shfl_sync(kFull, hl, k);
-          if (k < Keff) {
-            const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
+          const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
 #pragma unroll 4
-            for (int c = c0; c < c1; ++c) {
-              const uint4 a4 = ap[c * 32 + lane];
-              cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
-            }
+          for (int c = c0; c < c1; ++c) {
+            const uint4 a4 = ap[c * 32 + lane];
+            cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
           }
         }
       }
@@ -616,7 +627,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             } else {
               const int64_t ax =
                   av[j] == 0xFFFFFFFFu ? exact_penalty(cur, curL, rck, p0 + j) : (int64_t)av[j];
-              const int r = ax <= lo ? 1 : ax > hi ? 0 : prefilter(__ll2float_rn(ax), df, tv[j]);
+              const int r = ax <= lo ? 1 : ax > hi ? 0 : prefilter(penalty_f32(ax), df, tv[j]);
               acc[j] = r > 0 || (r < 0 && (double)ax <= __dmul_rn(delta, __ldg(&table[d[j] >> 16])));
             }
           }
@@ -669,7 +680,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
               r = av[j] <= lo32 ? 1 : prefilter(__uint2float_rn(av[j]), df, tv[j]);
             } else {
               if (av[j] == 0xFFFFFFFFu) ai[j] = exact_penalty(cur, curL, rck, p0 + j);
-              r = ai[j] <= lo ? 1 : ai[j] > hi ? 0 : prefilter(__ll2float_rn(ai[j]), df, tv[j]);
+              r = ai[j] <= lo ? 1 : ai[j] > hi ? 0 : prefilter(penalty_f32(ai[j]), df, tv[j]);
             }
             acc[j] = r > 0;
             amb[j] = r < 0;
@@ -712,7 +723,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const int2 *Lk = curL;
       const unsigned char *rck = rc_stale ? bRC(cur) : rcp;
       if (k > 0) {
-        const int4 pr = sPf[(tk - 1u) & 15u];
+        const int4 pr = sPf[(tk - 1u) & pfm];
         sb = pr.x;
         Lk = gLR + (size_t)pr.y * rec.mp;
         rck = bRC(sb);
@@ -766,8 +777,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
               amb[j] = false;
               if (need[j]) {
                 const float tf = __ldg(&tablef[d[j] >> 16]);
-                const float af =
-                    NARROW ? __uint2float_rn((uint32_t)ai[j]) : __ll2float_rn(ai[j]);
+                const float af = NARROW ? __uint2float_rn((uint32_t)ai[j]) : penalty_f32(ai[j]);
                 const int r = prefilter(af, df, tf);
                 acc[j] = r > 0;
                 amb[j] = r < 0;
@@ -799,23 +809,23 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         break;
       }
     }
-    if (lane == 0) cntr[64 + wt] = first_w;
+    if (lane == 0) cntr[cst - 8 + wt] = first_w;
     // every warp's counts, and whether any warp gave up a wait
     if (sync_or(fail)) {
       fail = true;
       break;
     }
     int kstar = Keff;  // the window's first iteration with an accepted bit
-    for (int w = 0; w < G; ++w) kstar = min(kstar, (int)cntr[64 + w]);
+    for (int w = 0; w < G; ++w) kstar = min(kstar, (int)cntr[cst - 8 + w]);
     ++rnd;
 
     // ---- iterations t .. t + kstar - 1 jump (Alg. 3), or escape with an
     // empty archive (R12)
     if (kstar > 0) {
-      if (lane < kstar) sWr[(t + (uint32_t)lane) & 15u] = -1;
+      if (lane < kstar) sWr[(t + (uint32_t)lane) & pfm] = -1;
       __syncwarp();
       if (acount == 0) {  // K = 1: one iteration
-        const int4 pr = LA > 0 ? sPf[t & 15u] : make_int4(-1, 0, 0, 0);
+        const int4 pr = LA > 0 ? sPf[t & pfm] : make_int4(-1, 0, 0, 0);
         if (pr.x >= 0) freeb |= 1u << pr.x;
         ++nempty;
         if (trace != nullptr && leader && lane == 0) {
@@ -830,7 +840,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const int ns = min(kstar, Keff - 1);
         if (trace != nullptr && leader && lane == 0)
           for (int k = 0; k < ns; ++k) {
-            const int4 pr = sPf[(t + (uint32_t)k) & 15u];
+            const int4 pr = sPf[(t + (uint32_t)k) & pfm];
             const int64_t *be = bE(pr.x);
             int64_t *tr = trace + ((size_t)row * (size_t)I_max + (size_t)(t + k - 1)) * 3;
             tr[0] = be[0];
@@ -838,10 +848,10 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             tr[2] = -1 - (int64_t)pr.y;
           }
         if (ns > 0) {
-          const int pb = lane + 1 < ns ? sPf[(t + (uint32_t)lane) & 15u].x : -1;
+          const int pb = lane + 1 < ns ? sPf[(t + (uint32_t)lane) & pfm].x : -1;
           freeb |= __reduce_or_sync(kFull, pb >= 0 ? 1u << pb : 0u);  // passed through
           freeb |= 1u << cur;
-          const int4 pr = sPf[(t + (uint32_t)(ns - 1)) & 15u];
+          const int4 pr = sPf[(t + (uint32_t)(ns - 1)) & pfm];
           cur = pr.x;
           curL = gLR + (size_t)pr.y * rec.mp;
           const int64_t *be = bE(cur);
@@ -855,7 +865,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           // the window's last iteration jumps to a member no trial holds
           const uint32_t tk = t + (uint32_t)(kstar - 1);
           const int slot = pick(ring[tk % kWarpRing].rst, acount);
-          const int4 pr = LA > 0 ? sPf[tk & 15u] : make_int4(-1, 0, 0, 0);
+          const int4 pr = LA > 0 ? sPf[tk & pfm] : make_int4(-1, 0, 0, 0);
           int nbuf;
           if (LA > 0 && usable(tk, slot, tk)) {
             nbuf = pr.x;
@@ -940,12 +950,12 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       staged = tf + 1u;
     }
     if (LA > 0) {
-      // lane k gives up target tf + k (at most K + LA <= 13 of them)
+      // lane k gives up target tf + k (at most K + LA < 32 of them)
       const int nd = (int)issued_to - (int)tf + 1;
       const uint32_t tau = tf + (uint32_t)lane;
-      const int b = lane < nd ? sPf[tau & 15u].x : -1;
+      const int b = lane < nd ? sPf[tau & pfm].x : -1;
       freeb |= __reduce_or_sync(kFull, b >= 0 ? 1u << b : 0u);
-      if (lane < nd) sPf[tau & 15u].x = -1;
+      if (lane < nd) sPf[tau & pfm].x = -1;
       __syncwarp();
       issued_to = tf;
     }
@@ -1114,7 +1124,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         }
         if (target < 0 && acount < s) target = acount++;
       }
-      sWr[tf & 15u] = target;
+      sWr[tf & pfm] = target;
       if (target >= 0) last_wr_t = tf;
       if (target >= 0 && leader && lane == 0) {
         gE[2 * target] = nE1;
@@ -1280,7 +1290,7 @@ __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L)
   T.ts = smem + (size_t)team * L.sm.total;
   T.ws0 = T.ts + L.sm.team;
   uint64_t *bar = reinterpret_cast<uint64_t *>(T.ts + L.sm.mbar);
-  int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 640);
+  int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 8 * L.sm.cst);
   const bool leader = T.wt == 0;
   if (leader && lane == 0) {
     for (int b = 0; b < L.nbuf; ++b) mbar_init(&bar[b], 1);

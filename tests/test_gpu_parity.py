@@ -310,7 +310,7 @@ def test_autotune_picks_a_layout_with_identical_results():
     assert np.array_equal(a.stats[:, :4], b.stats[:, :4])
     # the warp engine: a prefetch distance, no block shape
     best, ms = moda.autotune(g, trial_iters=500, engine="warp", **kw)
-    assert best.block_threads == 0 and best.prefetch in (1, 3, 5, 7) and ms > 0
+    assert best.block_threads == 0 and best.prefetch in (1, 3, 7, 11, 15) and ms > 0
     a = moda.anneal(g, params=best).wait().read()
     for key in ("count", "E", "bits", "x", "E_final"):
         assert np.array_equal(getattr(a, key), getattr(b, key)), key

@@ -35,10 +35,10 @@ def test_warp_traced_small(acc, arc, cache, team):
 
 
 @pytest.mark.parametrize("team", [1, 4])
-@pytest.mark.parametrize("prefetch", [1, 2, 3, 7])
+@pytest.mark.parametrize("prefetch", [1, 2, 3, 7, 15])
 def test_warp_prefetch_distances(prefetch, team):
-    """Jump records copied 0, 1, 2 or 6 iterations ahead give the oracle's
-    run."""
+    """Jump records copied 0, 1, 2, 6 or 14 iterations ahead (windows of up
+    to 15 iterations) give the oracle's run."""
     inst = inputs.euclid_instance(23, 0.5, False, index=3, workload="P25")
     kw = dict(replicas=5, I_max=4000, seed=8, **FAST)
     _, _, res, tr = gpu_run(inst, trace=True, prefetch=prefetch, engine="warp",

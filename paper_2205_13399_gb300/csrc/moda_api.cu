@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "moda.h"
+#include "moda_check.h"
 #include "moda_host.h"
 #include "moda_internal.h"
 
@@ -1855,6 +1856,49 @@ moda_status moda_sbda_front(moda_instance src, const moda_run *runs, int32_t cou
 
 
 // ---- autotuning ------------------------------------------------------------
+
+moda_status moda_check_accept(const int64_t *a, const double *delta, const uint32_t *idx,
+                              int32_t count, void *cuda_stream, uint8_t *accept, int8_t *path) {
+  if (count < 0) return fail(MODA_EINVAL, "count must be >= 0");
+  if (count > 0 && (!a || !delta || !idx || !accept || !path))
+    return fail(MODA_EINVAL, "NULL array");
+  for (int32_t k = 0; k < count; ++k) {
+    if (a[k] < 0) return fail(MODA_EINVAL, "penalties must be >= 0");
+    if (!(delta[k] > 0.0) || !std::isfinite(delta[k]))
+      return fail(MODA_EINVAL, "delta must be positive and finite");
+    if (idx[k] >= (uint32_t)moda::kTableSize) return fail(MODA_EINVAL, "idx must be < 65536");
+  }
+  if (count == 0) return MODA_OK;
+  int dev = 0;
+  MODA_CUDA(cudaGetDevice(&dev));
+  DeviceData *dd = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mutex);
+    moda_status st = device_table(dev, &dd);
+    if (st != MODA_OK) return st;
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const size_t n = (size_t)count;
+  const size_t bytes = n * (8 + 8 + 4 + 1 + 1) + 64;
+  unsigned char *d = nullptr;
+  MODA_CUDA(cudaMalloc(&d, bytes));
+  int64_t *da = reinterpret_cast<int64_t *>(d);
+  double *dd_ = reinterpret_cast<double *>(d + 8 * n);
+  uint32_t *di = reinterpret_cast<uint32_t *>(d + 16 * n);
+  uint8_t *dacc = d + 20 * n;
+  int8_t *dpath = reinterpret_cast<int8_t *>(d + 21 * n);
+  cudaError_t e = cudaMemcpyAsync(da, a, 8 * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dd_, delta, 8 * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(di, idx, 4 * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess)
+    e = moda::launch_check_accept(da, dd_, di, count, dd->table, dd->tablef, dacc, dpath, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(accept, dacc, n, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(path, dpath, n, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "moda_check_accept");
+  return MODA_OK;
+}
 
 moda_status moda_autotune(moda_instance inst, const moda_params *params, int32_t trial_iters,
                           void *cuda_stream, moda_params *best, float *best_ms) {

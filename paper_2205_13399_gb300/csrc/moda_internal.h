@@ -376,6 +376,11 @@ cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
 // warps, for a CUDA graph node, with `smem` bytes of dynamic shared memory
 // allowed.
 cudaError_t warp_function(bool narrow, int team, size_t smem, const void **func);
+// The warp engine's acceptance decisions for `count` (penalty, delta, table
+// index) triples in device memory (moda_check_accept).
+cudaError_t launch_check_accept(const int64_t *a, const double *delta, const uint32_t *idx,
+                                int count, const double *T, const float *Tf, uint8_t *accept,
+                                int8_t *path, cudaStream_t stream);
 // Resident blocks (one team of `team` warps each) per SM.
 cudaError_t warp_occupancy(bool narrow, int team, size_t smem, int *blocks);
 

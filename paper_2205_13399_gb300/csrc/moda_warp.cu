@@ -128,6 +128,10 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   using dE_t = typename WA::dE_t;
   const int lane = T.lane, G = T.G, wt = T.wt;
   const bool leader = wt == 0;
+  // the warp that refills the ring and writes a flip's archive energies and
+  // record header: the last, so that the leader (which starts the copies)
+  // carries less of each iteration's serial work
+  const bool scribe = wt == G - 1;
   const int n = R.n, m = R.m, W = R.W, s = R.s;
   const WarpRec rec = warp_rec(n, m);
   const int NC = rec.nc;
@@ -213,7 +217,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   };
   auto divn = [&](int p) { return (int)__umulhi((uint32_t)p, magic); };
 
-  // Iterations first .. first + 31 into the ring (leader warp): schedule
+  // Iterations first .. first + 31 into the ring (one warp): schedule
   // entry (Alg. 3's cooling, the last entry held once delta reaches
   // delta_f) and the draws (0, q, replica, tag) of the select, restart and
   // exploit purposes.
@@ -436,7 +440,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   uint32_t issued_to = (uint32_t)LA;
   uint32_t t = 1, rnd = 0;
   while (t <= I_max) {
-    if (leader)
+    if (scribe)  // entries read before this round's barrier were written in earlier rounds
       while (filled < t + 48u) {
         fill(filled + 1u);
         filled += 32u;
@@ -1126,7 +1130,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       }
       sWr[tf & pfm] = target;
       if (target >= 0) last_wr_t = tf;
-      if (target >= 0 && leader && lane == 0) {
+      if (target >= 0 && scribe && lane == 0) {
         gE[2 * target] = nE1;
         gE[2 * target + 1] = nE2;
         if (target < se) sAE[target] = make_longlong2(nE1, nE2);
@@ -1215,7 +1219,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         rcp[n + v] = (unsigned char)((int)rcp[n + v] + sgn);
       }
       __syncwarp();
-      if (target >= 0 && leader) {
+      if (target >= 0 && scribe) {
         if (cached) {
           const uint32_t *rcw = reinterpret_cast<const uint32_t *>(rcp);
           uint32_t *jrc = reinterpret_cast<uint32_t *>(jrec + rec.off_rc);
@@ -1321,6 +1325,22 @@ __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L)
 }  // namespace
 
 namespace {
+// The warp engine's acceptance decision for given penalties, one per thread
+// (the same device functions its trials run): accept[k] and the path taken
+// (1 or 0 decided in FP32, -1 by the double test).
+__global__ void check_accept_kernel(const int64_t *a, const double *delta, const uint32_t *idx,
+                                    int count, const double *T, const float *Tf,
+                                    uint8_t *accept, int8_t *path) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int64_t ak = a[k];
+  const double dk = delta[k];
+  const uint32_t ik = idx[k];
+  const int r = prefilter(penalty_f32(ak), __double2float_rn(dk), Tf[ik]);
+  accept[k] = (uint8_t)(r > 0 || (r < 0 && (double)ak <= __dmul_rn(dk, T[ik])));
+  path[k] = (int8_t)r;
+}
+
 // The kernel variant of a launch: narrow or not.
 const void *warp_kernel(bool narrow, int) {
   return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
@@ -1340,6 +1360,15 @@ cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
   void *args[1] = {const_cast<WarpLaunch *>(&L)};
   e = cudaLaunchKernel(f, dim3((unsigned)grid), dim3((unsigned)(32 * warps)), args, smem, stream);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_accept(const int64_t *a, const double *delta, const uint32_t *idx,
+                                int count, const double *T, const float *Tf, uint8_t *accept,
+                                int8_t *path, cudaStream_t stream) {
+  if (count < 1) return cudaSuccess;
+  check_accept_kernel<<<(count + 255) / 256, 256, 0, stream>>>(a, delta, idx, count, T, Tf,
+                                                               accept, path);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ ABI_FUNCTIONS = [
     "moda_server_destroy", "moda_probe_int_peak", "moda_probe_smem_peak", "moda_scalarize",
     "moda_sbda_front", "moda_read_snapshot", "moda_qubo_create", "moda_qubo_destroy",
     "moda_qubo_anneal", "moda_qrun_wait", "moda_qrun_read", "moda_qrun_elapsed_ms",
-    "moda_qrun_destroy", "moda_autotune",
+    "moda_qrun_destroy", "moda_autotune", "moda_check_accept",
 ]
 
 
@@ -154,6 +154,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = st
         f.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+    lib.moda_check_accept.restype = st
+    lib.moda_check_accept.argtypes = [P, P, P, i32, P, P, P]
     lib.moda_scalarize.restype = st
     lib.moda_scalarize.argtypes = [P, i32, i32, ctypes.POINTER(P)]
     lib.moda_sbda_front.restype = st
@@ -481,6 +483,21 @@ def probe_int_peak(iters: int = 20000, stream=None) -> tuple[float, float]:
     _check(_lib.moda_probe_int_peak(int(iters), _stream_handle(stream), ctypes.byref(v),
                                     ctypes.byref(ms)))
     return float(v.value), float(ms.value)
+
+
+def check_accept(a, delta, idx, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    """``moda_check_accept``: the device's acceptance decisions
+    a <= fl(delta T[idx]) and the path each took (1 / 0: FP32, -1: double)."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64).reshape(-1))
+    delta = np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(-1))
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.uint32).reshape(-1))
+    if not (a.size == delta.size == idx.size):
+        raise ValueError("a, delta and idx need the same length")
+    acc = np.zeros(a.size, dtype=np.uint8)
+    path = np.zeros(a.size, dtype=np.int8)
+    _check(_lib.moda_check_accept(_ptr(a), _ptr(delta), _ptr(idx), int(a.size),
+                                  _stream_handle(stream), _ptr(acc), _ptr(path)))
+    return acc.astype(bool), path
 
 
 def probe_smem_peak(iters: int = 20000, stream=None) -> tuple[float, float]:

@@ -164,3 +164,13 @@ def test_kernel_variant_choice(tmp_path):
                     os.path.join(here, "kernel_mode_check.cc"), "-o", exe], check=True)
     res = subprocess.run([exe], capture_output=True, text=True)
     assert res.returncode == 0, res.stdout
+
+
+def test_check_accept_rejects_bad_arguments():
+    """moda_check_accept validates every input before any device work."""
+    from paper_2205_13399_gb300 import moda
+    for a, d, i in (([-1], [1.0], [0]), ([1], [0.0], [0]), ([1], [1.0], [65536]),
+                    ([1], [float("inf")], [3])):
+        with pytest.raises(moda.MODAError) as ei:
+            moda.check_accept(a, d, i)
+        assert ei.value.status == moda.EINVAL

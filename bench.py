@@ -648,8 +648,14 @@ def run_hvtrace(args):
         out[acc] = [[(p["c1"], p["c2"]) for p in r.read_archive(snapshot=j, perms=False)
                      if p["feasible"]] for j in range(I_max // K)]
         r.close()
-    plain = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"]).wait()
+    # the snapshot cost against the same engine without snapshots (the
+    # block engine: snapshots are one of its options), and the warp engine
+    # a run without snapshots takes by default
+    plain = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"], engine="block").wait()
     plain_ms = plain.elapsed_ms()
+    plain.close()
+    plain = moda.anneal(inst, replicas=R, I_max=I_max, seed=run["seed"]).wait()
+    warp_ms = plain.elapsed_ms()
     plain.close()
     clk = clocks.stop()
     allp = [p for acc in out for f in out[acc] for p in f]
@@ -675,7 +681,9 @@ def run_hvtrace(args):
         "hv_final": {acc: hv[acc][-1] for acc in hv},
         "iterations_to_95pct_hv": {acc: reach(hv[acc]) for acc in hv},
         "hv_every_10_snapshots": {acc: [round(v, 4) for v in hv[acc][9::10]] for acc in hv},
-        "snapshot_overhead": {"ms_with": ms["strict"], "ms_plain": plain_ms},
+        "snapshot_overhead": {"ms_with": ms["strict"], "ms_plain": plain_ms,
+                              "engine": "block",
+                              "ms_default_engine_without_snapshots": warp_ms},
         "gpu_launches": 2, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

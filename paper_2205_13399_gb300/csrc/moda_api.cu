@@ -818,6 +818,7 @@ moda_status prepare_run(moda_instance inst, const moda_params *p,
   a.sch_lo = sch.lo;
   a.sch_hi = sch.hi;
   a.table = dd->table;
+  a.tablef = dd->tablef;
   a.Fs1 = inst->dFs1;
   a.Fs2 = inst->dFs2;
   a.D = inst->dD;

@@ -173,6 +173,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Inclusive prefix sum of `v` over the lanes.
+// The acceptance test of a bit whose penalty a (an integer >= 0) lies in
+// (lo_t, hi_t] is a <= fl(delta T) (R7).  This part's FP64 rate is low, so
+// it is first decided in FP32 where that is exact: with df = fl32(delta),
+// Tf = fl32(T) and pf = fl32(df Tf), pf lies within (1 +- 2^-24)^3 of
+// delta T, fl(delta T) within 2^-53 of it, and af = fl32(a) within 2^-24 of
+// a.  Hence af <= fl32(pf (1 - 2^-20)) implies a <= (1 - 11 2^-24)
+// fl(delta T) (accept, 1), and af >= fl32(pf (1 + 2^-20)) implies
+// a >= (1 + 11 2^-24) fl(delta T) (reject, 0).  Otherwise (-1, a within
+// about 2^-20 of the product, rare) the caller takes the double test.
+// fl32(a) of a penalty a >= 0: the 32-bit conversion whenever a fits it
+// (the 64-bit one is slow here), both rounding to nearest.
+__device__ __forceinline__ float penalty_f32(int64_t a) {
+  return a < 0x100000000ll ? __uint2float_rn((uint32_t)a) : __ll2float_rn(a);
+}
+
+__device__ __forceinline__ int prefilter(float af, float df, float Tf) {
+  const float pf = __fmul_rn(df, Tf);
+  if (af <= __fmul_rn(pf, 1.0f - 0x1p-20f)) return 1;
+  if (af >= __fmul_rn(pf, 1.0f + 0x1p-20f)) return 0;
+  return -1;
+}
+
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {

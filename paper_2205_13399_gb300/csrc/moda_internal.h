@@ -71,6 +71,7 @@ struct AnnealArgs {
   const int64_t *sch_lo;    // [nsched] floor(delta_t * T_min): a <= lo accepts
   const int64_t *sch_hi;    // [nsched] floor(delta_t * T_max): a > hi rejects
   const double *table;      // [65536] -ln((idx + 0.5) / 65536)
+  const float *tablef;      // [65536] the same rounded to float (FP32 test)
   const int32_t *Fs1, *Fs2; // [n][n] F_k + F_k^T (symmetric)
   const int32_t *D;         // [n][n] symmetric distances, zero diagonal
   // Field cache, [R][s] records of slot_layout(m, narrow).bytes, or
@@ -123,7 +124,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int W, int s,
   L.mask = o;  o = align_up(o + 4 * 2 * items, 16);  // accept ballots x 2
   L.amask = o; o = align_up(o + 4 * items, 16);
   L.rnd = o;   o = align_up(o + 32 * 4 * 4, 16);             // 32 iterations
-  L.sch = o;   o = align_up(o + 32 * 48, 16);                // 32 entries
+  L.sch = o;   o = align_up(o + 32 * 56, 16);                // 32 entries
   L.RC = o;    o = align_up(o + 4 * 4 * (size_t)n, 16);      // 2 x (R, C)
   L.red = o;   o = align_up(o + 8 * 32, 16);
   L.bc = o;    o = align_up(o + 32, 16);

@@ -160,7 +160,10 @@ struct SchEntry {
   // normalised acceptance: fl(delta T_min) and fl(delta T_max); lo and hi
   // then bound the integer penalty (see fill_rings)
   double lod, hid;
+  float deltaf;  // fl32(delta), for the FP32 test of prefilter()
+  uint32_t pad;
 };
+static_assert(sizeof(SchEntry) == 56, "schedule entry layout (smem_layout reserves 56 bytes)");
 
 // What iteration t does when no bit is accepted (Alg. 3), settled by
 // control warp A before the iteration's barrier.
@@ -345,7 +348,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (lane < 8)
       sSch[it % kRing] = SchEntry{sd, slo, shi,
                                   (uint32_t)(slo < 4294967295ll ? slo : 4294967295ll),
-                                  (uint32_t)(shi < 4294967295ll ? shi : 4294967295ll), lod, hid};
+                                  (uint32_t)(shi < 4294967295ll ? shi : 4294967295ll), lod, hid,
+                                  __double2float_rn(sd), 0u};
   };
   if (ctlB && lane == 0 && pf) {
     for (int b = 0; b < NB; ++b) mbar_init(&sBar[b], 1);
@@ -537,10 +541,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   };
   // schedule entry of the current iteration, in registers
   double cur_delta, cur_lod = 0, cur_hid = 0;
+  float cur_deltaf;
   pen_t cur_lo, cur_hi;
   {
     const SchEntry e = sSch[1];
     cur_delta = e.delta;
+    cur_deltaf = e.deltaf;
     cur_lo = NARROW ? (pen_t)e.lo32 : (pen_t)e.lo;
     cur_hi = NARROW ? (pen_t)e.hi32 : (pen_t)e.hi;
     if (NORM_ON) {
@@ -665,7 +671,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             philox10(c, k0, k1);
             w = word_of(c, p & 3);
           }
-          if (need) acc = (double)a <= __dmul_rn(delta, A.table[w >> 16]);
+          if (need) {  // FP32 where exact, else the double test (prefilter)
+            const uint32_t ix = w >> 16;
+            const int r = prefilter(penalty_f32((int64_t)a), cur_deltaf, A.tablef[ix]);
+            acc = r > 0 || (r < 0 && (double)a <= __dmul_rn(delta, A.table[ix]));
+          }
         }
         if (acc && de_smem) {
           dE2_t v;
@@ -1046,6 +1056,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     if (ctlB) flip_streak = kind == kFlip ? flip_streak + 1 : 0;
     cur_delta = nse.delta;
+    cur_deltaf = nse.deltaf;
     cur_lo = NARROW ? (pen_t)nse.lo32 : (pen_t)nse.lo;
     cur_hi = NARROW ? (pen_t)nse.hi32 : (pen_t)nse.hi;
     if (NORM_ON) {

@@ -41,6 +41,7 @@ constexpr int kNN = moda::kMaxN * moda::kMaxN;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static __device__ __align__(256) double g_table[moda::kTableSize];
+static __device__ __align__(256) float g_tablef[moda::kTableSize];
 static __device__ __align__(256) double g_sched_delta[kSchedMax];
 static __device__ __align__(256) int64_t g_sched_lo[kSchedMax];
 static __device__ __align__(256) int64_t g_sched_hi[kSchedMax];
@@ -52,6 +53,7 @@ struct DeviceSymbols {
   bool ready = false;
   unsigned char *scratch = nullptr;
   double *table = nullptr, *delta = nullptr;
+  float *tablef = nullptr;
   int64_t *lo = nullptr, *hi = nullptr;
   int32_t *fs1 = nullptr, *fs2 = nullptr, *d = nullptr;
   double tmin = 0, tmax = 0;
@@ -62,6 +64,7 @@ struct DeviceSymbols {
 std::mutex g_mutex;
 DeviceSymbols g_symbols[64];
 double h_table[moda::kTableSize];
+float h_tablef[moda::kTableSize];
 double h_delta[kSchedMax];
 int64_t h_lo[kSchedMax], h_hi[kSchedMax];
 int32_t h_fs1[kNN], h_fs2[kNN], h_d[kNN];
@@ -83,6 +86,7 @@ moda_status setup(int dev, DeviceSymbols **out) {
   if (!S.ready) {
     cudaError_t e = symbol(&S.scratch, g_scratch);
     if (e == cudaSuccess) e = symbol(&S.table, g_table);
+    if (e == cudaSuccess) e = symbol(&S.tablef, g_tablef);
     if (e == cudaSuccess) e = symbol(&S.delta, g_sched_delta);
     if (e == cudaSuccess) e = symbol(&S.lo, g_sched_lo);
     if (e == cudaSuccess) e = symbol(&S.hi, g_sched_hi);
@@ -93,7 +97,9 @@ moda_status setup(int dev, DeviceSymbols **out) {
       return nofail(MODA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     for (int idx = 0; idx < moda::kTableSize; ++idx)
       h_table[idx] = -std::log((static_cast<double>(idx) + 0.5) / 65536.0);
+    for (int idx = 0; idx < moda::kTableSize; ++idx) h_tablef[idx] = static_cast<float>(h_table[idx]);
     e = cudaMemcpy(S.table, h_table, sizeof(h_table), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(S.tablef, h_tablef, sizeof(h_tablef), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
       return nofail(MODA_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
     S.tmax = h_table[0];
@@ -308,6 +314,7 @@ extern "C" moda_status moda_anneal_noalloc(int32_t n, const int16_t *F1,
   a.sch_lo = S->lo;
   a.sch_hi = S->hi;
   a.table = S->table;
+  a.tablef = S->tablef;
   a.Fs1 = S->fs1;
   a.Fs2 = S->fs2;
   a.D = S->d;

@@ -323,9 +323,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // Copies into buffer b complete phases of mbarrier b in turn; every warp
   // tracks the parity of the next phase.  A copy whose data the team uses
   // is waited for by every warp (take_buf); one that is given up only by
-  // the leader, before that buffer is filled again (retire_buf).  A warp
-  // therefore never polls a phase that the barrier may already have left
-  // twice: after a take the buffer is refilled only one barrier later.
+  // the thread that fills that buffer again, before it does (retire_buf, or
+  // the stale wait of the prefetch issue).  Those waits come before the
+  // barrier that precedes any take of the new copy, so a warp never polls
+  // a phase that the barrier may already have left twice: after a take the
+  // buffer is refilled only one barrier later.
   auto take_buf = [&](int b) {
     const bool ok = mbar_wait(&sbar[b], (par >> b) & 1u);
     if (!__all_sync(kFull, ok)) fail = true;
@@ -436,7 +438,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
     // replica is in a run of flips.  At most LA + K + 1 buffers are held:
     // the state's and those of targets t .. t + K - 1 + LA.  Lane k
     // handles target issued_to + 1 + k; every warp keeps the same books,
-    // the leader warp's lanes start the copies.
+    // and warp k % G starts lane k's copy.
     if (LA > 0 && !(acount > 0 && flip_streak < 3)) {
       // no copies now: the targets get empty records
       const int nI = (int)(t + (uint32_t)(K - 1 + LA)) - (int)issued_to;
@@ -469,16 +471,18 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const uint32_t bm = __reduce_or_sync(kFull, b >= 0 ? 1u << b : 0u);  // buffers taken now
       freeb &= ~bm;
       const uint32_t stale = pend & bm;  // unused earlier copies still land there
+      // lane k's copy is started by warp k % G (the warps keep the same
+      // books), which first waits for an unused earlier copy into its
+      // buffer itself, so that the two cannot overlap
+      const bool issuer = lane % G == wt;
       if (stale) {
-        if (leader) {
-          bool ok = true;
-          if (b >= 0 && ((stale >> b) & 1u)) ok = mbar_wait(&sbar[b], (par >> b) & 1u);
-          if (!__all_sync(kFull, ok)) fail = true;
-        }
+        bool ok = true;
+        if (issuer && b >= 0 && ((stale >> b) & 1u)) ok = mbar_wait(&sbar[b], (par >> b) & 1u);
+        if (!__all_sync(kFull, ok)) fail = true;
         par ^= stale;
         pend &= ~stale;
       }
-      if (leader && b >= 0) {
+      if (issuer && b >= 0) {
         fence_proxy_async_shared();
         mbar_expect_tx(&sbar[b], rec.jr);
         bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);

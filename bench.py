@@ -51,8 +51,8 @@ KERNEL_FILES = {
 }
 KERNEL_TRAFFIC = {
     "anneal_kernel": {"workload": "P25", "bytes": None, "sha256": None},
-    "warp_anneal_kernel": {"workload": "P25", "bytes": 700750848 + 1878468096,
-                           "sha256": "63cd3b4f789f8aa422d26300cb500dc7a837b2ad9038e4b708c07222d4361352"},
+    "warp_anneal_kernel": {"workload": "P25", "bytes": 703444224 + 1880742144,
+                           "sha256": "ce9cec2aad81f7bea42f68754b07b8b87c70b4d28bbace9973c496157ce62ce4"},
 }
 
 

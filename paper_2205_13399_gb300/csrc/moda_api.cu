@@ -930,7 +930,7 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
         moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G, false, kw_try);
     *blocks = 0;
     if ((int64_t)L.total > optin) return false;
-    if (moda::warp_occupancy(narrow, G, L.total, blocks) != cudaSuccess || *blocks < 1)
+    if (moda::warp_occupancy(narrow, false, G, L.total, blocks) != cudaSuccess || *blocks < 1)
       return false;
     *out = L;
     return true;
@@ -979,11 +979,34 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
     const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true, kw);
     int blocks = 0;
     if ((int64_t)L.total <= optin &&
-        moda::warp_occupancy(narrow, best_w, L.total, &blocks) == cudaSuccess &&
+        moda::warp_occupancy(narrow, false, best_w, L.total, &blocks) == cudaSuccess &&
         (blocks >= best_blocks || (int64_t)blocks * sms >= items_total)) {
       sfields = true;
       best_blocks = blocks;
       sm = L;
+    }
+  }
+  // The frozen layout (once the schedule no longer changes a jump brings
+  // only the record's header): the longest window whose header buffers
+  // keep the residency, in the same shared memory, when it is longer than
+  // the window of full records.  (A window position with a candidate bit
+  // then reads that chunk's penalties from the record in global memory; on
+  // P25, whose full-record windows already reach 15, that cost 13 ms.)
+  int nbf = 0, laf = 0, kwf = 1;
+  for (const auto &o : kOpts) {
+    if (o[0] > la_max || o[1] <= kw) continue;
+    const int nb = o[0] + o[1] + 1;
+    const moda::WarpSmem L =
+        moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, sfields, kw, nb, o[1]);
+    int blocks = 0;
+    if ((int64_t)L.total <= optin &&
+        moda::warp_occupancy(narrow, true, best_w, L.total, &blocks) == cudaSuccess &&
+        blocks >= best_blocks) {
+      nbf = nb;
+      laf = o[0];
+      kwf = o[1];
+      sm = L;
+      break;
     }
   }
   const int64_t resident_teams = (int64_t)best_blocks * sms;
@@ -1064,6 +1087,9 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   L.sfields = sfields ? 1 : 0;
   L.window = kw;
   L.nbuf = la + kw + 1;
+  L.nbuf_f = nbf;
+  L.lookahead_f = laf;
+  L.window_f = kwf;
   L.team = best_w;
   L.counter = reinterpret_cast<int32_t *>(base + d_bytes + i_bytes);
   L.cache = static_cast<unsigned char *>(scratch->cache);
@@ -1478,7 +1504,7 @@ moda_status moda_anneal_batch(const moda_instance *insts, const moda_params *par
     }
     const void *func = nullptr;
     const size_t smem = (size_t)G.warps * G.L.sm.total;
-    if (e == cudaSuccess) e = moda::warp_function(G.narrow, G.L.team, smem, &func);
+    if (e == cudaSuccess) e = moda::warp_function(G.narrow, G.L.nbuf_f > 0, G.L.team, smem, &func);
     cudaGraphNode_t kn;
     if (e == cudaSuccess) {
       void *kargs[1] = {const_cast<moda::WarpLaunch *>(&G.L)};

@@ -172,7 +172,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
-// Inclusive prefix sum of `v` over the lanes.
 // The acceptance test of a bit whose penalty a (an integer >= 0) lies in
 // (lo_t, hi_t] is a <= fl(delta T) (R7).  This part's FP64 rate is low, so
 // it is first decided in FP32 where that is exact: with df = fl32(delta),
@@ -195,6 +194,7 @@ __device__ __forceinline__ int prefilter(float af, float df, float Tf) {
   return -1;
 }
 
+// Inclusive prefix sum of `v` over the lanes.
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {

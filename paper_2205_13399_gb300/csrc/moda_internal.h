@@ -241,25 +241,35 @@ constexpr int kWarpMaxLA = 14;  // prefetch distance (iterations ahead)
 
 // Records of one archive slot for a run of n, m (the field cache of the
 // warp annealer):
-//   jump record  a[mp] uint32 penalties, the state words [mp / 32], the row
-//                and column counts [2n] uint8 (16-byte padded), (E1, E2)
-//                int64 -- brought into shared memory by one bulk copy when
-//                the replica jumps to the slot;
+//   jump record  a[mp] uint32 penalties, the candidate masks [mp / 32],
+//                the state words [mp / 32], the row and column counts [2n]
+//                uint8 (16-byte padded), (E1, E2) int64 -- brought into
+//                shared memory by one bulk copy when the replica jumps to
+//                the slot (once the schedule is frozen, the header alone:
+//                the masks say which penalties can still be accepted);
 //   field record (L1, L2) int32 pairs [mp].
 // mp = 128 ceil(m / 128): bits past m carry a = 0xFFFFFFFF and no state.
 struct WarpRec {
   int32_t nc, mp;                        // chunks of 128 bits, padded bits
+  uint32_t off_cm;                       // candidate masks (the header starts here)
   uint32_t off_xw, off_rc, off_E, jr;    // jump-record offsets and bytes
+  uint32_t hb;                           // header bytes: jr - off_cm
   uint32_t lr;                           // field-record bytes
 };
+// Jump record: the penalties a(p) (uint32 each), then the header: per chunk
+// four 32-bit candidate masks (word j, bit l: bit 128 c + 4 l + j has
+// a <= hi of the frozen schedule), the state words, the row and column
+// counts and the energies.  Every part starts on a 16-byte boundary.
 __host__ __device__ inline WarpRec warp_rec(int n, int m) {
   WarpRec r;
   r.nc = (m + 127) / 128;
   r.mp = 128 * r.nc;
-  r.off_xw = 4u * (uint32_t)r.mp;
+  r.off_cm = 4u * (uint32_t)r.mp;
+  r.off_xw = r.off_cm + (uint32_t)(r.mp / 8);
   r.off_rc = r.off_xw + 4u * (uint32_t)(r.mp / 32);
   r.off_E = r.off_rc + (uint32_t)align_up((size_t)(2 * n), 16);
   r.jr = r.off_E + 16u;
+  r.hb = r.jr - r.off_cm;
   r.lr = 8u * (uint32_t)r.mp;
   return r;
 }
@@ -272,6 +282,7 @@ __host__ __device__ inline WarpRec warp_rec(int n, int m) {
 // flip and its copy of the row and column counts.
 struct WarpSmem {
   uint32_t jr;     // buffer stride
+  uint32_t scr, hbuf;  // frozen layout, from buf: rebuild scratch, header buffers
   uint32_t buf, mbar, ring, aE, cnt, fld, team;   // team part (bytes: team)
   uint32_t acc, rows, rc, pf, tbl, warp;          // warp part (bytes: warp)
   int32_t nc_max;
@@ -286,17 +297,26 @@ __host__ __device__ inline bool warp_stage(int m_max, int G) {
 }
 // sfields: the team part also holds the fields of the state a flip
 // reached (8 bytes per bit), so that flips following flips read them on chip.
+// nbuf_f > 0: the frozen layout's header buffers (window_f iterations), in
+// the same region: one full record, a rebuild scratch, nbuf_f headers.
 __host__ __device__ inline WarpSmem warp_smem(int n_max, int m_max, int se_max, int nbuf, int G,
-                                              bool sfields, int window) {
+                                              bool sfields, int window, int nbuf_f = 0,
+                                              int window_f = 1) {
   const WarpRec r = warp_rec(n_max, m_max);
   WarpSmem L;
   size_t o = 0;
   L.jr = r.jr;
   L.nc_max = r.nc;
-  L.pfr = nbuf <= 16 ? 16 : 32;  // holds targets t .. t + window - 1 + lookahead
-  L.cst = 8 * (window + 1);
-  L.buf = 0;                 o = align_up(o + (size_t)nbuf * r.jr, 16);
-  L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nbuf, 16);
+  const int nb_max = nbuf > nbuf_f ? nbuf : nbuf_f;
+  const int w_max = window > window_f ? window : window_f;
+  L.pfr = nb_max <= 16 ? 16 : 32;  // holds targets t .. t + window - 1 + lookahead
+  L.cst = 8 * (w_max + 1);
+  L.scr = r.jr;
+  L.hbuf = r.jr + (uint32_t)align_up(4 * (size_t)m_max, 16);
+  size_t region = (size_t)nbuf * r.jr;
+  if (nbuf_f > 0 && L.hbuf + (size_t)nbuf_f * r.hb > region) region = L.hbuf + (size_t)nbuf_f * r.hb;
+  L.buf = 0;                 o = align_up(o + region, 16);
+  L.mbar = (uint32_t)o;      o = align_up(o + 8 * (size_t)nb_max, 16);
   L.ring = (uint32_t)o;      o = align_up(o + 40 * (size_t)kWarpRing, 16);
   L.aE = (uint32_t)o;        o = align_up(o + 16 * (size_t)se_max, 16);
   // accepted counts of the warps by round parity [2][window positions +
@@ -352,6 +372,9 @@ struct WarpLaunch {
   const int2 *items;         // (run, replica row), largest runs first
   int32_t nitems;
   int32_t nbuf;              // jump-record buffers per team: lookahead + window + 1
+  // the frozen layout (nbuf_f > 0): header buffers, prefetch distance and
+  // window once the schedule no longer changes
+  int32_t nbuf_f, lookahead_f, window_f;
   int32_t lookahead;         // prefetch distance, 0 .. kWarpMaxLA
   int32_t team;              // G: warps per replica (1 .. 8)
   int32_t window;            // iterations tried together, 1 .. lookahead + 1
@@ -373,17 +396,18 @@ inline size_t warp_cache_bytes(int n, int m, int cslots) {
 // Launches the warp annealer: `grid` blocks of `teams` teams of L.team warps.
 cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
                         cudaStream_t stream);
-// The warp annealer's kernel (one WarpLaunch argument) for teams of `team`
+// The warp annealer's kernel (one WarpLaunch argument; fz: the variant with
+// the frozen layout, for launches with nbuf_f > 0) for teams of `team`
 // warps, for a CUDA graph node, with `smem` bytes of dynamic shared memory
 // allowed.
-cudaError_t warp_function(bool narrow, int team, size_t smem, const void **func);
+cudaError_t warp_function(bool narrow, bool fz, int team, size_t smem, const void **func);
 // The warp engine's acceptance decisions for `count` (penalty, delta, table
 // index) triples in device memory (moda_check_accept).
 cudaError_t launch_check_accept(const int64_t *a, const double *delta, const uint32_t *idx,
                                 int count, const double *T, const float *Tf, uint8_t *accept,
                                 int8_t *path, cudaStream_t stream);
-// Resident blocks (one team of `team` warps each) per SM.
-cudaError_t warp_occupancy(bool narrow, int team, size_t smem, int *blocks);
+// Resident blocks (one team of `team` warps each) per SM of that variant.
+cudaError_t warp_occupancy(bool narrow, bool fz, int team, size_t smem, int *blocks);
 
 // Sets the thread-local message that moda_last_error() returns.
 void set_last_error(const char *msg);

@@ -98,8 +98,9 @@ struct Team {
 // Runs replica `row` of run R on this team for all I_max iterations.
 // `par` holds the phase parity of the team's mbarriers across items (the
 // same in every warp).  Returns false when a bounded wait gave up (the
-// error word is set).
-template <bool NARROW>
+// error word is set).  FZ: the variant that carries the frozen layout
+// (without it every test of `frozen` folds away).
+template <bool NARROW, bool FZ>
 __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const WarpLaunch &Lc,
                          unsigned char *cache, uint32_t &par) {
   using WA = WarpAnnealer<NARROW>;
@@ -126,7 +127,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   const bool lenient = R.accept != 0;
   const bool exploit = R.archive != 0;
   const uint32_t magic = R.magic;
-  const int LA = Lc.lookahead, NB = Lc.nbuf;
+  // prefetch distance and buffers of the current layout (the frozen layout
+  // below has its own)
+  int LA = Lc.lookahead, NB = Lc.nbuf;
   const WarpSmem &SL = Lc.sm;
   const double *const table = R.table;
   const float *const tablef = R.tablef;
@@ -185,14 +188,33 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   int2 *gWork = gLR + (size_t)cslots * rec.mp;                            // [mp] working fields
   const int32_t *Fs1 = R.Fs1, *Fs2 = R.Fs2, *Dm = R.D;
 
-  auto bA = [&](int b) { return reinterpret_cast<uint32_t *>(sbuf + (size_t)b * SL.jr); };
-  auto bX = [&](int b) {
-    return reinterpret_cast<uint32_t *>(sbuf + (size_t)b * SL.jr + rec.off_xw);
+  // Frozen layout (from iteration nsched on, when the launch has one): the
+  // schedule no longer changes, so a jump record's candidate masks decide
+  // which of its penalties can still be accepted and a copy brings only the
+  // header.  The buffer region then holds one full record for the state a
+  // flip or a rebuild reached (buffer kFull_b), a rebuild's scratch
+  // (kScr_b) and Lc.nbuf_f header buffers.
+  constexpr int kFull_b = 31, kScr_b = 30;
+  const bool fz_on = FZ && Lc.nbuf_f > 0;
+  bool frozen = false;
+  auto base = [&](int b) -> unsigned char * {
+    if (!frozen) return sbuf + (size_t)b * SL.jr;
+    if (b == kFull_b) return sbuf;
+    if (b == kScr_b) return sbuf + SL.scr;
+    return sbuf + SL.hbuf + (size_t)b * rec.hb - rec.off_cm;  // header at base + off_cm
   };
-  auto bRC = [&](int b) { return sbuf + (size_t)b * SL.jr + rec.off_rc; };
-  auto bE = [&](int b) {
-    return reinterpret_cast<int64_t *>(sbuf + (size_t)b * SL.jr + rec.off_E);
-  };
+  // penalties: only a full record (normal layout, or kFull_b / kScr_b)
+  auto bA = [&](int b) { return reinterpret_cast<uint32_t *>(base(b)); };
+  auto bCM = [&](int b) { return reinterpret_cast<const uint4 *>(base(b) + rec.off_cm); };
+  auto bX = [&](int b) { return reinterpret_cast<uint32_t *>(base(b) + rec.off_xw); };
+  auto bRC = [&](int b) { return base(b) + rec.off_rc; };
+  auto bE = [&](int b) { return reinterpret_cast<int64_t *>(base(b) + rec.off_E); };
+  // a buffer of header only (its penalties are read from the record)
+  auto hdr_only = [&](int b) { return frozen && b != kFull_b; };
+  // the frozen schedule's hi: masks mark a(p) <= it (saturated penalties
+  // too when it reaches 2^32 - 1)
+  const int64_t hiF = R.sch_hi[nsched - 1];
+  const uint32_t hiF32 = hiF < 0xFFFFFFFFll ? (uint32_t)hiF : 0xFFFFFFFFu;
   auto divn = [&](int p) { return (int)__umulhi((uint32_t)p, magic); };
 
   // Iterations first .. first + 31 into the ring (one warp): schedule
@@ -322,12 +344,15 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   bool fail = false;
   // Copies into buffer b complete phases of mbarrier b in turn; every warp
   // tracks the parity of the next phase.  A copy whose data the team uses
-  // is waited for by every warp (take_buf); one that is given up only by
-  // the thread that fills that buffer again, before it does (retire_buf, or
-  // the stale wait of the prefetch issue).  Those waits come before the
-  // barrier that precedes any take of the new copy, so a warp never polls
-  // a phase that the barrier may already have left twice: after a take the
-  // buffer is refilled only one barrier later.
+  // is waited for by every warp (take_buf).  One that is given up is
+  // waited for by the thread that fills that buffer again, before it does
+  // (the stale wait of the prefetch issue; retire_buf when the item ends),
+  // and a barrier separates that wait from any take of the new copy; where
+  // the new copy is taken at once (a jump to a member without a prefetched
+  // record), every warp waits for the old copy and then for a barrier.  So
+  // no warp polls a phase whose predecessor is still open, nor one that the
+  // barrier may already have left twice: after a take the buffer is
+  // refilled only one barrier later.
   auto take_buf = [&](int b) {
     const bool ok = mbar_wait(&sbar[b], (par >> b) & 1u);
     if (!__all_sync(kFull, ok)) fail = true;
@@ -344,8 +369,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   auto copy_record = [&](int b, int y) {
     if (leader && lane == 0) {
       fence_proxy_async_shared();
-      mbar_expect_tx(&sbar[b], rec.jr);
-      bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)y * rec.jr, rec.jr, &sbar[b]);
+      if (frozen) {
+        mbar_expect_tx(&sbar[b], rec.hb);
+        bulk_g2s(base(b) + rec.off_cm, gJR + (size_t)y * rec.jr + rec.off_cm, rec.hb, &sbar[b]);
+      } else {
+        mbar_expect_tx(&sbar[b], rec.jr);
+        bulk_g2s(base(b), gJR + (size_t)y * rec.jr, rec.jr, &sbar[b]);
+      }
     }
   };
 
@@ -353,6 +383,9 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // Chunk c's 128 bits are the four words of Philox block (c, 0, replica,
   // init): state word 4c + w is word w.
   int cur = 0;
+  // the archive slot whose record the state's buffer holds (-1: the buffer
+  // holds a full record), for a header-only buffer's penalties
+  int cur_slot = -1;
   {
     uint32_t *x0 = bX(0);
     for (int c = c0 + lane; c < c1; c += 32) {
@@ -412,7 +445,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   // first iteration of the window that accepts a bit flips (the window's
   // earlier iterations were jumps, as assumed), and the trials after it
   // are discarded; a window without an accepted bit commits K jumps.
-  const int KW = Lc.window;
+  int KW = Lc.window;
   uint32_t filled = 64;  // the ring holds the iterations up to `filled`
   // Every target iteration tau gets one record sPf[tau & 15], a copy or
   // none, written once, in the round that first reaches it; records up to
@@ -425,6 +458,33 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         fill(filled + 1u);
         filled += 32u;
       }
+    if (fz_on && !frozen && t >= nsched) {
+      // ---- the schedule is frozen from iteration t on: the copies in
+      // flight land, the state's record moves to kFull_b, and jumps bring
+      // headers into the frozen layout's buffers from now on
+      bool ok = true;
+      if ((pend >> lane) & 1u) ok = mbar_wait(&sbar[lane], (par >> lane) & 1u);
+      if (!__all_sync(kFull, ok)) fail = true;
+      par ^= pend;
+      pend = 0u;
+      sync();  // every warp is done with the old buffers
+      if (cur != 0) {  // kFull_b is where buffer 0 was
+        const int4 *src = reinterpret_cast<const int4 *>(sbuf + (size_t)cur * SL.jr);
+        int4 *dst = reinterpret_cast<int4 *>(sbuf);
+        for (int i = wt * 32 + lane; i < (int)(rec.jr / 16); i += team_threads) dst[i] = src[i];
+      }
+      frozen = true;
+      cur = kFull_b;
+      cur_slot = -1;
+      LA = Lc.lookahead_f;
+      KW = Lc.window_f;
+      NB = Lc.nbuf_f;
+      freeb = (1u << NB) - 1u;
+      if (lane < SL.pfr) sPf[lane] = make_int4(-1, 0, 0, 0);
+      __syncwarp();
+      issued_to = t - 1u;
+      sync();  // the record has moved before anyone reads it
+    }
     if (unfenced) {
       fence_proxy_async_global();
       unfenced = false;
@@ -484,8 +544,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       }
       if (issuer && b >= 0) {
         fence_proxy_async_shared();
-        mbar_expect_tx(&sbar[b], rec.jr);
-        bulk_g2s(sbuf + (size_t)b * SL.jr, gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
+        if (frozen) {  // the header: masks, state, counts, energies
+          mbar_expect_tx(&sbar[b], rec.hb);
+          bulk_g2s(base(b) + rec.off_cm, gJR + (size_t)sp * rec.jr + rec.off_cm, rec.hb,
+                   &sbar[b]);
+        } else {
+          mbar_expect_tx(&sbar[b], rec.jr);
+          bulk_g2s(base(b), gJR + (size_t)sp * rec.jr, rec.jr, &sbar[b]);
+        }
       }
       pend |= bm;
       if (lane < nI) sPf[tt & pfm] = make_int4(b, b >= 0 ? sp : 0, (int)t, 0);
@@ -560,8 +626,13 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             const int sbk = __shfl_sync(kFull, sbl, k);
             const uint32_t h32 = __shfl_sync(kFull, hl, k);
             if (k < Keff) {
-              const uint4 a4 = reinterpret_cast<const uint4 *>(bA(sbk))[c * 32 + lane];
-              cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+              if (hdr_only(sbk)) {  // the chunk's candidate masks
+                const uint4 cm = bCM(sbk)[c];
+                cand |= (cm.x | cm.y | cm.z | cm.w) != 0u;
+              } else {
+                const uint4 a4 = reinterpret_cast<const uint4 *>(bA(sbk))[c * 32 + lane];
+                cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+              }
             }
           }
         }
@@ -571,11 +642,20 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
           if (k >= Keff) break;  // Keff is the same in every lane
           const int sbk = __shfl_sync(kFull, sbl, k);
           const uint32_t h32 = __shfl_sync(kFull, hl, k);
-          const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
+          if (hdr_only(sbk)) {  // the chunks' candidate masks
+            const uint4 *cmp = bCM(sbk);
 #pragma unroll 4
-          for (int c = c0; c < c1; ++c) {
-            const uint4 a4 = ap[c * 32 + lane];
-            cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+            for (int c = c0; c < c1; ++c) {
+              const uint4 cm = cmp[c];
+              cand |= (cm.x | cm.y | cm.z | cm.w) != 0u;
+            }
+          } else {
+            const uint4 *ap = reinterpret_cast<const uint4 *>(bA(sbk));
+#pragma unroll 4
+            for (int c = c0; c < c1; ++c) {
+              const uint4 a4 = ap[c * 32 + lane];
+              cand |= min(min(a4.x, a4.y), min(a4.z, a4.w)) <= h32;
+            }
           }
         }
       }
@@ -705,19 +785,28 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const int64_t lo = e.lo, hi = e.hi;
       const uint32_t hi32 = hi < 0xFFFFFFFFll ? (uint32_t)hi : 0xFFFFFFFFu;
       const uint32_t lo32 = lo < 0xFFFFFFFFll ? (uint32_t)lo : 0xFFFFFFFFu;
-      int sb = cur;
+      int sb = cur, slot_k = cur_slot;
       const int2 *Lk = curL;
       const unsigned char *rck = rc_stale ? bRC(cur) : rcp;
       if (k > 0) {
         const int4 pr = sPf[(tk - 1u) & pfm];
         sb = pr.x;
+        slot_k = pr.y;
         Lk = gLR + (size_t)pr.y * rec.mp;
         rck = bRC(sb);
       }
-      const uint4 *a4p = reinterpret_cast<const uint4 *>(bA(sb));
+      // a header-only buffer: chunks with a candidate read their penalties
+      // from the slot's record
+      const bool ho = hdr_only(sb);
+      const uint4 *a4p = ho ? reinterpret_cast<const uint4 *>(gJR + (size_t)slot_k * rec.jr)
+                            : reinterpret_cast<const uint4 *>(bA(sb));
       int cnt_w = 0;
 #pragma unroll 4
       for (int c = c0; c < c1; ++c) {
+        if (ho) {
+          const uint4 cm = bCM(sb)[c];
+          if ((cm.x | cm.y | cm.z | cm.w) == 0u) continue;  // no bit of the chunk can be accepted
+        }
         const uint4 a4 = a4p[c * 32 + lane];
         const uint32_t amin = min(min(a4.x, a4.y), min(a4.z, a4.w));
         if (__any_sync(kFull, amin <= hi32)) {
@@ -833,12 +922,17 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             tr[1] = be[1];
             tr[2] = -1 - (int64_t)pr.y;
           }
+        // (the records read for the trace are given up just below, and a
+        // faster warp may refill them in its next round: the trace is
+        // written first)
+        if (trace != nullptr && ns > 0) sync();
         if (ns > 0) {
           const int pb = lane + 1 < ns ? sPf[(t + (uint32_t)lane) & pfm].x : -1;
           freeb |= __reduce_or_sync(kFull, pb >= 0 ? 1u << pb : 0u);  // passed through
-          freeb |= 1u << cur;
+          if (cur != kFull_b) freeb |= 1u << cur;
           const int4 pr = sPf[(t + (uint32_t)(ns - 1)) & pfm];
           cur = pr.x;
+          cur_slot = pr.y;
           curL = gLR + (size_t)pr.y * rec.mp;
           const int64_t *be = bE(cur);
           E1 = be[0];
@@ -860,30 +954,41 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
             ++npref;
           } else {
             if (pr.x >= 0) freeb |= 1u << pr.x;
-            nbuf = __ffs(freeb) - 1;
-            freeb &= ~(1u << nbuf);
-            if ((pend >> nbuf) & 1u) {
-              retire_buf(nbuf);
-              pend &= ~(1u << nbuf);
+            if (frozen && slot >= cslots) {
+              nbuf = kFull_b;  // a rebuild needs a full record
+            } else {
+              nbuf = __ffs(freeb) - 1;
+              freeb &= ~(1u << nbuf);
+              if ((pend >> nbuf) & 1u) {
+                // an unused earlier copy still lands there: every warp
+                // waits for it and the barrier orders that before the new
+                // copy, which every warp then waits for in turn (a warp
+                // must not poll the new copy's phase while the old one is
+                // still open)
+                take_buf(nbuf);
+                pend &= ~(1u << nbuf);
+                sync();
+              }
             }
             if (slot < cslots) {
               copy_record(nbuf, slot);
               take_buf(nbuf);
             } else {
               // no records for this slot: rebuild from its state (the old
-              // state's buffer is the scratch)
+              // state's buffer is the scratch; kScr_b when frozen)
               uint32_t *xn = bX(nbuf);
               for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32)
                 xn[q2] = q2 < W ? gB[(size_t)slot * W + q2] : 0u;
               sync();
               int64_t t1, t2, gp;
-              rebuild(nbuf, cur, gWork, t1, t2, gp);  // also this warp's counts
+              rebuild(nbuf, frozen ? kScr_b : cur, gWork, t1, t2, gp);  // also this warp's counts
               ++nrebuild;
             }
             ++ndirect;
           }
-          freeb |= 1u << cur;
+          if (cur != kFull_b) freeb |= 1u << cur;
           cur = nbuf;
+          cur_slot = slot < cslots ? slot : -1;
           if (slot < cslots) {
             curL = gLR + (size_t)slot * rec.mp;
             const int64_t *be = bE(cur);
@@ -1037,6 +1142,16 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       const int64_t hps = (int64_t)rcp[j] + (int64_t)rcp[n + v] - 1 - 2 * xps;
       const int64_t nE1 = E1 + (int64_t)sgn * ((int64_t)Lp.x + w1l * hps);
       const int64_t nE2 = E2 + (int64_t)sgn * ((int64_t)Lp.y + w2l * hps);
+      // frozen layout, state in a header buffer: the flip's state is built
+      // in kFull_b, starting from this warp's state words (the header
+      // buffer is read no more once every warp passes the next barrier)
+      const int fdst = frozen && cur != kFull_b ? kFull_b : cur;
+      if (fdst != cur) {
+        uint32_t *xd = bX(fdst);
+        for (int q2 = 4 * c0 + lane; q2 < 4 * c1; q2 += 32) xd[q2] = xw[q2];
+        __syncwarp();
+        xw = xd;
+      }
 
       // ---- archive update: Alg. 4 (explore) or Alg. 5 (exploit), decided
       // the same way by every warp of the team
@@ -1127,7 +1242,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
       int2 *dstL = use_sf ? sF : cached ? slotL : gWork;
       unsigned char *jrec = cached ? gJR + (size_t)target * rec.jr : nullptr;
       uint4 *dA = reinterpret_cast<uint4 *>(jrec);
-      uint4 *sa4 = reinterpret_cast<uint4 *>(bA(cur));
+      uint4 *sa4 = reinterpret_cast<uint4 *>(bA(fdst));
       int c_next = c0;
       for (int cc = c0; cc < c1; ++cc) {
         const int p0 = cc * 128 + lane * 4;
@@ -1181,6 +1296,14 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         const uint4 a4n = make_uint4(an[0], an[1], an[2], an[3]);
         sa4[cc * 32 + lane] = a4n;
         if (cached) dA[cc * 32 + lane] = a4n;
+        if (FZ && cached) {
+          // the record's candidate masks for the frozen schedule
+          const uint32_t m0 = __ballot_sync(kFull, an[0] <= hiF32),
+                         m1 = __ballot_sync(kFull, an[1] <= hiF32),
+                         m2 = __ballot_sync(kFull, an[2] <= hiF32),
+                         m3 = __ballot_sync(kFull, an[3] <= hiF32);
+          if (lane == 0) reinterpret_cast<uint4 *>(jrec + rec.off_cm)[cc] = make_uint4(m0, m1, m2, m3);
+        }
       }
       // this warp's state words of x' (bit ps toggled) into the archive
       const int qps = ps >> 5;
@@ -1214,6 +1337,11 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
         }
       }
       if (cached) unfenced = true;  // fenced before the next bulk copy
+      if (fdst != cur) {  // the header buffer is free again
+        freeb |= 1u << cur;
+        cur = fdst;
+      }
+      cur_slot = -1;
       curL = dstL;
       E1 = nE1;
       E2 = nE2;
@@ -1231,7 +1359,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
   }
   // no copy may be in flight when the item ends
   cp_async_wait_all();
-  for (int b = 0; b < NB; ++b)
+  for (int b = 0; b < 32; ++b)
     if ((pend >> b) & 1u) retire_buf(b);
   fail = sync_or(fail);
   if (fail) {
@@ -1262,7 +1390,7 @@ __device__ bool team_run(const WarpRun &R, const int row, const Team &T, const W
 // The register allocation is sized for one block per SM: no register
 // spills (their local-memory reads missed L1 and sat on every iteration's
 // chain), at the cost of resident warps.
-template <bool NARROW>
+template <bool NARROW, bool FZ>
 __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1279,7 +1407,8 @@ __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L)
   int32_t *sItem = reinterpret_cast<int32_t *>(T.ts + L.sm.cnt + 8 * L.sm.cst);
   const bool leader = T.wt == 0;
   if (leader && lane == 0) {
-    for (int b = 0; b < L.nbuf; ++b) mbar_init(&bar[b], 1);
+    const int nbar = L.nbuf > L.nbuf_f ? L.nbuf : L.nbuf_f;
+    for (int b = 0; b < nbar; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   if (G > 1) team_sync(T.bar, 32 * G);
@@ -1300,7 +1429,7 @@ __global__ void __launch_bounds__(256, 1) warp_anneal_kernel(const WarpLaunch L)
       if (leader && lane == 0) atomicExch(R.error, kErrVariant);
       continue;
     }
-    if (!team_run<NARROW>(R, item.y, T, L, cache, par)) break;
+    if (!team_run<NARROW, FZ>(R, item.y, T, L, cache, par)) break;
   }
 }
 
@@ -1324,9 +1453,12 @@ __global__ void check_accept_kernel(const int64_t *a, const double *delta, const
 }
 
 // The kernel variant of a launch: narrow or not.
-const void *warp_kernel(bool narrow, int) {
-  return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true>)
-                : reinterpret_cast<const void *>(warp_anneal_kernel<false>);
+const void *warp_kernel(bool narrow, bool fz) {
+  if (fz)
+    return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, true>)
+                  : reinterpret_cast<const void *>(warp_anneal_kernel<false, true>);
+  return narrow ? reinterpret_cast<const void *>(warp_anneal_kernel<true, false>)
+                : reinterpret_cast<const void *>(warp_anneal_kernel<false, false>);
 }
 }  // namespace
 
@@ -1336,7 +1468,7 @@ cudaError_t launch_warp(const WarpLaunch &L, bool narrow, int grid, int teams,
   if (L.team < 1 || L.team > 8 || teams < 1 || warps > 8 || teams > 15 || grid < 1)
     return cudaErrorInvalidValue;
   const size_t smem = (size_t)teams * L.sm.total;
-  const void *f = warp_kernel(narrow, L.team);
+  const void *f = warp_kernel(narrow, L.nbuf_f > 0);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void *args[1] = {const_cast<WarpLaunch *>(&L)};
@@ -1354,15 +1486,16 @@ cudaError_t launch_check_accept(const int64_t *a, const double *delta, const uin
   return cudaGetLastError();
 }
 
-cudaError_t warp_function(bool narrow, int team, size_t smem, const void **func) {
-  const void *f = warp_kernel(narrow, team);
+cudaError_t warp_function(bool narrow, bool fz, int team, size_t smem, const void **func) {
+  (void)team;
+  const void *f = warp_kernel(narrow, fz);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) *func = f;
   return e;
 }
 
-cudaError_t warp_occupancy(bool narrow, int team, size_t smem, int *blocks) {
-  const void *f = warp_kernel(narrow, team);
+cudaError_t warp_occupancy(bool narrow, bool fz, int team, size_t smem, int *blocks) {
+  const void *f = warp_kernel(narrow, fz);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, 32 * team, smem);

@@ -51,8 +51,8 @@ KERNEL_FILES = {
 }
 KERNEL_TRAFFIC = {
     "anneal_kernel": {"workload": "P25", "bytes": None, "sha256": None},
-    "warp_anneal_kernel": {"workload": "P25", "bytes": 703444224 + 1880742144,
-                           "sha256": "ce9cec2aad81f7bea42f68754b07b8b87c70b4d28bbace9973c496157ce62ce4"},
+    "warp_anneal_kernel": {"workload": "P25", "bytes": 1052635392 + 1924999424,
+                           "sha256": "53a5ceb321a40b0fe68edded14958ce48972a2441468e5ad548d69a129d1f59b"},
 }
 
 

@@ -108,8 +108,10 @@ typedef struct {
                             free device memory), 1 on (MODA_EUNSUPPORTED if it
                             does not fit), 2 off.  Results are identical. */
   int32_t prefetch;      /* field-cache prefetch distance: 0 auto, k in 1..4
-                            copies a jump's target k - 1 iterations ahead
-                            (MODA_EUNSUPPORTED if it does not fit). */
+                            (block engine; 1..15 for the warp engine, see
+                            `engine`) copies a jump's target k - 1
+                            iterations ahead (MODA_EUNSUPPORTED if it does
+                            not fit). */
   int32_t normalize;     /* 1: QUBO normalisation of Sec. 4.2 -- each
                             objective's largest cost-QUBO coefficient set to
                             2^23 -- applied where it acts: the acceptance

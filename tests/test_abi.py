@@ -166,6 +166,28 @@ def test_kernel_variant_choice(tmp_path):
     assert res.returncode == 0, res.stdout
 
 
+def test_warp_layouts(tmp_path):
+    """The warp engine's jump-record and shared-memory layouts, for every n
+    and every buffer count the planner can choose: each part a bulk copy
+    moves starts on a 16-byte boundary with a multiple of 16 bytes, the
+    frozen-schedule layout stays inside the buffer region, and no parts
+    overlap (a host-only C++ check against the library's internal
+    header)."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if gxx is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    here = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(os.path.dirname(here), "paper_2205_13399_gb300", "csrc")
+    exe = str(tmp_path / "warp_layout_check")
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", csrc, "-I", cuda_inc,
+                    os.path.join(here, "warp_layout_check.cc"), "-o", exe], check=True)
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout
+
+
 def test_check_accept_rejects_bad_arguments():
     """moda_check_accept validates every input before any device work."""
     from paper_2205_13399_gb300 import moda

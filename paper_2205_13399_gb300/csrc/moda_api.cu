@@ -2,6 +2,7 @@
 // upload, the cooling schedule with its integer acceptance thresholds, the
 // -ln(u) table, run buffers, launch, wait and result read-back.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -916,98 +917,133 @@ moda_status plan_warp_group(std::vector<moda_run> &runs, std::vector<Prepared> &
   // iterations; when even single warps cannot hold them all, single warps
   // (the most replicas in flight).  The on-chip archive energies shrink if
   // nothing fits.
-  int best_w = 0, best_blocks = 0, se_max = std::min(s_max, kWarpSmemEnergies);
-  const int nc_max = (m_max + 127) / 128;
+  // The launch shape depends only on these; the server and batches plan
+  // the same shapes again and again, so the occupancy queries run once per
+  // shape and device (a plan is a pure function of the key).
   const int la_max = la;
-  moda::WarpSmem sm{};
-  // (lookahead, window) pairs, preferred first; la + window + 1 buffers
-  static const int kOpts[][2] = {{14, 15}, {10, 11}, {8, 9}, {6, 7}, {5, 6}, {4, 5},
-                                 {3, 4}, {2, 3}, {1, 2}, {2, 1}, {1, 1}, {0, 1}};
-  int kw = 1;
-  auto resident = [&](int G, int la_try, int kw_try, int se_try, int *blocks,
-                      moda::WarpSmem *out) {
-    const moda::WarpSmem L =
-        moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G, false, kw_try);
-    *blocks = 0;
-    if ((int64_t)L.total > optin) return false;
-    if (moda::warp_occupancy(narrow, false, G, L.total, blocks) != cudaSuccess || *blocks < 1)
-      return false;
-    *out = L;
-    return true;
-  };
   // params.block_threads = 32 G prescribes the team size
   const int forced = r0->prm.block_threads / 32;
-  // (a shorter on-chip archive-energy list is traded for buffers)
-  const int se_opts[2] = {se_max, std::min(se_max, 128)};
-  for (int gsz = forced > 0 ? forced : std::min(8, nc_max); gsz >= 1 && best_w == 0; --gsz)
-    for (const auto &o : kOpts)
-      for (int se_try : se_opts) {
-        if (o[0] > la_max || best_w != 0) continue;
+  int best_w = 0, best_blocks = 0, se_max = std::min(s_max, kWarpSmemEnergies);
+  moda::WarpSmem sm{};
+  int kw = 1;
+  bool sfields = false;
+  int nbf = 0, laf = 0, kwf = 1;
+  struct Shape {
+    int best_w, best_blocks, la, kw, se_max, nbf, laf, kwf;
+    bool sfields;
+    moda::WarpSmem sm;
+  };
+  static std::mutex shape_mu;
+  static std::map<std::array<int64_t, 8>, Shape> shapes;
+  const std::array<int64_t, 8> key = {dev, narrow ? 1 : 0, n_max, m_max, s_max, items_total,
+                                      la_max, forced};
+  bool known = false;
+  {
+    std::lock_guard<std::mutex> lk(shape_mu);
+    auto it = shapes.find(key);
+    if (it != shapes.end()) {
+      const Shape &sh = it->second;
+      best_w = sh.best_w;
+      best_blocks = sh.best_blocks;
+      la = sh.la;
+      kw = sh.kw;
+      se_max = sh.se_max;
+      nbf = sh.nbf;
+      laf = sh.laf;
+      kwf = sh.kwf;
+      sfields = sh.sfields;
+      sm = sh.sm;
+      known = true;
+    }
+  }
+  if (!known) {
+    const int nc_max = (m_max + 127) / 128;
+    // (lookahead, window) pairs, preferred first; la + window + 1 buffers
+    static const int kOpts[][2] = {{14, 15}, {10, 11}, {8, 9}, {6, 7}, {5, 6}, {4, 5},
+                                   {3, 4}, {2, 3}, {1, 2}, {2, 1}, {1, 1}, {0, 1}};
+    auto resident = [&](int G, int la_try, int kw_try, int se_try, int *blocks,
+                        moda::WarpSmem *out) {
+      const moda::WarpSmem L =
+          moda::warp_smem(n_max, m_max, se_try, la_try + kw_try + 1, G, false, kw_try);
+      *blocks = 0;
+      if ((int64_t)L.total > optin) return false;
+      if (moda::warp_occupancy(narrow, false, G, L.total, blocks) != cudaSuccess || *blocks < 1)
+        return false;
+      *out = L;
+      return true;
+    };
+    // (a shorter on-chip archive-energy list is traded for buffers)
+    const int se_opts[2] = {se_max, std::min(se_max, 128)};
+    for (int gsz = forced > 0 ? forced : std::min(8, nc_max); gsz >= 1 && best_w == 0; --gsz)
+      for (const auto &o : kOpts)
+        for (int se_try : se_opts) {
+          if (o[0] > la_max || best_w != 0) continue;
+          int blocks = 0;
+          moda::WarpSmem L{};
+          if (resident(gsz, o[0], o[1], se_try, &blocks, &L) &&
+              ((int64_t)blocks * sms >= items_total || forced > 0)) {
+            best_w = gsz;
+            best_blocks = blocks;
+            la = o[0];
+            kw = o[1];
+            sm = L;
+            se_max = se_try;
+          }
+        }
+    for (int attempt = 0; attempt < 2 && best_w == 0; ++attempt) {
+      // throughput: single warps, the most resident (then the larger window)
+      for (const auto &o : kOpts) {
+        if (o[0] > la_max) continue;
         int blocks = 0;
         moda::WarpSmem L{};
-        if (resident(gsz, o[0], o[1], se_try, &blocks, &L) &&
-            ((int64_t)blocks * sms >= items_total || forced > 0)) {
-          best_w = gsz;
+        if (resident(1, o[0], o[1], se_max, &blocks, &L) && blocks > best_blocks) {
+          best_w = 1;
           best_blocks = blocks;
           la = o[0];
           kw = o[1];
           sm = L;
-          se_max = se_try;
         }
       }
-  for (int attempt = 0; attempt < 2 && best_w == 0; ++attempt) {
-    // throughput: single warps, the most resident (then the larger window)
-    for (const auto &o : kOpts) {
-      if (o[0] > la_max) continue;
+      if (best_w == 0) se_max = std::min(se_max, 64);
+    }
+    if (best_w == 0) return fail(MODA_EUNSUPPORTED, "warp engine: shared memory need exceeds the device");
+    // The fields of a flip's state on chip too, where that keeps the
+    // residency (as many teams, or still every replica, per launch).
+    {
+      const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true, kw);
       int blocks = 0;
-      moda::WarpSmem L{};
-      if (resident(1, o[0], o[1], se_max, &blocks, &L) && blocks > best_blocks) {
-        best_w = 1;
+      if ((int64_t)L.total <= optin &&
+          moda::warp_occupancy(narrow, false, best_w, L.total, &blocks) == cudaSuccess &&
+          (blocks >= best_blocks || (int64_t)blocks * sms >= items_total)) {
+        sfields = true;
         best_blocks = blocks;
-        la = o[0];
-        kw = o[1];
         sm = L;
       }
     }
-    if (best_w == 0) se_max = std::min(se_max, 64);
-  }
-  if (best_w == 0) return fail(MODA_EUNSUPPORTED, "warp engine: shared memory need exceeds the device");
-  // The fields of a flip's state on chip too, where that keeps the
-  // residency (as many teams, or still every replica, per launch).
-  bool sfields = false;
-  {
-    const moda::WarpSmem L = moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, true, kw);
-    int blocks = 0;
-    if ((int64_t)L.total <= optin &&
-        moda::warp_occupancy(narrow, false, best_w, L.total, &blocks) == cudaSuccess &&
-        (blocks >= best_blocks || (int64_t)blocks * sms >= items_total)) {
-      sfields = true;
-      best_blocks = blocks;
-      sm = L;
+    // The frozen layout (once the schedule no longer changes a jump brings
+    // only the record's header): the longest window whose header buffers
+    // keep the residency, in the same shared memory, when it is longer than
+    // the window of full records.  (A window position with a candidate bit
+    // then reads that chunk's penalties from the record in global memory; on
+    // P25, whose full-record windows already reach 15, that cost 13 ms.)
+    for (const auto &o : kOpts) {
+      if (o[0] > la_max || o[1] <= kw) continue;
+      const int nb = o[0] + o[1] + 1;
+      const moda::WarpSmem L =
+          moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, sfields, kw, nb, o[1]);
+      int blocks = 0;
+      if ((int64_t)L.total <= optin &&
+          moda::warp_occupancy(narrow, true, best_w, L.total, &blocks) == cudaSuccess &&
+          blocks >= best_blocks) {
+        nbf = nb;
+        laf = o[0];
+        kwf = o[1];
+        sm = L;
+        break;
+      }
     }
-  }
-  // The frozen layout (once the schedule no longer changes a jump brings
-  // only the record's header): the longest window whose header buffers
-  // keep the residency, in the same shared memory, when it is longer than
-  // the window of full records.  (A window position with a candidate bit
-  // then reads that chunk's penalties from the record in global memory; on
-  // P25, whose full-record windows already reach 15, that cost 13 ms.)
-  int nbf = 0, laf = 0, kwf = 1;
-  for (const auto &o : kOpts) {
-    if (o[0] > la_max || o[1] <= kw) continue;
-    const int nb = o[0] + o[1] + 1;
-    const moda::WarpSmem L =
-        moda::warp_smem(n_max, m_max, se_max, la + kw + 1, best_w, sfields, kw, nb, o[1]);
-    int blocks = 0;
-    if ((int64_t)L.total <= optin &&
-        moda::warp_occupancy(narrow, true, best_w, L.total, &blocks) == cudaSuccess &&
-        blocks >= best_blocks) {
-      nbf = nb;
-      laf = o[0];
-      kwf = o[1];
-      sm = L;
-      break;
-    }
+    std::lock_guard<std::mutex> lk(shape_mu);
+    shapes[key] = Shape{best_w, best_blocks, la, kw, se_max, nbf, laf, kwf, sfields, sm};
   }
   const int64_t resident_teams = (int64_t)best_blocks * sms;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_teams, items_total));

@@ -197,6 +197,10 @@ typedef struct {
 moda_status moda_create_instance(int32_t n, const int16_t *F1,
                                  const int16_t *F2, const int16_t *D,
                                  const moda_penalty *pen, moda_instance *out);
+/* Frees the instance's host and device memory, stream-ordered and without
+ * synchronising the device.  Destroy an instance only after every run that
+ * uses it has been destroyed (moda_destroy_run waits for its run) or has
+ * finished. */
 void moda_destroy_instance(moda_instance inst);
 /* n and the penalty weights w1, w2 of an instance (any pointer may be
  * NULL). */

@@ -430,16 +430,24 @@ moda_status finish_instance(moda_instance inst, const moda_penalty *pen, moda_in
   inst->b1 = b1;
   inst->b2 = b2;
   cudaGetDevice(&inst->device);
+  // One stream-ordered allocation on the library's own stream, and the
+  // uploads on it too: neither waits for work in flight elsewhere on the
+  // device (a server creates an instance per request while others run).
   const size_t bytes = sizeof(int32_t) * nn;
-  cudaError_t e = cudaMalloc(&inst->dFs1, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&inst->dFs2, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&inst->dD, bytes);
+  cudaStream_t fs = free_stream(inst->device);
+  void *base = nullptr;
+  cudaError_t e = cudaMallocAsync(&base, 3 * bytes, fs);
+  if (e == cudaSuccess) {
+    inst->dFs1 = static_cast<int32_t *>(base);
+    inst->dFs2 = inst->dFs1 + nn;
+    inst->dD = inst->dFs2 + nn;
+    e = cudaMemcpyAsync(inst->dFs1, inst->Fs1.data(), bytes, cudaMemcpyHostToDevice, fs);
+  }
   if (e == cudaSuccess)
-    e = cudaMemcpy(inst->dFs1, inst->Fs1.data(), bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(inst->dFs2, inst->Fs2.data(), bytes, cudaMemcpyHostToDevice, fs);
   if (e == cudaSuccess)
-    e = cudaMemcpy(inst->dFs2, inst->Fs2.data(), bytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(inst->dD, inst->D.data(), bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(inst->dD, inst->D.data(), bytes, cudaMemcpyHostToDevice, fs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(fs);
   if (e != cudaSuccess) {
     moda_destroy_instance(inst);
     return cuda_fail(e, "instance upload");
@@ -486,9 +494,9 @@ void moda_destroy_instance(moda_instance inst) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(inst->device);
-  if (inst->dFs1) cudaFree(inst->dFs1);
-  if (inst->dFs2) cudaFree(inst->dFs2);
-  if (inst->dD) cudaFree(inst->dD);
+  // stream-ordered, without synchronising the device; every run of the
+  // instance has been destroyed (and so has finished) by now
+  if (inst->dFs1) cudaFreeAsync(inst->dFs1, free_stream(inst->device));
   cudaSetDevice(prev);
   delete inst;
 }

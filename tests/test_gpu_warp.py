@@ -179,3 +179,24 @@ def test_warp_engine_rejects_unsupported_options():
         with pytest.raises(moda.MODAError) as ei:
             moda.anneal(g, replicas=2, I_max=100, engine="warp", **kw)
         assert ei.value.status == moda.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_warp_frozen_layout_random_shapes(case):
+    """Seeded random shapes through the frozen-schedule layout (the FAST
+    schedule freezes after about 320 of the 1,500 iterations): instance
+    size, team size, prefetch distance, acceptance and archive rule and the
+    field cache drawn per case; per-iteration traces against the oracle."""
+    rng = np.random.default_rng(1000 + case)
+    n = int(rng.integers(5, 31))
+    team = int(rng.choice([0, 1, 2, 3, 4, 5, 8]))
+    prefetch = int(rng.choice([0, 2, 5, 11, 15]))
+    acc = str(rng.choice(["strict", "lenient"]))
+    arc = str(rng.choice(["explore", "exploit"]))
+    cache = str(rng.choice(["auto", "auto", "off"]))
+    inst = inputs.uniform_instance(n, index=500 + case, workload="P8")
+    kw = dict(replicas=3, I_max=1500, seed=700 + case, accept=acc, archive=arc, **FAST)
+    _, _, res, tr = gpu_run(inst, trace=True, field_cache=cache, engine="warp",
+                            block_threads=32 * team, prefetch=prefetch, **kw)
+    _, orc = oracle_run(inst, trace=True, **kw)
+    compare(res, range(3), orc, n * n, gpu_trace=tr)

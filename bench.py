@@ -405,7 +405,8 @@ def run_batch(args):
     return 0
 
 
-def serve_measure(args, rate: float, requests: int, warmup: int, seq_instances: int):
+def serve_measure(args, rate: float, requests: int, warmup: int, seq_instances: int,
+                  batch_same: bool = False):
     """SERVE: Poisson arrivals (``rate`` per second) of solves with n in
     {20, 30, 50, 75} and I_max in {10^4, 10^5}, 32 replicas each, through
     the serving queue; latency is arrival to the poll that returns the
@@ -474,6 +475,23 @@ def serve_measure(args, rate: float, requests: int, warmup: int, seq_instances: 
               "speedup": seq_span / span_k,
               "kernel_ms_served_over_alone": sum(served_ms) / max(sum(alone_ms), 1e-9)}
     work = sum(32 * q.I_max for q in reqs)
+    # the same requests as one batch launch (all known in advance): the
+    # throughput the GPU gives this mix of sizes and schedules
+    same = None
+    if batch_same:
+        insts = [moda.Instance(q.instance.F1, q.instance.F2, q.instance.D) for q in reqs]
+        prms = [moda.make_params(replicas=32, I_max=q.I_max, seed=q.seed, engine=args.engine)
+                for q in reqs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        runs = moda.anneal_batch(insts, prms)
+        for r in runs:
+            r.wait()
+        bspan = time.perf_counter() - t0
+        for r in runs:
+            r.close()
+        same = {"batch_s": bspan, "batch_replica_steps_per_s": work / bspan,
+                "served_over_batch_time": span / bspan}
     return {
         "metric": "bQAP solves/s", "value": value, "unit": "solves/s", "n_gpus": 1,
         "steps": 1, "warmup": warmup, "ms_per_step": span * 1e3,
@@ -489,6 +507,7 @@ def serve_measure(args, rate: float, requests: int, warmup: int, seq_instances: 
         "most_running": most,
         "replica_steps_per_s": work / span,
         "vs_one_at_a_time": vs,
+        "vs_same_requests_batched": same,
         "e2e": {"value": value, "unit": "solves/s",
                 "h2d_bytes_per_step": sum(3 * q.instance.n ** 2 * 4 for q in reqs),
                 "d2h_bytes_per_step": None, "note": "serving is end to end by construction"},
@@ -499,7 +518,7 @@ def serve_measure(args, rate: float, requests: int, warmup: int, seq_instances: 
 def serve_both(args, requests: int, warmup: int, seq_instances: int):
     """The SERVE config's rate, then 70 % of the capacity it measured, so the
     latency of the second line is the server's own rather than queueing."""
-    line = serve_measure(args, args.rate, requests, warmup, seq_instances)
+    line = serve_measure(args, args.rate, requests, warmup, seq_instances, batch_same=True)
     cap = line["value"]
     if cap * 0.7 < args.rate:
         sus = serve_measure(args, 0.7 * cap, requests, 0, 0)
